@@ -1,0 +1,171 @@
+/*
+ * psdproj.h -- C ABI of the GB300 (sm_103a) composite-polynomial projection
+ * onto the cone of positive semidefinite matrices.
+ *
+ * The operation (paper: "Factorization-free Orthogonal Projection onto the
+ * PSD Cone with Composite Polynomial Filtering"):
+ *   Pi(X) = argmin_{Y PSD} ||Y - X||_F / 2                      (Sec. 1)
+ * approximated by Algorithm 2:
+ *   1. (sigma, q) = largest Ritz pair of a 20-step Lanczos run on X^2  (Sec. 3.4)
+ *   2. lam~ = sqrt(sigma + ||X^2 q - sigma q||_2)    (Theorem 2, upper bound of ||X||_2)
+ *   3. X_0 = X / lam~
+ *   4. X_t = f_t(X_{t-1}) / s_t,  f_t(x) = a_t x + b_t x^3 + c_t x^5, t = 1..T
+ *      (coefficients: Table 2, f~*_half, T = 7, or Table 1, f~*_single, T = 10;
+ *       s_t: the 1/1.01 resp. 1/1.001 rescale of Sec. 3.4)
+ *   5. return lam~ X_0 (I + X_T) / 2  =  (X + lam~ X_0 X_T) / 2
+ * Each stage costs three symmetric matrix products (X^2, (X^2)^2,
+ * X (a I + b X^2 + c X^4)), so a projection is 3T + 1 products: 22 (half),
+ * 31 (single).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are dense, FP32, column-major with leading dimension ld >= n,
+ *    in device memory owned by the caller.  X must be symmetric; the library
+ *    reads ONLY the upper triangle, i.e. the elements X[i + j*ld] with
+ *    i <= j, and treats X[j + i*ld] as equal to X[i + j*ld].  The output is
+ *    written in full (both triangles) and is exactly symmetric.
+ *  - out may be the same buffer as X (same pointer and the same ld); any
+ *    other overlap is rejected with PSD_ERR_INVALID_ARG.
+ *  - Calls are asynchronous on `stream`.  Argument errors are returned
+ *    synchronously; numerical and device-side conditions (non-finite input,
+ *    a bound that turned out too small, a device wait that timed out) are
+ *    written to a psd_info_t in device memory, whose `status` field holds a
+ *    psd_status_t.
+ *  - No entry point falls back to the CPU.  If the GPU is not an sm_103
+ *    device the calls return PSD_ERR_UNSUPPORTED.
+ *  - The Lanczos start vector is fixed: v_i = 2 u_i - 1 with
+ *    u_i = (SplitMix64(seed + (i+1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53,
+ *    seed = 0x243F6A8885A308D3, normalised to unit length.
+ */
+#ifndef PSDPROJ_H
+#define PSDPROJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *psd_stream_t;
+
+typedef enum {
+  PSD_OK = 0,
+  PSD_ERR_INVALID_ARG = 1, /* bad size, pointer, ld, overlap or precision */
+  PSD_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  PSD_ERR_NO_MEMORY = 3,   /* device allocation failed / workspace too small */
+  PSD_ERR_NONFINITE = 4,   /* device: NaN or Inf in the input or an iterate */
+  PSD_ERR_BOUND = 5,       /* device: max |X_T(i,j)| exceeded 1 + 1e-2: the norm
+                              bound was below ||X||_2 and the filter diverged */
+  PSD_ERR_TIMEOUT = 6,     /* device: a bounded wait inside a kernel gave up */
+  PSD_ERR_UNSUPPORTED = 7  /* no sm_103 device, or precision not built */
+} psd_status_t;
+
+typedef enum {
+  PSD_PREC_FP32 = 0,  /* f~*_single (Table 1), T = 10, 31 products; each product
+                         is three TF32 tensor-core products of the hi/lo split
+                         operands (Ootomo & Yokota 2022), FP32 accumulation */
+  PSD_PREC_FP16 = 1,  /* f~*_half (Table 2), T = 7, 22 products, FP16 operands,
+                         FP32 accumulation in tensor memory */
+  PSD_PREC_BF16 = 2,  /* as FP16 with BF16 operands */
+  PSD_PREC_MIXED = 3, /* FP16 stages, final product in FP32 (TF32 split) */
+  PSD_PREC_FP8_EARLY = 4 /* reserved: not built, returns PSD_ERR_UNSUPPORTED */
+} psd_precision_t;
+
+/* Per-projection report, written by the device. */
+typedef struct {
+  int32_t status;        /* psd_status_t of the device-side work */
+  int32_t lanczos_steps; /* m <= 20: Lanczos steps run (fewer on breakdown) */
+  double lambda_bound;   /* lam~ used to scale X */
+  double lanczos_sigma;  /* largest Ritz value of X^2 */
+  double lanczos_resid;  /* ||X^2 q - sigma q||_2 */
+  double fro_X;          /* ||X||_F (FP64) */
+  double max_diag;       /* max_i |X_ii| */
+  double overshoot_max;  /* max_ij |X_T(i,j)| of the last stage */
+} psd_info_t;
+
+/* Project one matrix (Algorithm 2).  X: n x n upper triangle read, ld >= n.
+ * out: n x n written, leading dimension ld.  Workspace comes from a library
+ * cache keyed by (device, stream, n, precision) and is kept until
+ * psd_release_workspaces(); the report goes to an internal device record
+ * readable with psd_last_info().  n == 0 is a no-op. */
+psd_status_t psd_project(int64_t n, const float *X, int64_t ld, float *out,
+                         psd_precision_t precision, psd_stream_t stream);
+
+/* As psd_project with a separate output leading dimension, a caller-owned
+ * device report (d_info, may be NULL) and an optional caller-owned device
+ * workspace of ws_bytes >= psd_workspace_size(n, precision) bytes (NULL: use
+ * the library cache).  The workspace must stay untouched until the call has
+ * finished on `stream`. */
+psd_status_t psd_project_ex(int64_t n, const float *X, int64_t ld, float *out, int64_t ld_out,
+                            psd_precision_t precision, psd_info_t *d_info, void *workspace,
+                            size_t ws_bytes, psd_stream_t stream);
+
+/* Bytes of device workspace psd_project_ex needs for (n, precision); 0 on bad args. */
+size_t psd_workspace_size(int64_t n, psd_precision_t precision);
+
+/* Waits for `stream` and copies the report of the last psd_project call on
+ * that stream to *host_info.  PSD_ERR_INVALID_ARG if no call was made. */
+psd_status_t psd_last_info(psd_stream_t stream, psd_info_t *host_info);
+
+/* Frees every cached workspace and captured graph (synchronises the device). */
+psd_status_t psd_release_workspaces(void);
+
+/* Norm bound alone (Algorithm 2 steps 1-2): writes lam~ and the Lanczos
+ * fields of *d_info (device memory).  Same X conventions as psd_project. */
+psd_status_t psd_norm_bound(int64_t n, const float *X, int64_t ld, psd_info_t *d_info,
+                            psd_stream_t stream);
+
+/* ---- Batched projection of a block-diagonal cone ------------------------ */
+/* One block: X, out column-major device matrices of order n (1 <= n <= 1024),
+ * upper triangle of X read; info may be NULL. */
+typedef struct {
+  int64_t n;
+  const float *X;
+  int64_t ld;
+  float *out;
+  int64_t ld_out;
+  psd_info_t *info;
+} psd_block_desc_t;
+
+/* Projects `count` independent blocks.  d_descs is an array of `count`
+ * descriptors in DEVICE memory.  The library reads the block orders back to
+ * the host once per call (a synchronous 8*count-byte copy) to pick the cached
+ * plan for that size signature; all compute is then enqueued on `stream`.
+ * Results are bit-identical to projecting each block alone with the same
+ * precision. */
+psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
+                                 psd_precision_t precision, psd_stream_t stream);
+
+/* ---- Building block exposed for tests and users ------------------------- */
+/* Symmetric product C = epi(A * B) of two n x n symmetric 16-bit matrices
+ * (A, B, C share the leading dimension ld, a multiple of 8; pointers 16-byte
+ * aligned; FP16 or BF16 by `precision`).  Only the upper tiles of A * B are
+ * formed on the tensor cores and mirrored, so C is exactly symmetric.
+ *   epi 0: C = A B                       (16-bit out)
+ *   epi 1: C = a I + b Y + c A B          (16-bit out, Y = aux, ld)
+ *   epi 2: C = (A B) * s                  (16-bit out)
+ *   epi 3: C = (Xf + lam * A B) / 2       (FP32 out with leading dim ld_out,
+ *                                          Xf = aux FP32 upper triangle, ld_aux)
+ * params: {a, b, c} for epi 1, {s} for epi 2, {lam} for epi 3.
+ * d_absmax (may be NULL): device float receiving max |C(i,j)| (atomic max). */
+psd_status_t psd_symm_product(int64_t n, const void *A, const void *B, int64_t ld, void *C,
+                              int64_t ld_out, psd_precision_t precision, int32_t epi,
+                              const double *params, const void *aux, int64_t ld_aux,
+                              float *d_absmax, psd_stream_t stream);
+
+/* ---- Host-only queries (no GPU needed) ----------------------------------- */
+const char *psd_status_string(psd_status_t status);
+/* Copies the library's schedule for `precision`: *T stages, coef[3*t + {0,1,2}]
+ * = (a_t, b_t, c_t), post_scale[t] = s_t.  Arrays must hold >= 10 entries
+ * (coef >= 30).  Returns PSD_ERR_INVALID_ARG for an unknown precision. */
+psd_status_t psd_schedule(psd_precision_t precision, int32_t *T, double *coef, double *post_scale);
+/* Number of tensor-core product launches one projection makes (3T + 1). */
+int32_t psd_gemm_count(psd_precision_t precision);
+/* Library version string. */
+const char *psd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSDPROJ_H */

@@ -1,0 +1,182 @@
+"""Thin ctypes binding of libpsdproj (include/psdproj.h), same names as the C ABI.
+
+Argument marshalling only: every step of the projection runs in the CUDA
+library.  Pointers may be given as integers or as objects with ``data_ptr()``
+(torch tensors); streams as integers, ``None`` (legacy default stream) or
+objects with ``cuda_stream``.  A non-zero status raises ``PsdError``.  If the
+library has not been built, ``lib()`` raises: there is no fallback.
+
+Storage note for torch users: the library reads the column-major upper
+triangle X[i + j*ld], i <= j.  For a C-contiguous (row-major) tensor T of
+shape (n, n) with ld = T.stride(0), that is T[r][c] with r >= c.  Symmetric
+inputs need no care.
+"""
+import ctypes
+import os
+
+from . import _build
+
+PSD_OK = 0
+STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID_ARG", 2: "PSD_ERR_CUDA", 3: "PSD_ERR_NO_MEMORY",
+          4: "PSD_ERR_NONFINITE", 5: "PSD_ERR_BOUND", 6: "PSD_ERR_TIMEOUT", 7: "PSD_ERR_UNSUPPORTED"}
+PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "mixed": 3, "fp8_early": 4}
+
+
+class PsdError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = int(status)
+        super().__init__("%s (%d) %s" % (STATUS.get(self.status, "?"), self.status, what))
+
+
+class psd_info_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
+                ("lambda_bound", ctypes.c_double), ("lanczos_sigma", ctypes.c_double),
+                ("lanczos_resid", ctypes.c_double), ("fro_X", ctypes.c_double),
+                ("max_diag", ctypes.c_double), ("overshoot_max", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class psd_block_desc_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("X", ctypes.c_void_p), ("ld", ctypes.c_int64),
+                ("out", ctypes.c_void_p), ("ld_out", ctypes.c_int64), ("info", ctypes.c_void_p)]
+
+
+_lib = None
+
+_VP, _I64, _I32, _SZ, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_double
+_SIGS = {
+    "psd_project": ([_I64, _VP, _I64, _VP, _I32, _VP], _I32),
+    "psd_project_ex": ([_I64, _VP, _I64, _VP, _I64, _I32, _VP, _VP, _SZ, _VP], _I32),
+    "psd_workspace_size": ([_I64, _I32], _SZ),
+    "psd_last_info": ([_VP, ctypes.POINTER(psd_info_t)], _I32),
+    "psd_release_workspaces": ([], _I32),
+    "psd_norm_bound": ([_I64, _VP, _I64, _VP, _VP], _I32),
+    "psd_project_batched": ([_I32, _VP, _I32, _VP], _I32),
+    "psd_symm_product": ([_I64, _VP, _VP, _I64, _VP, _I64, _I32, _I32, ctypes.POINTER(_D), _VP, _I64, _VP,
+                          _VP], _I32),
+    "psd_status_string": ([_I32], ctypes.c_char_p),
+    "psd_schedule": ([_I32, ctypes.POINTER(_I32), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I32),
+    "psd_gemm_count": ([_I32], _I32),
+    "psd_version": ([], ctypes.c_char_p),
+}
+
+
+def lib():
+    """Open libpsdproj.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libpsdproj.so is not built (%s); run __graft_entry__.build(). "
+                               "There is no CPU fallback." % path)
+        h = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            if hasattr(h, name):
+                f = getattr(h, name)
+                f.argtypes = args
+                f.restype = res
+        _lib = h
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, ctypes.c_void_p):
+        return x.value
+    raise TypeError("expected a device pointer, got %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError("expected a CUDA stream, got %r" % type(s))
+
+
+def _prec(p):
+    return PRECISION[p] if isinstance(p, str) else int(p)
+
+
+def _check(st, what=""):
+    if st != PSD_OK:
+        raise PsdError(st, what)
+
+
+def psd_project(n, X, ld, out, precision="fp16", stream=None):
+    _check(lib().psd_project(n, _ptr(X), ld, _ptr(out), _prec(precision), _stream(stream)), "psd_project")
+
+
+def psd_project_ex(n, X, ld, out, ld_out, precision="fp16", d_info=None, workspace=None, ws_bytes=0,
+                   stream=None):
+    _check(lib().psd_project_ex(n, _ptr(X), ld, _ptr(out), ld_out, _prec(precision), _ptr(d_info),
+                                _ptr(workspace), ws_bytes, _stream(stream)), "psd_project_ex")
+
+
+def psd_workspace_size(n, precision="fp16"):
+    return int(lib().psd_workspace_size(n, _prec(precision)))
+
+
+def psd_last_info(stream=None):
+    info = psd_info_t()
+    _check(lib().psd_last_info(_stream(stream), ctypes.byref(info)), "psd_last_info")
+    return info.as_dict()
+
+
+def psd_release_workspaces():
+    _check(lib().psd_release_workspaces(), "psd_release_workspaces")
+
+
+def psd_norm_bound(n, X, ld, d_info, stream=None):
+    _check(lib().psd_norm_bound(n, _ptr(X), ld, _ptr(d_info), _stream(stream)), "psd_norm_bound")
+
+
+def psd_project_batched(count, d_descs, precision="bf16", stream=None):
+    _check(lib().psd_project_batched(count, _ptr(d_descs), _prec(precision), _stream(stream)),
+           "psd_project_batched")
+
+
+def psd_symm_product(n, A, B, ld, C, ld_out=0, precision="fp16", epi=0, params=(), aux=None, ld_aux=0,
+                     d_absmax=None, stream=None):
+    arr = (ctypes.c_double * max(1, len(params)))(*params) if params else None
+    _check(lib().psd_symm_product(n, _ptr(A), _ptr(B), ld, _ptr(C), ld_out, _prec(precision), epi, arr,
+                                  _ptr(aux), ld_aux, _ptr(d_absmax), _stream(stream)), "psd_symm_product")
+
+
+def psd_status_string(status):
+    return lib().psd_status_string(status).decode()
+
+
+def psd_schedule(precision):
+    T = ctypes.c_int32()
+    coef = (ctypes.c_double * 30)()
+    post = (ctypes.c_double * 10)()
+    _check(lib().psd_schedule(_prec(precision), ctypes.byref(T), coef, post), "psd_schedule")
+    t = T.value
+    return [tuple(coef[3 * i:3 * i + 3]) for i in range(t)], list(post[:t])
+
+
+def psd_gemm_count(precision):
+    return int(lib().psd_gemm_count(_prec(precision)))
+
+
+def psd_version():
+    return lib().psd_version().decode()
+
+
+INFO_BYTES = ctypes.sizeof(psd_info_t)
+DESC_BYTES = ctypes.sizeof(psd_block_desc_t)
+
+
+def info_from_bytes(raw):
+    """Decode a psd_info_t copied from the device (bytes of length INFO_BYTES)."""
+    return psd_info_t.from_buffer_copy(bytes(raw)).as_dict()

@@ -1,0 +1,116 @@
+// Internal declarations shared by the translation units of libpsdproj.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "psdproj.h"
+
+namespace psd {
+
+constexpr int kMaxSteps = 20;     // Lanczos steps (Sec. 3.4, Algorithm 2)
+constexpr int kMaxStages = 10;    // T <= 10 (Table 1)
+constexpr int kSymvTile = 128;    // Lanczos mat-vec tile
+constexpr int kVecThreads = 64;   // threads per CTA of the Lanczos vector kernels
+constexpr int64_t kMaxOrder = 131072;
+constexpr double kBreakdown = 1e-12;       // beta_j <= 1e-12 ||X||_F^2: invariant subspace
+constexpr float kOvershootLimit = 1.01f;   // max |X_T(i,j)| above this: bound too small
+
+// Caller pointers read by the kernels of a captured graph.  A tiny kernel
+// launched (with these as parameters) in front of each graph replay writes it.
+struct DevArgs {
+  const float* X;
+  int64_t ld;
+  float* out;
+  int64_t ld_out;
+  psd_info_t* info;
+};
+
+// Device-resident state of one projection.
+struct DevState {
+  double alpha[kMaxSteps];
+  double beta[kMaxSteps];
+  double y[kMaxSteps];   // Ritz vector in the Lanczos basis
+  double sigma;
+  double resid;
+  double lambda;         // lam~
+  double fro;            // ||X||_F
+  double maxdiag;
+  double inv_lambda;     // 1 / lam~ (0 when lam~ == 0)
+  int m;                 // Lanczos steps taken
+  int done;              // breakdown reached
+  int status;            // first psd_status_t raised on the device
+  unsigned maxdiag_bits; // max |X_ii| as float bits (atomicMax)
+  unsigned absmax_bits;  // max |X_T(i,j)| as float bits (atomicMax)
+  int pad;
+};
+
+// Epilogue kinds of the symmetric product (fused into the tensor-core kernel).
+enum Epi : int { EPI_COPY = 0, EPI_POLY = 1, EPI_SCALE = 2, EPI_FINAL = 3 };
+
+// Operand storage of the chain.
+enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2 };
+
+struct EpiParams {
+  void* C;               // 16-bit output (ld = ldc) for EPI_COPY/POLY/SCALE
+  int64_t ldc;
+  void* C_lo;            // TF32x3: low parts of the output
+  const void* Y;         // EPI_POLY: the stage's X^2 (same storage as C)
+  const void* Y_lo;
+  int64_t ldy;
+  float a, b, c, s;      // EPI_POLY coefficients, EPI_SCALE factor
+  const DevArgs* args;   // EPI_FINAL: X, ld, out, ld_out
+  const DevState* st;    // EPI_FINAL: lam~
+  unsigned* absmax;      // optional: atomic max of |output|
+  int* status;           // device status word for timeouts
+};
+
+struct GemmParams {
+  int n;
+  int k_blocks;
+  int num_tiles;
+  const int2* tiles;     // (m0, n0) of each 128 x 256 output tile, upper triangle
+  uint32_t idesc;
+  EpiParams ep;
+};
+
+// --- host helpers (symgemm.cu) ---
+bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows);
+std::vector<int2> make_tile_list(int64_t n);
+cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                           const GemmParams& p, int grid, cudaStream_t stream);
+int num_sms();
+
+// --- norm bound and cast (normbound.cu) ---
+struct LanczosBufs {
+  int64_t n, npad;
+  int nb;                // 128-blocks
+  int ntiles;            // symv tiles nb (nb + 1) / 2
+  int nvec_ctas;         // CTAs of the vector kernels
+  double* Qv;            // (kMaxSteps + 1) x npad Lanczos vectors
+  double* u;             // npad
+  double* w;             // npad
+  double* q;             // npad  Ritz vector
+  float* vh;             // npad  hi part of the mat-vec input
+  float* vl;             // npad  lo part
+  float2* P1;            // nb x npad row partials
+  float2* P2;            // nb x npad column partials
+  double* dots;          // nvec_ctas x 32 partial dot products
+  double* dots2;         // nvec_ctas x 32
+  double* norms;         // nvec_ctas
+  double* tile_fro;      // ntiles
+};
+size_t lanczos_bytes(int64_t n);
+void lanczos_carve(LanczosBufs& b, int64_t n, uint8_t* base);
+cudaError_t enqueue_norm_bound(const LanczosBufs& b, const DevArgs* args, DevState* st,
+                               cudaStream_t stream);
+cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n,
+                               void* M, void* M_lo, int64_t ldm, cudaStream_t stream);
+cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t stream);
+cudaError_t enqueue_state_reset(DevState* st, cudaStream_t stream);
+cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t stream);
+
+}  // namespace psd

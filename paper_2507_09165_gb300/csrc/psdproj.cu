@@ -1,0 +1,531 @@
+// Host side of libpsdproj: argument checks, plans (workspace carve-up, tensor
+// maps, tile list), CUDA-graph capture of the whole projection, and the C ABI
+// of include/psdproj.h.
+//
+// One projection enqueues (Algorithm 2):
+//   norm bound: 20-step Lanczos on X^2 + Theorem 2          (normbound.cu)
+//   X_0 = RN(X / lam~), full symmetric 16-bit matrix          (normbound.cu)
+//   for t = 1..T: Y = X^2; P = a I + b Y + c Y^2; X_t = X P / s_t   (symgemm.cu)
+//   out = (X + lam~ X_0 X_T) / 2                               (symgemm.cu)
+//   status / overshoot report
+// The sequence is captured once per (device, stream, n, precision, workspace)
+// into a CUDA graph; the caller's pointers reach the graph through a small
+// device argument block written by a one-thread kernel in front of each replay.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace psd {
+
+namespace {
+
+// Table 2 of the paper, column f~*_half (T = 7).
+const double kHalfCoef[7][3] = {
+    {8.2885332412, -22.5927099246, 15.8201383114}, {4.1666196466, -2.9679004036, 0.5307623217},
+    {4.0611848147, -2.9698947955, 0.5492133813},   {3.6678301399, -2.7561018955, 0.5421513305},
+    {2.7632556383, -2.0607754898, 0.4695405857},   {2.0527445797, -1.4345145882, 0.4070669182},
+    {1.8804816691, -1.2583997294, 0.3779501813},
+};
+// Table 1 of the paper, column f~*_single (T = 10).
+const double kSingleCoef[10][3] = {
+    {8.3119043343, -23.0739115930, 16.4664144722}, {4.1439360087, -2.9176674704, 0.5246212487},
+    {4.0257813209, -2.9025002398, 0.5334261214},   {3.5118574347, -2.5740236523, 0.5050097282},
+    {2.4398158400, -1.7586675341, 0.4191290613},   {1.9779835097, -1.3337358510, 0.3772169049},
+    {1.9559726949, -1.3091355170, 0.3746734515},   {1.9282822454, -1.2823649693, 0.3704626545},
+    {1.9220135179, -1.2812524618, 0.3707011753},   {1.8942192942, -1.2613293407, 0.3676616051},
+};
+
+struct Schedule {
+  int T;
+  double coef[kMaxStages][3];
+  double post[kMaxStages];  // s_t
+};
+
+// Sec. 3.4: half divides the iterate by 1.01 after every stage but the last;
+// single divides by 1.001 after each of the first eight stages.
+bool get_schedule(psd_precision_t prec, Schedule& s) {
+  switch (prec) {
+    case PSD_PREC_FP16:
+    case PSD_PREC_BF16:
+    case PSD_PREC_MIXED:
+      s.T = 7;
+      for (int t = 0; t < 7; ++t) {
+        for (int k = 0; k < 3; ++k) s.coef[t][k] = kHalfCoef[t][k];
+        s.post[t] = t < 6 ? 1.01 : 1.0;
+      }
+      return true;
+    case PSD_PREC_FP32:
+      s.T = 10;
+      for (int t = 0; t < 10; ++t) {
+        for (int k = 0; k < 3; ++k) s.coef[t][k] = kSingleCoef[t][k];
+        s.post[t] = t < 8 ? 1.001 : 1.0;
+      }
+      return true;
+    default:
+      return false;
+  }
+}
+
+int dtype_of(psd_precision_t prec) {
+  return prec == PSD_PREC_BF16 ? DT_BF16 : prec == PSD_PREC_FP32 ? DT_TF32X3 : DT_F16;
+}
+
+bool prec_built(psd_precision_t prec) { return prec == PSD_PREC_FP16 || prec == PSD_PREC_BF16; }
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Leading dimension of the internal iterates: a multiple of 64 elements (128 B rows).
+int64_t internal_ld(int64_t n) { return round_up(std::max<int64_t>(n, 1), 64); }
+
+size_t matrix_bytes(int64_t n, int dtype) {
+  const int64_t ld = internal_ld(n);
+  const size_t one = static_cast<size_t>(ld) * static_cast<size_t>(n) * (dtype == DT_TF32X3 ? 8 : 2);
+  return round_up(static_cast<int64_t>(one), 1024);
+}
+
+size_t total_ws_bytes(int64_t n, psd_precision_t prec) {
+  return 4 * matrix_bytes(n, dtype_of(prec)) + lanczos_bytes(n) + 1024;
+}
+
+psd_status_t check_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PSD_ERR_CUDA;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return PSD_ERR_UNSUPPORTED;
+  return PSD_OK;
+}
+
+struct Plan {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0;
+  psd_precision_t prec = PSD_PREC_FP16;
+  int dtype = DT_F16;
+  Schedule sched{};
+  uint8_t* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = false;
+  void* M[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* Mlo[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t ldm = 0;
+  LanczosBufs L{};
+  DevArgs* d_args = nullptr;
+  DevState* d_state = nullptr;
+  psd_info_t* d_info = nullptr;  // default report
+  int2* d_tiles = nullptr;
+  int ntiles = 0;
+  CUtensorMap tmA[4], tmB[4];
+  cudaGraphExec_t exec = nullptr;
+  bool graph_tried = false;
+};
+
+using PlanKey = std::tuple<int, cudaStream_t, int64_t, int, void*>;
+std::mutex g_mu;
+std::map<PlanKey, Plan*> g_plans;
+std::map<std::pair<int, cudaStream_t>, Plan*> g_last;  // last default-report plan per stream
+
+void free_plan(Plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->owns_ws && p->ws) cudaFree(p->ws);
+  if (p->d_args) cudaFree(p->d_args);  // one allocation: args | state | info | tiles
+  delete p;
+}
+
+psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
+  const int64_t n = p->n;
+  p->dtype = dtype_of(p->prec);
+  if (!get_schedule(p->prec, p->sched)) return PSD_ERR_INVALID_ARG;
+  p->ldm = internal_ld(n);
+  p->ws_bytes = total_ws_bytes(n, p->prec);
+  if (user_ws) {
+    if (user_bytes < p->ws_bytes) return PSD_ERR_NO_MEMORY;
+    p->ws = static_cast<uint8_t*>(user_ws);
+    p->owns_ws = false;
+  } else {
+    if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p->ws = nullptr;
+      return PSD_ERR_NO_MEMORY;
+    }
+    p->owns_ws = true;
+  }
+  uint8_t* base = reinterpret_cast<uint8_t*>(round_up(reinterpret_cast<int64_t>(p->ws), 1024));
+  const size_t mb = matrix_bytes(n, p->dtype);
+  for (int i = 0; i < 4; ++i) {
+    p->M[i] = base + i * mb;
+    if (p->dtype == DT_TF32X3)
+      p->Mlo[i] = base + i * mb + static_cast<size_t>(p->ldm) * static_cast<size_t>(n) * 4;
+  }
+  lanczos_carve(p->L, n, base + 4 * mb);
+
+  // small library-owned records: args | state | info | tiles
+  std::vector<int2> tiles = make_tile_list(n);
+  p->ntiles = static_cast<int>(tiles.size());
+  const size_t o_state = round_up(sizeof(DevArgs), 256);
+  const size_t o_info = o_state + round_up(sizeof(DevState), 256);
+  const size_t o_tiles = o_info + round_up(sizeof(psd_info_t), 256);
+  const size_t small = o_tiles + sizeof(int2) * std::max<size_t>(tiles.size(), 1);
+  uint8_t* sm = nullptr;
+  if (cudaMalloc(&sm, small) != cudaSuccess) {
+    cudaGetLastError();
+    return PSD_ERR_NO_MEMORY;
+  }
+  cudaMemset(sm, 0, small);
+  p->d_args = reinterpret_cast<DevArgs*>(sm);
+  p->d_state = reinterpret_cast<DevState*>(sm + o_state);
+  p->d_info = reinterpret_cast<psd_info_t*>(sm + o_info);
+  p->d_tiles = reinterpret_cast<int2*>(sm + o_tiles);
+  if (!tiles.empty() &&
+      cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PSD_ERR_CUDA;
+  for (int i = 0; i < 4; ++i) {
+    if (p->dtype == DT_TF32X3) continue;
+    if (!encode_tmap(&p->tmA[i], p->dtype, p->M[i], n, p->ldm, 128) ||
+        !encode_tmap(&p->tmB[i], p->dtype, p->M[i], n, p->ldm, 256))
+      return PSD_ERR_CUDA;
+  }
+  return PSD_OK;
+}
+
+GemmParams base_params(const Plan* p) {
+  GemmParams g{};
+  g.n = static_cast<int>(p->n);
+  g.k_blocks = static_cast<int>((p->n + 63) / 64);
+  g.num_tiles = p->ntiles;
+  g.tiles = p->d_tiles;
+  const uint32_t fmt = p->dtype == DT_BF16 ? 1u : 0u;
+  g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(256 >> 3) << 17) |
+            (static_cast<uint32_t>(128 >> 4) << 24);
+  g.ep.status = &p->d_state->status;
+  return g;
+}
+
+// Enqueue the whole projection (used for graph capture and for direct launch).
+cudaError_t enqueue_projection(Plan* p, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = enqueue_norm_bound(p->L, p->d_args, p->d_state, s)) != cudaSuccess) return e;
+  if ((e = enqueue_scale_cast(p->dtype, p->d_args, p->d_state, p->n, p->M[0], p->Mlo[0], p->ldm, s)) !=
+      cudaSuccess)
+    return e;
+  const int grid = num_sms();
+  int cur = 0;
+  for (int t = 0; t < p->sched.T; ++t) {
+    int a, b;
+    if (cur == 0) {
+      a = 1;
+      b = 2;
+    } else {
+      int o[2], k = 0;
+      for (int i = 1; i <= 3; ++i)
+        if (i != cur) o[k++] = i;
+      a = o[0];
+      b = o[1];
+    }
+    // Y = X_{t-1}^2 -> a
+    GemmParams g = base_params(p);
+    g.ep.C = p->M[a];
+    g.ep.ldc = p->ldm;
+    if ((e = launch_symgemm(p->dtype, EPI_COPY, p->tmA[cur], p->tmB[cur], g, grid, s)) != cudaSuccess) return e;
+    // P = a_t I + b_t Y + c_t Y^2 -> b
+    g = base_params(p);
+    g.ep.C = p->M[b];
+    g.ep.ldc = p->ldm;
+    g.ep.Y = p->M[a];
+    g.ep.ldy = p->ldm;
+    g.ep.a = static_cast<float>(p->sched.coef[t][0]);
+    g.ep.b = static_cast<float>(p->sched.coef[t][1]);
+    g.ep.c = static_cast<float>(p->sched.coef[t][2]);
+    if ((e = launch_symgemm(p->dtype, EPI_POLY, p->tmA[a], p->tmB[a], g, grid, s)) != cudaSuccess) return e;
+    // X_t = X_{t-1} P / s_t -> a
+    g = base_params(p);
+    g.ep.C = p->M[a];
+    g.ep.ldc = p->ldm;
+    g.ep.s = static_cast<float>(1.0 / p->sched.post[t]);
+    if (t == p->sched.T - 1) g.ep.absmax = &p->d_state->absmax_bits;
+    if ((e = launch_symgemm(p->dtype, EPI_SCALE, p->tmA[cur], p->tmB[b], g, grid, s)) != cudaSuccess) return e;
+    cur = a;
+  }
+  // out = (X + lam~ X_0 X_T) / 2
+  GemmParams g = base_params(p);
+  g.ep.args = p->d_args;
+  g.ep.st = p->d_state;
+  if ((e = launch_symgemm(p->dtype, EPI_FINAL, p->tmA[0], p->tmB[cur], g, grid, s)) != cudaSuccess) return e;
+  return enqueue_finalize(p->d_args, p->d_state, s);
+}
+
+Plan* get_plan(int dev, cudaStream_t stream, int64_t n, psd_precision_t prec, void* user_ws, size_t user_bytes,
+               psd_status_t* st) {
+  PlanKey key{dev, stream, n, static_cast<int>(prec), user_ws};
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) {
+    *st = PSD_OK;
+    return it->second;
+  }
+  Plan* p = new Plan();
+  p->device = dev;
+  p->stream = stream;
+  p->n = n;
+  p->prec = prec;
+  *st = build_plan(p, user_ws, user_bytes);
+  if (*st != PSD_OK) {
+    free_plan(p);
+    return nullptr;
+  }
+  g_plans[key] = p;
+  return p;
+}
+
+// Capture the projection into a graph on a private stream (once per plan).
+void ensure_graph(Plan* p) {
+  if (p->graph_tried) return;
+  p->graph_tried = true;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaError_t e = enqueue_projection(p, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess && e2 == cudaSuccess && graph) {
+      if (cudaGraphInstantiate(&p->exec, graph, 0) != cudaSuccess) p->exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  cudaGetLastError();
+  cudaStreamDestroy(cs);
+}
+
+bool ranges_overlap(const float* a, const float* b, int64_t n, int64_t lda, int64_t ldb) {
+  const char* a0 = reinterpret_cast<const char*>(a);
+  const char* a1 = reinterpret_cast<const char*>(a + (n - 1) * lda + n);
+  const char* b0 = reinterpret_cast<const char*>(b);
+  const char* b1 = reinterpret_cast<const char*>(b + (n - 1) * ldb + n);
+  return a0 < b1 && b0 < a1;
+}
+
+psd_status_t project_impl(int64_t n, const float* X, int64_t ld, float* out, int64_t ld_out,
+                          psd_precision_t prec, psd_info_t* d_info, void* ws, size_t ws_bytes,
+                          cudaStream_t stream) {
+  if (n < 0 || n > kMaxOrder) return PSD_ERR_INVALID_ARG;
+  if (prec < PSD_PREC_FP32 || prec > PSD_PREC_FP8_EARLY) return PSD_ERR_INVALID_ARG;
+  if (n == 0) return PSD_OK;
+  if (!X || !out || ld < n || ld_out < n) return PSD_ERR_INVALID_ARG;
+  if (ranges_overlap(X, out, n, ld, ld_out) && !(static_cast<const void*>(X) == out && ld == ld_out))
+    return PSD_ERR_INVALID_ARG;
+  if (!prec_built(prec)) return PSD_ERR_UNSUPPORTED;
+  psd_status_t st = check_device();
+  if (st != PSD_OK) return st;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Plan* p = get_plan(dev, stream, n, prec, ws, ws_bytes, &st);
+  if (!p) return st;
+  ensure_graph(p);
+  DevArgs h{X, ld, out, ld_out, d_info ? d_info : p->d_info};
+  if (enqueue_set_args(p->d_args, h, stream) != cudaSuccess) return PSD_ERR_CUDA;
+  cudaError_t e = p->exec ? cudaGraphLaunch(p->exec, stream) : enqueue_projection(p, stream);
+  if (e != cudaSuccess) return PSD_ERR_CUDA;
+  if (!d_info) g_last[{dev, stream}] = p;
+  return PSD_OK;
+}
+
+// --- scratch for the building-block entry point
+struct ProductScratch {
+  DevArgs* d_args = nullptr;
+  DevState* d_state = nullptr;
+  std::map<int64_t, int2*> tiles;
+  std::map<int64_t, int> ntiles;
+};
+std::map<int, ProductScratch> g_prod;
+
+__global__ void set_lambda_kernel(DevState* st, double lam) {
+  st->lambda = lam;
+  st->status = 0;
+}
+
+}  // namespace
+}  // namespace psd
+
+using namespace psd;
+
+extern "C" {
+
+psd_status_t psd_project(int64_t n, const float* X, int64_t ld, float* out, psd_precision_t precision,
+                         psd_stream_t stream) {
+  return project_impl(n, X, ld, out, ld, precision, nullptr, nullptr, 0,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+psd_status_t psd_project_ex(int64_t n, const float* X, int64_t ld, float* out, int64_t ld_out,
+                            psd_precision_t precision, psd_info_t* d_info, void* workspace, size_t ws_bytes,
+                            psd_stream_t stream) {
+  if (workspace && ws_bytes == 0) return PSD_ERR_INVALID_ARG;
+  return project_impl(n, X, ld, out, ld_out, precision, d_info, workspace, ws_bytes,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t psd_workspace_size(int64_t n, psd_precision_t precision) {
+  if (n <= 0 || n > kMaxOrder || precision < PSD_PREC_FP32 || precision > PSD_PREC_FP8_EARLY) return 0;
+  return total_ws_bytes(n, precision);
+}
+
+psd_status_t psd_last_info(psd_stream_t stream, psd_info_t* host_info) {
+  if (!host_info) return PSD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PSD_ERR_CUDA;
+  Plan* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_last.find({dev, reinterpret_cast<cudaStream_t>(stream)});
+    if (it == g_last.end()) return PSD_ERR_INVALID_ARG;
+    p = it->second;
+  }
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return PSD_ERR_CUDA;
+  if (cudaMemcpy(host_info, p->d_info, sizeof(psd_info_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PSD_ERR_CUDA;
+  return PSD_OK;
+}
+
+psd_status_t psd_release_workspaces(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaDeviceSynchronize();
+  for (auto& kv : g_plans) free_plan(kv.second);
+  g_plans.clear();
+  g_last.clear();
+  for (auto& kv : g_prod) {
+    if (kv.second.d_args) cudaFree(kv.second.d_args);
+    for (auto& t : kv.second.tiles) cudaFree(t.second);
+  }
+  g_prod.clear();
+  return PSD_OK;
+}
+
+psd_status_t psd_norm_bound(int64_t n, const float* X, int64_t ld, psd_info_t* d_info, psd_stream_t stream) {
+  if (n <= 0 || n > kMaxOrder || !X || ld < n || !d_info) return PSD_ERR_INVALID_ARG;
+  psd_status_t st = check_device();
+  if (st != PSD_OK) return st;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Plan* p = get_plan(dev, s, n, PSD_PREC_FP16, nullptr, 0, &st);
+  if (!p) return st;
+  DevArgs h{X, ld, nullptr, 0, d_info};
+  if (enqueue_set_args(p->d_args, h, s) != cudaSuccess) return PSD_ERR_CUDA;
+  if (enqueue_norm_bound(p->L, p->d_args, p->d_state, s) != cudaSuccess) return PSD_ERR_CUDA;
+  return PSD_OK;
+}
+
+psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t ld, void* C, int64_t ld_out,
+                              psd_precision_t precision, int32_t epi, const double* params, const void* aux,
+                              int64_t ld_aux, float* d_absmax, psd_stream_t stream) {
+  if (n <= 0 || n > kMaxOrder || !A || !B || !C || ld < n || (ld % 8) != 0) return PSD_ERR_INVALID_ARG;
+  if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16) return PSD_ERR_INVALID_ARG;
+  if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;
+  if ((epi == 1 || epi == 2 || epi == 3) && !params) return PSD_ERR_INVALID_ARG;
+  if ((epi == 1 || epi == 3) && !aux) return PSD_ERR_INVALID_ARG;
+  if (epi == 3 && (ld_aux < n || ld_out < n)) return PSD_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return PSD_ERR_INVALID_ARG;
+  psd_status_t st = check_device();
+  if (st != PSD_OK) return st;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(g_mu);
+  ProductScratch& ps = g_prod[dev];
+  if (!ps.d_args) {
+    const size_t o_state = round_up(sizeof(DevArgs), 256);
+    const size_t bytes = o_state + round_up(sizeof(DevState), 256);
+    uint8_t* sm = nullptr;
+    if (cudaMalloc(&sm, bytes) != cudaSuccess) return PSD_ERR_NO_MEMORY;
+    cudaMemset(sm, 0, bytes);
+    ps.d_args = reinterpret_cast<DevArgs*>(sm);
+    ps.d_state = reinterpret_cast<DevState*>(sm + o_state);
+  }
+  if (!ps.tiles.count(n)) {
+    std::vector<int2> tl = make_tile_list(n);
+    int2* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int2) * tl.size()) != cudaSuccess) return PSD_ERR_NO_MEMORY;
+    cudaMemcpy(d, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+    ps.tiles[n] = d;
+    ps.ntiles[n] = static_cast<int>(tl.size());
+  }
+  const int dtype = precision == PSD_PREC_BF16 ? DT_BF16 : DT_F16;
+  CUtensorMap ta, tb;
+  if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 256)) return PSD_ERR_CUDA;
+  GemmParams g{};
+  g.n = static_cast<int>(n);
+  g.k_blocks = static_cast<int>((n + 63) / 64);
+  g.num_tiles = ps.ntiles[n];
+  g.tiles = ps.tiles[n];
+  const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;
+  g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (32u << 17) | (8u << 24);
+  g.ep.C = C;
+  g.ep.ldc = ld;
+  g.ep.status = &ps.d_state->status;
+  g.ep.absmax = reinterpret_cast<unsigned*>(d_absmax);
+  if (epi == 1) {
+    g.ep.Y = aux;
+    g.ep.ldy = ld;
+    g.ep.a = static_cast<float>(params[0]);
+    g.ep.b = static_cast<float>(params[1]);
+    g.ep.c = static_cast<float>(params[2]);
+  } else if (epi == 2) {
+    g.ep.s = static_cast<float>(params[0]);
+  } else if (epi == 3) {
+    DevArgs h{static_cast<const float*>(aux), ld_aux, static_cast<float*>(C), ld_out, nullptr};
+    if (enqueue_set_args(ps.d_args, h, s) != cudaSuccess) return PSD_ERR_CUDA;
+    set_lambda_kernel<<<1, 1, 0, s>>>(ps.d_state, params[0]);
+    g.ep.args = ps.d_args;
+    g.ep.st = ps.d_state;
+    g.ep.absmax = nullptr;
+  }
+  cudaError_t e = launch_symgemm(dtype, epi, ta, tb, g, num_sms(), s);
+  return e == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
+}
+
+const char* psd_status_string(psd_status_t status) {
+  switch (status) {
+    case PSD_OK: return "ok";
+    case PSD_ERR_INVALID_ARG: return "invalid argument";
+    case PSD_ERR_CUDA: return "CUDA runtime error";
+    case PSD_ERR_NO_MEMORY: return "out of device memory or workspace too small";
+    case PSD_ERR_NONFINITE: return "non-finite value in the input or an iterate";
+    case PSD_ERR_BOUND: return "norm bound below ||X||_2: the filter diverged";
+    case PSD_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case PSD_ERR_UNSUPPORTED: return "unsupported device or precision";
+    default: return "unknown status";
+  }
+}
+
+psd_status_t psd_schedule(psd_precision_t precision, int32_t* T, double* coef, double* post_scale) {
+  Schedule s;
+  if (!T || !coef || !post_scale || !get_schedule(precision, s)) return PSD_ERR_INVALID_ARG;
+  *T = s.T;
+  for (int t = 0; t < s.T; ++t) {
+    for (int k = 0; k < 3; ++k) coef[3 * t + k] = s.coef[t][k];
+    post_scale[t] = s.post[t];
+  }
+  return PSD_OK;
+}
+
+int32_t psd_gemm_count(psd_precision_t precision) {
+  Schedule s;
+  if (!get_schedule(precision, s)) return 0;
+  return 3 * s.T + 1;
+}
+
+const char* psd_version(void) { return "psdproj 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,467 @@
+// Symmetric matrix product on the sm_103a tensor cores with fused epilogues.
+//
+// Every product of Algorithm 2 multiplies two polynomials in X, which
+// commute, so the exact result is symmetric.  The kernel forms only the
+// 128 x 256 output tiles of the upper triangle (256 x 256 blocks (I, J) with
+// I <= J, each split into two 128-row tiles), accumulates them in tensor
+// memory with tcgen05.mma (operands staged by TMA with the 128-byte swizzle),
+// and writes every 32 x 32 chunk twice -- at (r, c) and mirrored at (c, r) --
+// so the stored result is exactly symmetric and no separate pass over HBM is
+// needed.  The epilogue applies the stage arithmetic of Sec. 3 / Algorithm 2:
+//   EPI_COPY   Y   = X_{t-1}^2
+//   EPI_POLY   P   = a_t I + b_t Y + c_t Y^2          (the degree-5 stage, Sec. 3.3)
+//   EPI_SCALE  X_t = (X_{t-1} P) / s_t               (Sec. 3.4 rescale)
+//   EPI_FINAL  out = (X + lam~ X_0 X_T) / 2           (Algorithm 2 return, FP32)
+//
+// Warp roles (192 threads, one CTA per SM, persistent over a static tile list):
+//   warp 0   TMA producer (one lane)
+//   warp 1   tensor-memory allocation and MMA issue (one lane)
+//   warps 2-5 epilogue; warp w reads TMEM lanes 32 (w % 4) .. +31
+// Two 256-column FP32 accumulators in tensor memory let the epilogue of one
+// tile overlap the main loop of the next.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace psd {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 256;
+constexpr int kThreads = 192;
+
+// 16-bit operands: 64 K-elements per stage (one 128-byte swizzle row).
+constexpr int kBK16 = 64;
+constexpr int kStages16 = 4;
+constexpr int kABytes16 = kBM * kBK16 * 2;          // 16 KB
+constexpr int kBBytes16 = kBN * kBK16 * 2;          // 32 KB
+constexpr int kStageBytes16 = kABytes16 + kBBytes16;  // 48 KB
+
+// Epilogue staging per warp: 32 rows x 33 words (covers FP32 and 16-bit).
+constexpr int kStgWords = 33;
+constexpr int kEpiWarpBytes = 32 * kStgWords * 4;
+
+constexpr int kTmemCols = 512;
+
+__host__ __device__ constexpr int smem_bytes16() {
+  return 1024 /* alignment slack */ + kStages16 * kStageBytes16 + 4 * kEpiWarpBytes +
+         8 * (2 * kStages16 + 5) + 16;
+}
+
+__device__ __forceinline__ float ld16(const uint16_t* p, int64_t idx, bool bf16) {
+  const uint16_t u = p[idx];
+  return bf16 ? __bfloat162float(__ushort_as_bfloat16(u)) : __half2float(__ushort_as_half(u));
+}
+__device__ __forceinline__ uint16_t to16(float v, bool bf16) {
+  return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+}
+__device__ __forceinline__ float from16(uint16_t u, bool bf16) {
+  return bf16 ? __bfloat162float(__ushort_as_bfloat16(u)) : __half2float(__ushort_as_half(u));
+}
+
+__device__ __forceinline__ void raise_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// One 32 x 32 chunk with 16-bit output.  Lane l holds row r0 + l, v[j] is the
+// accumulator at column c0 + j.  Diagonal chunks (r0 == c0) are symmetrised
+// from their upper part; off-diagonal chunks are written at both positions.
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16, int r0, int c0,
+                                                 const uint32_t (&v)[32], uint32_t* stg, int lane,
+                                                 unsigned& amax_bits) {
+  const int n = p.n;
+  const int r = r0 + lane;
+  const bool diag = (r0 == c0);
+  const bool row_ok = r < n;
+  uint16_t h[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float acc = __uint_as_float(v[j]);
+    float val;
+    if (EPI == EPI_POLY) {
+      const int c = c0 + j;
+      float y = 0.f;
+      if (row_ok && c < n)
+        y = ld16(static_cast<const uint16_t*>(p.ep.Y), static_cast<int64_t>(c) * p.ep.ldy + r, bf16);
+      val = fmaf(p.ep.c, acc, p.ep.b * y);
+      if (diag && j == lane) val += p.ep.a;
+    } else if (EPI == EPI_SCALE) {
+      val = acc * p.ep.s;
+    } else {
+      val = acc;
+    }
+    h[j] = to16(val, bf16);
+  }
+  if (diag) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stg[lane * kStgWords + j] = h[j];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < lane) h[j] = static_cast<uint16_t>(stg[j * kStgWords + lane]);
+    __syncwarp();
+  }
+  if (p.ep.absmax && row_ok) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(from16(h[j], bf16))));
+  }
+  uint16_t* C = static_cast<uint16_t*>(p.ep.C);
+  const int64_t ldc = p.ep.ldc;
+  if (row_ok) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < n) C[static_cast<int64_t>(c0 + j) * ldc + r] = h[j];
+  }
+  if (!diag) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stg[lane * kStgWords + j] = h[j];
+    __syncwarp();
+    const int c = c0 + lane;
+    if (c < n) {
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr)
+        if (r0 + rr < n)
+          C[static_cast<int64_t>(r0 + rr) * ldc + c] = static_cast<uint16_t>(stg[rr * kStgWords + lane]);
+    }
+    __syncwarp();
+  }
+}
+
+// One 32 x 32 chunk of the final output out = (X + lam~ acc) / 2 in FP32,
+// reading only the upper triangle of the caller's X (column-major).
+__device__ __forceinline__ void epilogue_chunk_final(const GemmParams& p, int r0, int c0,
+                                                     const uint32_t (&v)[32], uint32_t* stg,
+                                                     int lane, float lam) {
+  const int n = p.n;
+  const DevArgs* a = p.ep.args;
+  const float* X = a->X;
+  const int64_t ld = a->ld;
+  float* out = a->out;
+  const int64_t ldo = a->ld_out;
+  const int r = r0 + lane;
+  const bool diag = (r0 == c0);
+  const bool row_ok = r < n;
+  float o[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int c = c0 + j;
+    float x = 0.f;
+    const bool upper = !diag || j >= lane;
+    if (row_ok && c < n && upper) x = X[static_cast<int64_t>(c) * ld + r];
+    o[j] = 0.5f * fmaf(lam, __uint_as_float(v[j]), x);
+  }
+  float* sf = reinterpret_cast<float*>(stg);
+  if (diag) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sf[lane * kStgWords + j] = o[j];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < lane) o[j] = sf[j * kStgWords + lane];
+    __syncwarp();
+  }
+  if (row_ok) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < n) out[static_cast<int64_t>(c0 + j) * ldo + r] = o[j];
+  }
+  if (!diag) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sf[lane * kStgWords + j] = o[j];
+    __syncwarp();
+    const int c = c0 + lane;
+    if (c < n) {
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr)
+        if (r0 + rr < n) out[static_cast<int64_t>(r0 + rr) * ldo + c] = sf[rr * kStgWords + lane];
+    }
+    __syncwarp();
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+    symgemm16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const GemmParams p, const int bf16_flag) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* stages = smem;
+  uint32_t* epi_stg = reinterpret_cast<uint32_t*>(smem + kStages16 * kStageBytes16);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages16 * kStageBytes16 + 4 * kEpiWarpBytes);
+  // bars: full[S] | empty[S] | tfull[2] | tempty[2] | drain
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStages16 + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const bool bf16 = bf16_flag != 0;
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + kStages16 + s); };
+  auto tfull_bar = [&](int a) { return smem_u32(bars + 2 * kStages16 + a); };
+  auto tempty_bar = [&](int a) { return smem_u32(bars + 2 * kStages16 + 2 + a); };
+  const uint32_t drain_bar = smem_u32(bars + 2 * kStages16 + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages16; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 4);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int last_parity[kStages16];
+      for (int s = 0; s < kStages16; ++s) last_parity[s] = -1;
+      uint32_t s = 0, ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+        const int2 tc = p.tiles[t];
+        for (int kb = 0; kb < p.k_blocks; ++kb) {
+          if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full_bar(s), kStageBytes16);
+          const uint32_t a_dst = smem_u32(stages + s * kStageBytes16);
+          tma_load_2d(a_dst, &tmA, kb * kBK16, tc.x, full_bar(s));
+          tma_load_2d(a_dst + kABytes16, &tmB, kb * kBK16, tc.y, full_bar(s));
+          last_parity[s] = static_cast<int>(ph);
+          if (++s == kStages16) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies already in flight land before the CTA exits
+        for (int q = 0; q < kStages16; ++q)
+          if (last_parity[q] >= 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(full_bar(q), static_cast<uint32_t>(last_parity[q])) &&
+                   globaltimer_ns() - t0 < kWaitLimitNs) {
+            }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+      if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + acc * kBN;
+      for (int kb = 0; kb < p.k_blocks; ++kb) {
+        if (!wait_bounded(full_bar(s), ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t a_addr = smem_u32(stages + s * kStageBytes16);
+          const uint32_t b_addr = a_addr + kABytes16;
+#pragma unroll
+          for (int k = 0; k < kBK16 / 16; ++k) {
+            mma_f16(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
+                    p.idesc, (kb | k) != 0 ? 1u : 0u);
+          }
+          mma_commit(empty_bar(s));
+        }
+        __syncwarp();
+        if (++s == kStages16) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(tfull_bar(acc));
+      __syncwarp();
+      acc ^= 1u;
+      if (acc == 0) acc_ph ^= 1u;
+    }
+    if (!ok && lane == 0) {
+      // wait for the MMAs already issued before tensor memory is released
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+    __syncwarp();
+  } else {
+    const int ew = warp & 3;
+    uint32_t* stg = epi_stg + ew * (kEpiWarpBytes / 4);
+    uint32_t acc = 0, acc_ph = 0;
+    unsigned amax_bits = 0;
+    float lam = 0.f;
+    if (EPI == EPI_FINAL) lam = static_cast<float>(p.ep.st->lambda);
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+      const int2 tc = p.tiles[t];
+      if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
+      tc_fence_after();
+      const int r0 = tc.x + 32 * ew;
+#pragma unroll 1
+      for (int ch = 0; ch < kBN / 32; ++ch) {
+        const int c0 = tc.y + 32 * ch;
+        if (r0 > c0 || r0 >= p.n || c0 >= p.n) continue;  // warp-uniform
+        uint32_t v[32];
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
+        if (EPI == EPI_FINAL)
+          epilogue_chunk_final(p, r0, c0, v, stg, lane, lam);
+        else
+          epilogue_chunk16<EPI>(p, bf16, r0, c0, v, stg, lane, amax_bits);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      acc ^= 1u;
+      if (acc == 0) acc_ph ^= 1u;
+    }
+    if (EPI != EPI_FINAL && p.ep.absmax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
+      if (lane == 0 && amax_bits) atomicMax(p.ep.absmax, amax_bits);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag) raise_status(p.ep.status, PSD_ERR_TIMEOUT);
+}
+
+using Kernel16 = void (*)(const CUtensorMap, const CUtensorMap, const GemmParams, const int);
+
+Kernel16 kernel16_for(int epi) {
+  switch (epi) {
+    case EPI_COPY: return symgemm16_kernel<EPI_COPY>;
+    case EPI_POLY: return symgemm16_kernel<EPI_POLY>;
+    case EPI_SCALE: return symgemm16_kernel<EPI_SCALE>;
+    default: return symgemm16_kernel<EPI_FINAL>;
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(ptr);
+  }
+  return fn;
+}
+
+}  // namespace
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// Tensor map of an n x n symmetric operand with row stride ld elements.  The
+// box is 128 bytes of K (one swizzle row) by box_rows rows; boxes that reach
+// past n are zero-filled by the TMA unit.
+bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows) {
+  EncodeFn fn = get_encode();
+  if (!fn) return false;
+  const int esz = dtype == DT_TF32X3 ? 4 : 2;
+  const CUtensorMapDataType dt = dtype == DT_F16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : dtype == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Upper-triangle tiles of 256 x 256 blocks, each split into two 128-row
+// tiles, in a grouped raster: block rows are taken in groups of 8, and inside
+// a group the columns advance first so that the tiles resident at one time
+// share their operand panels in L2.
+std::vector<int2> make_tile_list(int64_t n) {
+  std::vector<int2> tiles;
+  const int nb = static_cast<int>((n + kBN - 1) / kBN);
+  const int G = 8;
+  for (int g0 = 0; g0 < nb; g0 += G) {
+    for (int J = g0; J < nb; ++J) {
+      const int iend = std::min(g0 + G, J + 1);
+      for (int I = g0; I < iend; ++I) {
+        for (int h = 0; h < 2; ++h) {
+          const int m0 = I * kBN + h * kBM;
+          if (m0 >= n) continue;
+          tiles.push_back(make_int2(m0, J * kBN));
+        }
+      }
+    }
+  }
+  return tiles;
+}
+
+cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                           const GemmParams& p, int grid, cudaStream_t stream) {
+  if (p.num_tiles == 0) return cudaSuccess;
+  if (dtype == DT_TF32X3) return cudaErrorNotSupported;
+  Kernel16 k = kernel16_for(epi);
+  static bool attr_set[4] = {false, false, false, false};
+  const int smem = smem_bytes16();
+  if (!attr_set[epi]) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set[epi] = true;
+  }
+  const int g = std::max(1, std::min(grid, p.num_tiles));
+  k<<<g, kThreads, smem, stream>>>(tmA, tmB, p, dtype == DT_BF16 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace psd

@@ -1,0 +1,155 @@
+"""GPU tests of the tensor-core symmetric product (the building block of every
+stage of Algorithm 2), called through the C ABI.
+
+Expected values are FP64 products of the same 16-bit operands computed on the
+CPU with numpy; the kernel accumulates in FP32 and rounds the result once to
+16 bits (or writes FP32 for the final epilogue).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2507_09165_gb300 import binding as b  # noqa: E402
+
+SIZES = [16, 100, 128, 255, 256, 300, 513, 1000]
+DT = {"fp16": torch.float16, "bf16": torch.bfloat16}
+EPS = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+def sym16(n, ld, seed, prec, scale=1.0):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n)) * (scale / np.sqrt(n))
+    A = 0.5 * (G + G.T)
+    t = torch.zeros((n, ld), dtype=DT[prec])
+    t[:, :n] = torch.from_numpy(A).to(DT[prec])
+    return t
+
+
+def as64(t, n):
+    return t[:, :n].double().numpy()
+
+
+def check_upper(C, D, n, prec, absA, absB):
+    # |C - D| <= one rounding of D plus the FP32 accumulation error bound
+    acc = n * 2.0 ** -23 * (absA @ absB)
+    tol = EPS[prec] * np.abs(D) + 2 * acc + 1e-30
+    err = np.abs(C - D)
+    iu = np.triu_indices(n)
+    bad = err[iu] > tol[iu]
+    assert not np.any(bad), (np.max(err[iu] / tol[iu]), int(np.sum(bad)))
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("n", SIZES)
+def test_product_copy(n, prec):
+    ld = (n + 7) // 8 * 8
+    A = sym16(n, ld, 1 + n, prec)
+    B = sym16(n, ld, 2 + n, prec)
+    dev = torch.device("cuda")
+    Ad, Bd = A.to(dev), B.to(dev)
+    Cd = torch.full((n, ld), float("nan"), dtype=DT[prec], device=dev)
+    b.psd_symm_product(n, Ad, Bd, ld, Cd, 0, prec, 0)
+    torch.cuda.synchronize()
+    C = as64(Cd.cpu(), n)
+    A64, B64 = as64(A, n), as64(B, n)
+    D = A64 @ B64.T
+    assert np.all(np.isfinite(C))
+    assert np.array_equal(C, C.T)  # exactly symmetric
+    check_upper(C, D, n, prec, np.abs(A64), np.abs(B64))
+    # the padding columns are never written
+    if ld > n:
+        assert torch.isnan(Cd[:, n:].float()).all()
+
+
+@pytest.mark.parametrize("n", [64, 300, 700])
+def test_product_poly_scale_and_absmax(n):
+    prec = "fp16"
+    ld = (n + 7) // 8 * 8
+    dev = torch.device("cuda")
+    Y = sym16(n, ld, 10 + n, prec)
+    Yd = Y.to(dev)
+    P = torch.zeros((n, ld), dtype=torch.float16, device=dev)
+    a, bb, c = 2.7632556383, -2.0607754898, 0.4695405857
+    amax = torch.zeros(1, dtype=torch.float32, device=dev)
+    b.psd_symm_product(n, Yd, Yd, ld, P, 0, prec, 1, (a, bb, c), Yd, ld, amax)
+    S = torch.zeros((n, ld), dtype=torch.float16, device=dev)
+    b.psd_symm_product(n, Yd, Yd, ld, S, 0, prec, 2, (1 / 1.01,))
+    torch.cuda.synchronize()
+    Y64 = as64(Y, n)
+    D = Y64 @ Y64
+    # FP32 epilogue arithmetic on the FP32 accumulator, one rounding to fp16
+    Dp = a * np.eye(n) + bb * Y64 + c * D
+    Pc = as64(P.cpu(), n)
+    assert np.array_equal(Pc, Pc.T)
+    absY = np.abs(Y64)
+    acc = n * 2.0 ** -23 * (absY @ absY)
+    tol = EPS[prec] * np.abs(Dp) + 2 * abs(c) * acc + 1e-6 * (abs(a) + abs(bb) * absY)
+    assert np.all(np.abs(Pc - Dp) <= tol)
+    assert float(amax.item()) == float(np.max(np.abs(Pc)))
+    Sc = as64(S.cpu(), n)
+    Ds = D / 1.01
+    assert np.all(np.abs(Sc - Ds) <= EPS[prec] * np.abs(Ds) + 2 * acc)
+
+
+@pytest.mark.parametrize("n", [33, 256, 517])
+def test_product_final_reads_upper_triangle_only(n):
+    # out = (Xf + lam A B) / 2 in FP32; Xf's other triangle holds NaN and must
+    # never be read.  In a row-major tensor the library's (column-major) upper
+    # triangle X[i + j ld], i <= j, is T[j][i]: the row >= col part.
+    prec = "fp16"
+    ld = (n + 7) // 8 * 8
+    dev = torch.device("cuda")
+    A = sym16(n, ld, 20 + n, prec)
+    B = sym16(n, ld, 21 + n, prec)
+    rng = np.random.default_rng(n)
+    Xs = rng.standard_normal((n, n)).astype(np.float32)
+    Xs = np.tril(Xs) + np.tril(Xs, -1).T
+    Xpoison = Xs.copy()
+    Xpoison[np.triu_indices(n, 1)] = np.nan
+    ldx = n + 3
+    Xt = torch.zeros((n, ldx), dtype=torch.float32)
+    Xt[:, :n] = torch.from_numpy(Xpoison)
+    ldo = n + 5
+    out = torch.full((n, ldo), -7.0, dtype=torch.float32, device=dev)
+    lam = 3.25
+    b.psd_symm_product(n, A.to(dev), B.to(dev), ld, out, ldo, prec, 3, (lam,), Xt.to(dev), ldx)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().astype(np.float64)
+    assert np.all(o[:, n:] == -7.0)
+    o = o[:, :n]
+    assert np.all(np.isfinite(o))
+    assert np.array_equal(o, o.T)
+    A64, B64 = as64(A, n), as64(B, n)
+    D = 0.5 * (Xs.astype(np.float64) + lam * (A64 @ B64.T))
+    acc = n * 2.0 ** -23 * (np.abs(A64) @ np.abs(B64))
+    tol = 2.0 ** -22 * (np.abs(D) + np.abs(Xs)) + lam * acc
+    iu = np.triu_indices(n)
+    assert np.all(np.abs(o - D)[iu] <= tol[iu] + 1e-6)
+
+
+def test_product_is_deterministic():
+    n, prec = 777, "bf16"
+    ld = 784
+    dev = torch.device("cuda")
+    A = sym16(n, ld, 5, prec).to(dev)
+    outs = []
+    for _ in range(3):
+        C = torch.zeros((n, ld), dtype=DT[prec], device=dev)
+        b.psd_symm_product(n, A, A, ld, C, 0, prec, 0)
+        outs.append(C)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+
+
+def test_product_rejects_bad_arguments():
+    dev = torch.device("cuda")
+    A = torch.zeros((8, 8), dtype=torch.float16, device=dev)
+    with pytest.raises(b.PsdError):
+        b.psd_symm_product(8, A, A, 7, A, 0, "fp16", 0)  # ld not a multiple of 8
+    with pytest.raises(b.PsdError):
+        b.psd_symm_product(8, A, A, 8, A, 0, "fp32", 0)  # 16-bit only
+    with pytest.raises(b.PsdError):
+        b.psd_symm_product(8, A, A, 8, A, 0, "fp16", 9)  # unknown epilogue
