@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the composite-polynomial PSD-cone projection on GB300.
+
+Workload: one dense symmetric n x n FP32 Wigner matrix (G + G^T) / (2 sqrt n),
+n = 10,000, seed 2 (synthetic stand-in for the paper's n = 10,000 Matrix Depot
+matrices).  A step is one full projection through the C ABI (norm bound,
+cast, 3T + 1 tensor-core products, output), inputs resident in HBM.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU FP64 oracle
+instead (the reference arm of this repository: a plain Jacobi projection on
+the host cores, on a bounded sample scaled by n^3 to the same unit).
+Multi-GPU: replicas only (a single projection does not shard); under torchrun
+each rank projects its own matrix, timing is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per n=10k PSD projection at rel err ≤1e-3 vs FP32 path; tensor-pipe %"
+DTYPE = {"fp16": "f16", "bf16": "bf16", "fp32": "f32 (tf32x3)", "mixed": "f16+bf16x3"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--precision", default="fp16")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the full-size accuracy check")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+
+    def summary(self):
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def cpu_baseline(n_target, sample_n=1024, seed=2):
+    """The CPU FP64 oracle (Jacobi projection + filter output) on a bounded sample,
+    scaled by n^3 to one n_target projection."""
+    import numpy as np
+    import oracle
+    from paper_2507_09165_gb300 import synth
+    X = synth.wigner(sample_n, seed).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.oracle_project(X, "half")
+    dt = time.perf_counter() - t0
+    scale = (n_target / sample_n) ** 3
+    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "one oracle projection (20-step FP64 Lanczos bound, cyclic Jacobi eigen-decomposition, "
+                      "Pi and F) of a Wigner n=%d matrix, %.2f s, scaled by (n/%d)^3 to n=%d"
+                      % (sample_n, dt, sample_n, n_target),
+            "sample_seconds": dt}
+
+
+def accuracy_check(n, prec, dev, seed=20):
+    """Full-size parity: Q diag(l) Q^T with Haar Q and semicircle l (the eigenvector and
+    eigenvalue laws of the timed Wigner matrix), where Pi and F are known exactly."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle import schedules as S
+    from paper_2507_09165_gb300 import binding as b
+    from paper_2507_09165_gb300 import synth
+    t0 = time.perf_counter()
+    X32, Q, lam = synth.spectral_matrix("semicircle", n, seed)
+    Xd = torch.from_numpy(X32).to(dev)
+    out = torch.empty_like(Xd)
+    info = torch.zeros(b.INFO_BYTES, dtype=torch.uint8, device=dev)
+    b.psd_project_ex(n, Xd, n, out, n, prec, info)
+    torch.cuda.synchronize(dev)
+    inf = b.info_from_bytes(info.cpu().numpy())
+    o = out.cpu().numpy().astype(np.float64)
+    del Xd, out
+    coefs, scales = S.schedule("single" if prec == "fp32" else "half")
+    F = oracle.filter_from_eig(lam, Q, inf["lambda_bound"], coefs, scales)
+    rel_f = oracle.rel_err(o, F)
+    del F
+    P = oracle.project_from_eig(lam, Q)
+    rel_pi = oracle.rel_err(o, P)
+    return {"matrix": "Q diag(l) Q^T, Haar Q, l iid semicircle on [-sqrt2, sqrt2], n=%d, seed %d" % (n, seed),
+            "rel_err_F": rel_f, "rel_err_Pi": rel_pi, "status": inf["status"],
+            "lambda_bound": inf["lambda_bound"], "lambda_true": float(np.max(np.abs(lam))),
+            "seconds": time.perf_counter() - t0}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    sample_n = 640
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(args.n, sample_n=sample_n, seed=2 + i)
+        if i >= args.warmup:
+            times.append(r["value"])
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "wigner n=%d (oracle on a Wigner n=%d sample per step, scaled by n^3)"
+                                   % (args.n, sample_n)},
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"], "value": v,
+                             "unit": "ms"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_info()
+    from paper_2507_09165_gb300 import _build
+    from paper_2507_09165_gb300 import binding as b
+    from paper_2507_09165_gb300 import synth
+    _build.build()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    n, prec = args.n, args.precision
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    X = synth.wigner(n, 2 + rank)
+    Xh = torch.from_numpy(X).pin_memory()
+    Xd = Xh.to(dev)
+    out = torch.empty_like(Xd)
+    s = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        b.psd_project(n, Xd, n, out, prec, s)
+    info = b.psd_last_info(s)
+    if info["status"] != 0:
+        raise SystemExit("projection reported status %d" % info["status"])
+    launches = b.psd_kernel_launches(n, prec, s)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(dev.index) as clk:
+        ev0.record(s)
+        for _ in range(args.steps):
+            b.psd_project(n, Xd, n, out, prec, s)
+        ev1.record(s)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    clocks = clk.summary()
+
+    # end to end through the public call: pinned host X -> device, project, result -> pinned host
+    out_h = torch.empty_like(Xh).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    barrier()
+    ev0.record(s)
+    for _ in range(e2e_steps):
+        Xd.copy_(Xh, non_blocking=True)
+        b.psd_project(n, Xd, n, out, prec, s)
+        out_h.copy_(out, non_blocking=True)
+    ev1.record(s)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = ev0.elapsed_time(ev1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # dominant kernel: the symmetric tensor-core product, same kernel and shape as in the chain
+    ld = (n + 63) // 64 * 64
+    g16 = torch.float16 if prec != "bf16" else torch.bfloat16
+    A = (torch.randn(n, ld, device=dev) / math.sqrt(n)).to(g16)
+    C = torch.empty_like(A)
+    gprec = "bf16" if prec == "bf16" else "fp16"
+    for _ in range(3):
+        b.psd_symm_product(n, A, A, ld, C, 0, gprec, 0, stream=s)
+    reps = 20
+    ev0.record(s)
+    for _ in range(reps):
+        b.psd_symm_product(n, A, A, ld, C, 0, gprec, 0, stream=s)
+    ev1.record(s)
+    torch.cuda.synchronize(dev)
+    gemm_ms = ev0.elapsed_time(ev1) / reps
+    del A, C
+    peaks, peak_src = measured_peaks()
+    alg_flops = n ** 3 * (1 + 256 / n)  # symmetric product, 256-wide tiles: n^3 (1 + b/n)
+    achieved = alg_flops / (gemm_ms * 1e-3) / 1e12
+    peak = peaks["bf16_tflops"]
+
+    acc = None
+    if rank == 0 and not args.no_accuracy:
+        acc = accuracy_check(n, prec, dev)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n)
+
+    if rank == 0:
+        value = ms_step / world  # replicas: world projections per step
+        line = {
+            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE.get(prec, prec), "data": "synthetic",
+            "config": {"workload": "wigner n=%d (G+G^T)/(2 sqrt n), seed 2, FP32 input" % n,
+                       "precision": prec, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: 400 MB FP32 input + %d MB workspace per step"
+                             % (b.psd_workspace_size(n, prec) // 2 ** 20)},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "symgemm16 (one symmetric product, %s, timed alone: %.4f ms)" % (gprec, gemm_ms),
+                         "peak_source": "%s bf16 burst (MEASURED_PEAKS.json)" % peak_src,
+                         "algorithmic_flops_per_launch": alg_flops},
+            "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": n * n * 4,
+                    "d2h_bytes_per_step": n * n * 4},
+            "gpu_launches": launches * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "accuracy": acc,
+            "info": {k: info[k] for k in ("lambda_bound", "lanczos_steps", "overshoot_max")},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

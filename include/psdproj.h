@@ -160,6 +160,9 @@ const char *psd_status_string(psd_status_t status);
  * = (a_t, b_t, c_t), post_scale[t] = s_t.  Arrays must hold >= 10 entries
  * (coef >= 30).  Returns PSD_ERR_INVALID_ARG for an unknown precision. */
 psd_status_t psd_schedule(psd_precision_t precision, int32_t *T, double *coef, double *post_scale);
+/* Kernel launches one psd_project call on `stream` makes for (n, precision),
+ * counted from its captured graph (0 before the first such call). */
+int32_t psd_kernel_launches(int64_t n, psd_precision_t precision, psd_stream_t stream);
 /* Number of tensor-core product launches one projection makes (3T + 1). */
 int32_t psd_gemm_count(psd_precision_t precision);
 /* Library version string. */

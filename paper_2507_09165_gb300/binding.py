@@ -59,6 +59,7 @@ _SIGS = {
     "psd_status_string": ([_I32], ctypes.c_char_p),
     "psd_schedule": ([_I32, ctypes.POINTER(_I32), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I32),
     "psd_gemm_count": ([_I32], _I32),
+    "psd_kernel_launches": ([_I64, _I32, _VP], _I32),
     "psd_version": ([], ctypes.c_char_p),
 }
 
@@ -167,6 +168,10 @@ def psd_schedule(precision):
 
 def psd_gemm_count(precision):
     return int(lib().psd_gemm_count(_prec(precision)))
+
+
+def psd_kernel_launches(n, precision="fp16", stream=None):
+    return int(lib().psd_kernel_launches(n, _prec(precision), _stream(stream)))
 
 
 def psd_version():

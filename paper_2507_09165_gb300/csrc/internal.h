@@ -51,8 +51,9 @@ struct DevState {
 // Epilogue kinds of the symmetric product (fused into the tensor-core kernel).
 enum Epi : int { EPI_COPY = 0, EPI_POLY = 1, EPI_SCALE = 2, EPI_FINAL = 3 };
 
-// Operand storage of the chain.
-enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2 };
+// Operand storage of the chain: single 16-bit matrices, TF32 hi/lo pairs
+// (FP32 containers), BF16 hi/lo pairs.
+enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_BF16X3 = 3 };
 
 struct EpiParams {
   void* C;               // 16-bit output (ld = ldc) for EPI_COPY/POLY/SCALE
@@ -82,6 +83,10 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
 std::vector<int2> make_tile_list(int64_t n);
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const GemmParams& p, int grid, cudaStream_t stream);
+// split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
+// out: 0 = split pair, 1 = single FP16, (EPI_FINAL) FP32 to the caller's output.
+cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm, const GemmParams& p, int grid,
+                              cudaStream_t stream);
 int num_sms();
 
 // --- norm bound and cast (normbound.cu) ---
@@ -107,8 +112,10 @@ size_t lanczos_bytes(int64_t n);
 void lanczos_carve(LanczosBufs& b, int64_t n, uint8_t* base);
 cudaError_t enqueue_norm_bound(const LanczosBufs& b, const DevArgs* args, DevState* st,
                                cudaStream_t stream);
+// X_0 = X / lam~ as `dtype` (pairs: M = hi, M_lo = lo); M_f16 (may be null): an
+// additional FP16 copy (DT_BF16X3 only).
 cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n,
-                               void* M, void* M_lo, int64_t ldm, cudaStream_t stream);
+                               void* M, void* M_lo, void* M_f16, int64_t ldm, cudaStream_t stream);
 cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t stream);
 cudaError_t enqueue_state_reset(DevState* st, cudaStream_t stream);
 cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t stream);

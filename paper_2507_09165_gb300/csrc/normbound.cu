@@ -150,18 +150,20 @@ __global__ void lanczos_norm0_kernel(int n, double* Qv, float* vh, float* vl, co
   }
 }
 
-// One tile of y = X v over the upper triangle (see file comment).  STATS adds
-// the tile's share of ||X||_F^2 and max |X_ii| (first product only).
+// One tile of y = X v over the upper triangle (see file comment).  Thread
+// (tr, tc) = (lane & 15, 2 warp + lane / 16) owns rows i0 + 8 tr .. +7 and
+// columns j0 + 8 tc .. +7: each column's 128 rows are read by a half-warp as
+// 512 contiguous bytes.  STATS adds the tile's share of ||X||_F^2 and
+// max |X_ii| (first product only).
 template <bool STATS>
-__global__ void __launch_bounds__(256) symv_upper_kernel(const DevArgs* __restrict__ args, int n,
+__global__ void __launch_bounds__(256, 3) symv_upper_kernel(const DevArgs* __restrict__ args, int n,
                                                          const float* __restrict__ vh,
                                                          const float* __restrict__ vl,
                                                          float2* __restrict__ P1, float2* __restrict__ P2,
                                                          int64_t ps, double* __restrict__ tile_fro,
                                                          DevState* __restrict__ st, int skip_if_done) {
   if (skip_if_done && st->done) return;
-  __shared__ float red_h[8][kSymvTile];
-  __shared__ float red_l[8][kSymvTile];
+  __shared__ float2 red[8][kSymvTile];
   __shared__ double fro_sh[8];
   const float* __restrict__ X = args->X;
   const int64_t ld = args->ld;
@@ -169,44 +171,42 @@ __global__ void __launch_bounds__(256) symv_upper_kernel(const DevArgs* __restri
   tile_of(blockIdx.x, bi, bj);
   const int i0 = bi * kSymvTile, j0 = bj * kSymvTile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ib = i0 + 4 * lane;
-  const int jb = j0 + 16 * warp;
+  const int tr = lane & 15, tcol = 2 * warp + (lane >> 4);
+  const int ib = i0 + 8 * tr;
+  const int jb = j0 + 8 * tcol;
   const bool diag = bi == bj;
 
-  float vih[4], vil[4];
+  float vih[8], vil[8];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 8; ++k) {
     const int i = ib + k;
     vih[k] = i < n ? vh[i] : 0.f;
     vil[k] = i < n ? vl[i] : 0.f;
   }
-  F2 rs[4];
+  F2 rs[8], cs[8];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) rs[k] = F2{0.f, 0.f};
-  F2 cs[16];
+  for (int k = 0; k < 8; ++k) rs[k] = cs[k] = F2{0.f, 0.f};
   F2 fro{0.f, 0.f};
   unsigned mdiag = 0;
-  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ib + 3 < n);
+  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ib + 7 < n);
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    cs[c] = F2{0.f, 0.f};
+  for (int c = 0; c < 8; ++c) {
     const int j = jb + c;
     if (j >= n) continue;
-    const float* col = X + static_cast<int64_t>(j) * ld;
-    float x[4];
+    const float* col = X + static_cast<int64_t>(j) * ld + ib;
+    float x[8];
     if (vec) {
-      const float4 q4 = __ldg(reinterpret_cast<const float4*>(col + ib));
-      x[0] = q4.x;
-      x[1] = q4.y;
-      x[2] = q4.z;
-      x[3] = q4.w;
+      const float4 a4 = __ldg(reinterpret_cast<const float4*>(col));
+      const float4 b4 = __ldg(reinterpret_cast<const float4*>(col + 4));
+      x[0] = a4.x; x[1] = a4.y; x[2] = a4.z; x[3] = a4.w;
+      x[4] = b4.x; x[5] = b4.y; x[6] = b4.z; x[7] = b4.w;
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) x[k] = (ib + k < n) ? __ldg(col + ib + k) : 0.f;
+      for (int k = 0; k < 8; ++k) x[k] = (ib + k < n) ? __ldg(col + k) : 0.f;
     }
     const float vjh = vh[j], vjl = vl[j];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 8; ++k) {
       const int i = ib + k;
       const bool up = (!diag || i <= j) && i < n;
       const bool strict = (!diag || i < j) && i < n;
@@ -219,16 +219,20 @@ __global__ void __launch_bounds__(256) symv_upper_kernel(const DevArgs* __restri
       }
     }
   }
-  // rows: reduce over the 8 warps through shared memory
+  // rows: the two column groups of a warp, then the 8 warps through shared memory
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    red_h[warp][4 * lane + k] = rs[k].h;
-    red_l[warp][4 * lane + k] = rs[k].l;
+  for (int k = 0; k < 8; ++k) {
+    const F2 o = shfl_xor_f2(rs[k], 16);
+    rs[k] = (lane < 16) ? f2_add(rs[k], o) : f2_add(o, rs[k]);
   }
-  // columns: recursive halving over the 32 lanes; lanes 2c, 2c+1 end with column c
+  if (lane < 16) {
 #pragma unroll
-  for (int half = 8, m = 16; half >= 1; half >>= 1, m >>= 1) {
-    const bool upper = (lane & m) != 0;
+    for (int k = 0; k < 8; ++k) red[warp][8 * tr + k] = make_float2(rs[k].h, rs[k].l);
+  }
+  // columns: recursive halving over the 16 row groups of a half-warp
+#pragma unroll
+  for (int half = 4, m = 8; half >= 1; half >>= 1, m >>= 1) {
+    const bool upper = (tr & m) != 0;
 #pragma unroll
     for (int i = 0; i < half; ++i) {
       const F2 send = upper ? cs[i] : cs[i + half];
@@ -236,17 +240,18 @@ __global__ void __launch_bounds__(256) symv_upper_kernel(const DevArgs* __restri
       cs[i] = f2_add(keep, shfl_xor_f2(send, m));
     }
   }
-  cs[0] = f2_add(cs[0], shfl_xor_f2(cs[0], 1));
   {
-    const int j = jb + (lane >> 1);
-    if ((lane & 1) == 0 && j < n) P2[static_cast<int64_t>(bi) * ps + j] = make_float2(cs[0].h, cs[0].l);
+    const F2 o = shfl_xor_f2(cs[0], 1);
+    cs[0] = (tr & 1) ? f2_add(o, cs[0]) : f2_add(cs[0], o);
+    const int j = jb + (tr >> 1);
+    if ((tr & 1) == 0 && j < n) P2[static_cast<int64_t>(bi) * ps + j] = make_float2(cs[0].h, cs[0].l);
   }
   __syncthreads();
   if (threadIdx.x < kSymvTile) {
     const int r = threadIdx.x;
-    F2 a{red_h[0][r], red_l[0][r]};
+    F2 a{red[0][r].x, red[0][r].y};
 #pragma unroll
-    for (int w = 1; w < 8; ++w) a = f2_add(a, F2{red_h[w][r], red_l[w][r]});
+    for (int w = 1; w < 8; ++w) a = f2_add(a, F2{red[w][r].x, red[w][r].y});
     if (i0 + r < n) P1[static_cast<int64_t>(bj) * ps + i0 + r] = make_float2(a.h, a.l);
   }
   if (STATS) {
@@ -259,9 +264,9 @@ __global__ void __launch_bounds__(256) symv_upper_kernel(const DevArgs* __restri
     if (lane == 0 && mdiag) atomicMax(&st->maxdiag_bits, mdiag);
     __syncthreads();
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < 8; ++w) s += fro_sh[w];
-      tile_fro[blockIdx.x] = s;
+      double sum = 0.0;
+      for (int w = 0; w < 8; ++w) sum += fro_sh[w];
+      tile_fro[blockIdx.x] = sum;
     }
   }
 }
@@ -275,20 +280,43 @@ __global__ void fro_kernel(const double* tile_fro, int ntiles, DevState* st) {
   if (threadIdx.x == 0) st->fro = sqrt(f);
 }
 
-// y_e = sum_{bj >= b(e)} P1[bj][e] + sum_{bi <= b(e)} P2[bi][e] in double-float, then FP64.
-__device__ __forceinline__ double reduce_partials(int e, int nb, const float2* P1, const float2* P2,
-                                                  int64_t ps) {
+// y_e = sum_{bj >= b(e)} P1[bj][e] + sum_{bi <= b(e)} P2[bi][e] in double-float,
+// four interleaved accumulators (loads in flight), combined in a fixed order.
+__device__ __forceinline__ double reduce_partials(int e, int nb, const float2* __restrict__ P1,
+                                                  const float2* __restrict__ P2, int64_t ps) {
   const int b = e / kSymvTile;
-  F2 a{0.f, 0.f};
-  for (int bj = b; bj < nb; ++bj) {
-    const float2 t = P1[static_cast<int64_t>(bj) * ps + e];
-    a = f2_add(a, F2{t.x, t.y});
+  F2 a[4] = {F2{0.f, 0.f}, F2{0.f, 0.f}, F2{0.f, 0.f}, F2{0.f, 0.f}};
+  int q = 0;
+  auto take = [&](const float2* P, int blk) {
+    const float2 t = __ldg(P + static_cast<int64_t>(blk) * ps + e);
+    a[q & 3] = f2_add(a[q & 3], F2{t.x, t.y});
+    ++q;
+  };
+  int bj = b;
+  for (; bj + 3 < nb; bj += 4) {
+    const float2 t0 = __ldg(P1 + static_cast<int64_t>(bj) * ps + e);
+    const float2 t1 = __ldg(P1 + static_cast<int64_t>(bj + 1) * ps + e);
+    const float2 t2 = __ldg(P1 + static_cast<int64_t>(bj + 2) * ps + e);
+    const float2 t3 = __ldg(P1 + static_cast<int64_t>(bj + 3) * ps + e);
+    a[0] = f2_add(a[0], F2{t0.x, t0.y});
+    a[1] = f2_add(a[1], F2{t1.x, t1.y});
+    a[2] = f2_add(a[2], F2{t2.x, t2.y});
+    a[3] = f2_add(a[3], F2{t3.x, t3.y});
   }
-  for (int bi = 0; bi <= b; ++bi) {
-    const float2 t = P2[static_cast<int64_t>(bi) * ps + e];
-    a = f2_add(a, F2{t.x, t.y});
+  for (; bj < nb; ++bj) take(P1, bj);
+  int bi = 0;
+  for (; bi + 3 <= b; bi += 4) {
+    const float2 t0 = __ldg(P2 + static_cast<int64_t>(bi) * ps + e);
+    const float2 t1 = __ldg(P2 + static_cast<int64_t>(bi + 1) * ps + e);
+    const float2 t2 = __ldg(P2 + static_cast<int64_t>(bi + 2) * ps + e);
+    const float2 t3 = __ldg(P2 + static_cast<int64_t>(bi + 3) * ps + e);
+    a[0] = f2_add(a[0], F2{t0.x, t0.y});
+    a[1] = f2_add(a[1], F2{t1.x, t1.y});
+    a[2] = f2_add(a[2], F2{t2.x, t2.y});
+    a[3] = f2_add(a[3], F2{t3.x, t3.y});
   }
-  return f2_to_d(a);
+  for (; bi <= b; ++bi) take(P2, bi);
+  return f2_to_d(f2_add(f2_add(a[0], a[1]), f2_add(a[2], a[3])));
 }
 
 // u = X v (first product of X (X v)); split u for the second product.
@@ -355,13 +383,13 @@ __global__ void orth_kernel(int n, double* w, const double* Qv, int64_t npad, in
   if (st->done) return;
   __shared__ double h[32];
   __shared__ double sh[kVecThreads / 32][32];
-  if (threadIdx.x < 32) {
-    double t = 0.0;
-    if (static_cast<int>(threadIdx.x) <= j)
-      for (int c = 0; c < nctas; ++c) t += dots_in[c * 32 + threadIdx.x];
-    h[threadIdx.x] = t;
+  // h_k = sum over CTAs of the partial dots; warp w reduces k = w, w + nwarps, ...
+  // (every CTA sums the same partials in the same order)
+  for (int k = threadIdx.x >> 5; k <= j; k += kVecThreads / 32) {
+    const double t = warp_sum_array(dots_in + k, nctas, 32);
+    if ((threadIdx.x & 31) == 0) h[k] = t;
   }
-  __syncthreads();  // h_k: every CTA sums the same partials in the same order
+  __syncthreads();
   if (PASS == 1 && blockIdx.x == 0 && threadIdx.x == 0) st->alpha[j] = h[j];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -425,15 +453,24 @@ __global__ void lanczos_next_kernel(int n, const double* w, double* Qv, int64_t 
   }
 }
 
-// Sturm count: number of eigenvalues of T (m x m, diag a, off-diag b) below x.
+// Sturm count: number of eigenvalues of T (m x m, diag a, off-diag b) below x,
+// = sign changes of the leading principal minors p_k = det(T_k - x I),
+// p_k = (a_k - x) p_{k-1} - b_{k-1}^2 p_{k-2} (no divisions; T is scaled to
+// unit size beforehand so the minors stay in range).
 __device__ int sturm_count(const double* a, const double* b, int m, double x) {
-  int cnt = 0;
-  double d = a[0] - x;
-  if (d < 0.0) ++cnt;
+  double pm = 1.0, p = a[0] - x;
+  int cnt = (p < 0.0) ? 1 : 0;
   for (int k = 1; k < m; ++k) {
-    if (d == 0.0) d = -1e-300;
-    d = (a[k] - x) - b[k - 1] * b[k - 1] / d;
-    if (d < 0.0) ++cnt;
+    const double pn = (a[k] - x) * p - b[k - 1] * b[k - 1] * pm;
+    const bool change = (pn == 0.0) ? (p > 0.0) : ((pn < 0.0) != (p < 0.0));
+    if (p != 0.0 || pn != 0.0) cnt += change ? 1 : 0;
+    pm = p;
+    p = pn;
+    const double mag = fabs(p) + fabs(pm);
+    if (mag > 1e150) {
+      p *= 1e-150;
+      pm *= 1e-150;
+    }
   }
   return cnt;
 }
@@ -442,12 +479,19 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x) {
 // count (32 points per round), then inverse iteration with partial pivoting.
 __global__ void tridiag_kernel(DevState* st) {
   __shared__ double a[kMaxSteps], b[kMaxSteps];
-  __shared__ double lo_s, hi_s;
+  __shared__ double lo_s, hi_s, scale_s;
   const int lane = threadIdx.x;
   const int m = st->m;
+  if (lane == 0) {
+    double sc = 0.0;
+    for (int k = 0; k < m; ++k) sc = fmax(sc, fabs(st->alpha[k]) + (k < m - 1 ? fabs(st->beta[k]) : 0.0));
+    scale_s = sc > 0.0 ? sc : 1.0;
+  }
+  __syncwarp();
+  const double inv_sc = 1.0 / scale_s;
   if (lane < m) {
-    a[lane] = st->alpha[lane];
-    b[lane] = lane < m - 1 ? st->beta[lane] : 0.0;
+    a[lane] = st->alpha[lane] * inv_sc;
+    b[lane] = lane < m - 1 ? st->beta[lane] * inv_sc : 0.0;
   }
   __syncwarp();
   if (lane == 0) {
@@ -461,7 +505,7 @@ __global__ void tridiag_kernel(DevState* st) {
     hi_s = hi;
   }
   __syncwarp();
-  for (int round = 0; round < 40; ++round) {
+  for (int round = 0; round < 24; ++round) {
     const double lo = lo_s, hi = hi_s;
     if (!(hi - lo > 4.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi)))) break;
     const double x = lo + (hi - lo) * (lane + 1) / 33.0;
@@ -480,29 +524,27 @@ __global__ void tridiag_kernel(DevState* st) {
   if (lane != 0) return;
   const double sigma = 0.5 * (lo_s + hi_s);
   // inverse iteration on (T - sigma I): Gaussian elimination with partial
-  // pivoting on the tridiagonal (rows may swap, which creates a second
-  // super-diagonal).
-  double tnorm = 0.0;
-  for (int k = 0; k < m; ++k) tnorm = fmax(tnorm, fabs(a[k]) + (k ? fabs(b[k - 1]) : 0.0) + fabs(b[k]));
-  const double tiny = fmax(tnorm, 1e-300) * 1e-15;
-  double d[kMaxSteps], du[kMaxSteps], du2[kMaxSteps], dl[kMaxSteps], l[kMaxSteps];
-  int piv[kMaxSteps];
+  // pivoting on the tridiagonal (a row swap creates a second super-diagonal);
+  // the pivots' reciprocals are formed once.
+  const double tiny = 1e-15;
+  double d[kMaxSteps], du[kMaxSteps], du2[kMaxSteps], l[kMaxSteps], rd[kMaxSteps];
+  bool piv[kMaxSteps];
   for (int k = 0; k < m; ++k) {
     d[k] = a[k] - sigma;
     du[k] = k < m - 1 ? b[k] : 0.0;
-    dl[k] = k < m - 1 ? b[k] : 0.0;
     du2[k] = 0.0;
-    piv[k] = 0;
+    piv[k] = false;
   }
   for (int k = 0; k < m - 1; ++k) {
-    if (fabs(d[k]) >= fabs(dl[k])) {
+    const double dl = b[k];
+    if (fabs(d[k]) >= fabs(dl)) {
       if (d[k] == 0.0) d[k] = tiny;
-      l[k] = dl[k] / d[k];
+      l[k] = dl / d[k];
       d[k + 1] -= l[k] * du[k];
     } else {
-      piv[k] = 1;
-      l[k] = d[k] / dl[k];
-      d[k] = dl[k];
+      piv[k] = true;
+      l[k] = d[k] / dl;
+      d[k] = dl;
       const double t = d[k + 1];
       d[k + 1] = du[k] - l[k] * t;
       du[k] = t;
@@ -513,10 +555,10 @@ __global__ void tridiag_kernel(DevState* st) {
     }
   }
   if (d[m - 1] == 0.0) d[m - 1] = tiny;
+  for (int k = 0; k < m; ++k) rd[k] = 1.0 / d[k];
   double y[kMaxSteps];
   for (int k = 0; k < m; ++k) y[k] = 1.0;
   for (int it = 0; it < 3; ++it) {
-    // forward: apply L^-1 with the row swaps
     for (int k = 0; k < m - 1; ++k) {
       if (piv[k]) {
         const double t = y[k];
@@ -526,23 +568,23 @@ __global__ void tridiag_kernel(DevState* st) {
         y[k + 1] -= l[k] * y[k];
       }
     }
-    // backward: U y = rhs
     for (int k = m - 1; k >= 0; --k) {
-      double s = y[k];
-      if (k + 1 < m) s -= du[k] * y[k + 1];
-      if (k + 2 < m) s -= du2[k] * y[k + 2];
-      y[k] = s / d[k];
+      double sacc = y[k];
+      if (k + 1 < m) sacc -= du[k] * y[k + 1];
+      if (k + 2 < m) sacc -= du2[k] * y[k + 2];
+      y[k] = sacc * rd[k];
     }
     double nrm = 0.0;
     for (int k = 0; k < m; ++k) nrm += y[k] * y[k];
     nrm = sqrt(nrm);
-    if (!(nrm > 0.0)) {
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
       for (int k = 0; k < m; ++k) y[k] = k == 0 ? 1.0 : 0.0;
       break;
     }
-    for (int k = 0; k < m; ++k) y[k] /= nrm;
+    const double inv = 1.0 / nrm;
+    for (int k = 0; k < m; ++k) y[k] *= inv;
   }
-  st->sigma = sigma;
+  st->sigma = sigma * scale_s;
   for (int k = 0; k < kMaxSteps; ++k) st->y[k] = k < m ? y[k] : 0.0;
 }
 
@@ -621,81 +663,137 @@ __global__ void bound_final_kernel(int n, const double* norms, int nctas, DevSta
   }
 }
 
-// X_0 = RN(X * (1/lam~)) into a full symmetric 16-bit matrix, from the upper
-// triangle of X, in 32 x 32 tiles through shared memory.
+// TF32 rounding (10 explicit mantissa bits, nearest, ties away from zero) of a
+// finite value; the tensor cores read only these bits of an FP32 operand.
+__device__ __forceinline__ float tf32_round(float v) {
+  if (!isfinite(v)) return v;
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Four consecutive elements (positions pos .. pos+3 of a row) of the output
+// matrix in the chain's storage: 16-bit, TF32 hi/lo pairs, or BF16 hi/lo pairs
+// plus an FP16 copy (M_f16, may be null).
+__device__ __forceinline__ void put16(uint16_t* H, const uint16_t (&u)[4], int valid) {
+  if (valid == 4) {
+    *reinterpret_cast<uint2*>(H) =
+        make_uint2(u[0] | (static_cast<uint32_t>(u[1]) << 16), u[2] | (static_cast<uint32_t>(u[3]) << 16));
+  } else {
+    for (int k = 0; k < valid; ++k) H[k] = u[k];
+  }
+}
+
 template <int DT>
-__global__ void scale_cast_kernel(const DevArgs* __restrict__ args, int n, const DevState* __restrict__ st,
-                                  void* __restrict__ M, void* __restrict__ M_lo, int64_t ldm) {
-  __shared__ float s[32][33];
+__device__ __forceinline__ void store4(void* M, void* M_lo, void* M_f16, int64_t pos, const float (&v)[4],
+                                       int valid) {
+  if (DT == DT_TF32X3) {
+    float h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      h[k] = tf32_round(v[k]);
+      l[k] = tf32_round(v[k] - h[k]);
+    }
+    float* Mh = static_cast<float*>(M) + pos;
+    float* Ml = static_cast<float*>(M_lo) + pos;
+    if (valid == 4) {
+      *reinterpret_cast<float4*>(Mh) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(Ml) = make_float4(l[0], l[1], l[2], l[3]);
+    } else {
+      for (int k = 0; k < valid; ++k) {
+        Mh[k] = h[k];
+        Ml[k] = l[k];
+      }
+    }
+  } else if (DT == DT_BF16X3) {
+    uint16_t h[4], l[4], f[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat16 hb = __float2bfloat16_rn(v[k]);
+      h[k] = __bfloat16_as_ushort(hb);
+      l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k] - __bfloat162float(hb)));
+      f[k] = __half_as_ushort(__float2half_rn(v[k]));
+    }
+    put16(static_cast<uint16_t*>(M) + pos, h, valid);
+    put16(static_cast<uint16_t*>(M_lo) + pos, l, valid);
+    if (M_f16) put16(static_cast<uint16_t*>(M_f16) + pos, f, valid);
+  } else {
+    uint16_t u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      u[k] = DT == DT_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v[k])) : __half_as_ushort(__float2half_rn(v[k]));
+    put16(static_cast<uint16_t*>(M) + pos, u, valid);
+  }
+}
+
+// X_0 = RN(X * (1/lam~)) into a full symmetric matrix (16-bit, or TF32 hi/lo
+// pairs), from the upper triangle of X, in 64 x 64 tiles through shared memory.
+// Thread (tx, ty): rows i0 + 4 tx .. +3 (one 16-byte load), columns
+// j0 + ty + 16 c, c = 0..3.  Both output positions are written with
+// row-contiguous vector stores.
+template <int DT>
+__global__ void __launch_bounds__(256) scale_cast_kernel(const DevArgs* __restrict__ args, int n,
+                                                         const DevState* __restrict__ st, void* __restrict__ M,
+                                                         void* __restrict__ M_lo, void* __restrict__ M_f16,
+                                                         int64_t ldm) {
+  __shared__ float s[64][65];
   int bi, bj;
   tile_of(blockIdx.x, bi, bj);
-  const int i0 = bi * 32, j0 = bj * 32;
+  const int i0 = bi * 64, j0 = bj * 64;
   const float* __restrict__ X = args->X;
   const int64_t ld = args->ld;
   const float inv = static_cast<float>(st->inv_lambda);
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool diag = bi == bj;
+  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  const int ib = i0 + 4 * tx;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int jj = ty + 8 * r;
-    const int i = i0 + tx, j = j0 + jj;
-    float v = 0.f;
-    if (i < n && j < n && (!diag || tx <= jj)) v = X[static_cast<int64_t>(j) * ld + i] * inv;
-    s[tx][jj] = v;
+  for (int c = 0; c < 4; ++c) {
+    const int jj = ty + 16 * c, j = j0 + jj;
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    if (j < n) {
+      const float* col = X + static_cast<int64_t>(j) * ld + ib;
+      if (vec && ib + 3 < n) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(col));
+        x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (ib + k < n) x[k] = __ldg(col + k);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int ii = 4 * tx + k;
+      s[ii][jj] = (!diag || ii <= jj) ? x[k] * inv : 0.f;
+    }
   }
   __syncthreads();
   if (diag) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int jj = ty + 8 * r;
-      if (tx > jj) s[tx][jj] = s[jj][tx];
+    for (int c = 0; c < 4; ++c) {
+      const int jj = ty + 16 * c;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ii = 4 * tx + k;
+        if (ii > jj) s[ii][jj] = s[jj][ii];
+      }
     }
     __syncthreads();
   }
-  // store at (i + j ldm) and mirrored at (j + i ldm); both coalesced along tx
+  const int valid_i = min(4, n - ib);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int jj = ty + 8 * r;
-    const int i = i0 + tx, j = j0 + jj;
-    if (i < n && j < n) {
-      const float v = s[tx][jj];
-      const float w = s[jj][tx];
-      if (DT == DT_TF32X3) {
-        float* Mh = static_cast<float*>(M);
-        float* Ml = static_cast<float*>(M_lo);
-        // hi = v rounded to TF32 (10 explicit mantissa bits), lo = remainder rounded to TF32
-        uint32_t b = __float_as_uint(v);
-        uint32_t hb = (b + 0x1000u) & 0xFFFFE000u;
-        float hi = __uint_as_float(hb);
-        if (!isfinite(v)) hi = v;
-        float rem = v - hi;
-        uint32_t rb = (__float_as_uint(rem) + 0x1000u) & 0xFFFFE000u;
-        Mh[static_cast<int64_t>(j) * ldm + i] = hi;
-        Ml[static_cast<int64_t>(j) * ldm + i] = __uint_as_float(rb);
-        (void)w;
-      } else {
-        uint16_t* H = static_cast<uint16_t*>(M);
-        H[static_cast<int64_t>(j) * ldm + i] =
-            DT == DT_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
-      }
+  for (int c = 0; c < 4; ++c) {
+    const int jj = ty + 16 * c, j = j0 + jj;
+    // position (i + j ldm): memory row j, elements i0 + 4 tx .. +3
+    if (j < n && valid_i > 0) {
+      const float v[4] = {s[4 * tx][jj], s[4 * tx + 1][jj], s[4 * tx + 2][jj], s[4 * tx + 3][jj]};
+      store4<DT>(M, M_lo, M_f16, static_cast<int64_t>(j) * ldm + ib, v, valid_i);
     }
-    const int i2 = i0 + jj, j2 = j0 + tx;  // mirrored position, coalesced along tx
-    if (!diag && i2 < n && j2 < n) {
-      const float v2 = s[jj][tx];
-      if (DT == DT_TF32X3) {
-        float* Mh = static_cast<float*>(M);
-        float* Ml = static_cast<float*>(M_lo);
-        uint32_t b = __float_as_uint(v2);
-        float hi = __uint_as_float((b + 0x1000u) & 0xFFFFE000u);
-        if (!isfinite(v2)) hi = v2;
-        float rem = v2 - hi;
-        Mh[static_cast<int64_t>(i2) * ldm + j2] = hi;
-        Ml[static_cast<int64_t>(i2) * ldm + j2] = __uint_as_float((__float_as_uint(rem) + 0x1000u) & 0xFFFFE000u);
-      } else {
-        uint16_t* H = static_cast<uint16_t*>(M);
-        H[static_cast<int64_t>(i2) * ldm + j2] =
-            DT == DT_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v2)) : __half_as_ushort(__float2half_rn(v2));
-      }
+    // mirrored position (j + i ldm): memory row i = i0 + jj, elements j0 + 4 tx .. +3
+    const int i = i0 + jj, jc = j0 + 4 * tx;
+    const int valid_j = min(4, n - jc);
+    if (!diag && i < n && valid_j > 0) {
+      const float v[4] = {s[jj][4 * tx], s[jj][4 * tx + 1], s[jj][4 * tx + 2], s[jj][4 * tx + 3]};
+      store4<DT>(M, M_lo, M_f16, static_cast<int64_t>(i) * ldm + jc, v, valid_j);
     }
   }
 }
@@ -800,16 +898,17 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
 }
 
 cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n, void* M,
-                               void* M_lo, int64_t ldm, cudaStream_t s) {
-  const int nb = static_cast<int>((n + 31) / 32);
+                               void* M_lo, void* M_f16, int64_t ldm, cudaStream_t s) {
+  const int nb = static_cast<int>((n + 63) / 64);
   const int tiles = nb * (nb + 1) / 2;
-  dim3 blk(32, 8);
-  if (dtype == DT_F16)
-    scale_cast_kernel<DT_F16><<<tiles, blk, 0, s>>>(args, static_cast<int>(n), st, M, M_lo, ldm);
-  else if (dtype == DT_BF16)
-    scale_cast_kernel<DT_BF16><<<tiles, blk, 0, s>>>(args, static_cast<int>(n), st, M, M_lo, ldm);
-  else
-    scale_cast_kernel<DT_TF32X3><<<tiles, blk, 0, s>>>(args, static_cast<int>(n), st, M, M_lo, ldm);
+  const int blk = 256;
+  const int ni = static_cast<int>(n);
+  switch (dtype) {
+    case DT_F16: scale_cast_kernel<DT_F16><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
+    case DT_BF16: scale_cast_kernel<DT_BF16><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
+    case DT_TF32X3: scale_cast_kernel<DT_TF32X3><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
+    default: scale_cast_kernel<DT_BF16X3><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
+  }
   return cudaGetLastError();
 }
 

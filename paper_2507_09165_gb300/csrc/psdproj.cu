@@ -72,25 +72,38 @@ bool get_schedule(psd_precision_t prec, Schedule& s) {
   }
 }
 
-int dtype_of(psd_precision_t prec) {
-  return prec == PSD_PREC_BF16 ? DT_BF16 : prec == PSD_PREC_FP32 ? DT_TF32X3 : DT_F16;
-}
+// Storage of the iterates per precision: 16-bit single matrices (FP16, BF16),
+// TF32 hi/lo pairs (FP32 path), or BF16 hi/lo pairs for the first kMixedSplit
+// stages followed by FP16 (mixed).
+constexpr int kMixedSplit = 3;
 
-bool prec_built(psd_precision_t prec) { return prec == PSD_PREC_FP16 || prec == PSD_PREC_BF16; }
+int dtype16_of(psd_precision_t prec) { return prec == PSD_PREC_BF16 ? DT_BF16 : DT_F16; }
+
+bool prec_built(psd_precision_t prec) {
+  return prec == PSD_PREC_FP16 || prec == PSD_PREC_BF16 || prec == PSD_PREC_FP32 || prec == PSD_PREC_MIXED;
+}
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 // Leading dimension of the internal iterates: a multiple of 64 elements (128 B rows).
 int64_t internal_ld(int64_t n) { return round_up(std::max<int64_t>(n, 1), 64); }
 
-size_t matrix_bytes(int64_t n, int dtype) {
-  const int64_t ld = internal_ld(n);
-  const size_t one = static_cast<size_t>(ld) * static_cast<size_t>(n) * (dtype == DT_TF32X3 ? 8 : 2);
-  return round_up(static_cast<int64_t>(one), 1024);
+// Workspace is carved into slots of one n x ldm 16-bit matrix: a 16-bit
+// matrix takes 1 slot, a BF16 pair 2, a TF32 pair 4.
+size_t slot_bytes(int64_t n) {
+  return static_cast<size_t>(round_up(static_cast<int64_t>(internal_ld(n)) * n * 2, 1024));
+}
+
+int slots_needed(psd_precision_t prec) {
+  switch (prec) {
+    case PSD_PREC_FP32: return 16;   // X_0, X_{t-1}, P, X_t as TF32 pairs (Y and X_t share)
+    case PSD_PREC_MIXED: return 9;   // X_0 pair + X_0 FP16 + three BF16 pairs
+    default: return 4;               // X_0 + three rotating 16-bit matrices
+  }
 }
 
 size_t total_ws_bytes(int64_t n, psd_precision_t prec) {
-  return 4 * matrix_bytes(n, dtype_of(prec)) + lanczos_bytes(n) + 1024;
+  return slots_needed(prec) * slot_bytes(n) + lanczos_bytes(n) + 1024;
 }
 
 psd_status_t check_device() {
@@ -108,13 +121,13 @@ struct Plan {
   cudaStream_t stream = nullptr;
   int64_t n = 0;
   psd_precision_t prec = PSD_PREC_FP16;
-  int dtype = DT_F16;
   Schedule sched{};
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
   bool owns_ws = false;
-  void* M[4] = {nullptr, nullptr, nullptr, nullptr};
-  void* Mlo[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint8_t* slots = nullptr;  // slot 0 base
+  size_t slot_size = 0;
+  int nslots = 0;
   int64_t ldm = 0;
   LanczosBufs L{};
   DevArgs* d_args = nullptr;
@@ -122,9 +135,9 @@ struct Plan {
   psd_info_t* d_info = nullptr;  // default report
   int2* d_tiles = nullptr;
   int ntiles = 0;
-  CUtensorMap tmA[4], tmB[4];
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
+  int launches = 0;  // kernel launches of one projection (graph nodes + argument block)
 };
 
 using PlanKey = std::tuple<int, cudaStream_t, int64_t, int, void*>;
@@ -142,7 +155,6 @@ void free_plan(Plan* p) {
 
 psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   const int64_t n = p->n;
-  p->dtype = dtype_of(p->prec);
   if (!get_schedule(p->prec, p->sched)) return PSD_ERR_INVALID_ARG;
   p->ldm = internal_ld(n);
   p->ws_bytes = total_ws_bytes(n, p->prec);
@@ -159,13 +171,10 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
     p->owns_ws = true;
   }
   uint8_t* base = reinterpret_cast<uint8_t*>(round_up(reinterpret_cast<int64_t>(p->ws), 1024));
-  const size_t mb = matrix_bytes(n, p->dtype);
-  for (int i = 0; i < 4; ++i) {
-    p->M[i] = base + i * mb;
-    if (p->dtype == DT_TF32X3)
-      p->Mlo[i] = base + i * mb + static_cast<size_t>(p->ldm) * static_cast<size_t>(n) * 4;
-  }
-  lanczos_carve(p->L, n, base + 4 * mb);
+  p->slot_size = slot_bytes(n);
+  p->nslots = slots_needed(p->prec);
+  p->slots = base;
+  lanczos_carve(p->L, n, base + p->nslots * p->slot_size);
 
   // small library-owned records: args | state | info | tiles
   std::vector<int2> tiles = make_tile_list(n);
@@ -187,14 +196,41 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   if (!tiles.empty() &&
       cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return PSD_ERR_CUDA;
-  for (int i = 0; i < 4; ++i) {
-    if (p->dtype == DT_TF32X3) continue;
-    if (!encode_tmap(&p->tmA[i], p->dtype, p->M[i], n, p->ldm, 128) ||
-        !encode_tmap(&p->tmB[i], p->dtype, p->M[i], n, p->ldm, 256))
-      return PSD_ERR_CUDA;
-  }
   return PSD_OK;
 }
+
+// A matrix of the chain living in workspace slots.
+enum MatKind : int { MK_16 = 0, MK_BF16X3 = 1, MK_TF32X3 = 2 };
+struct Mat {
+  int kind = MK_16;
+  int slot = -1;
+  int dt16 = DT_F16;  // element type of an MK_16 matrix
+};
+
+int kind_slots(int kind) { return kind == MK_16 ? 1 : kind == MK_BF16X3 ? 2 : 4; }
+
+struct SlotPool {
+  uint32_t used = 0;
+  int nslots = 0;
+  int alloc(int k) {
+    for (int s = 0; s + k <= nslots; ++s) {
+      const uint32_t mask = ((1u << k) - 1u) << s;
+      if ((used & mask) == 0) {
+        used |= mask;
+        return s;
+      }
+    }
+    return -1;
+  }
+  void release(int s, int k) { used &= ~(((1u << k) - 1u) << s); }
+};
+
+void* part_ptr(const Plan* p, const Mat& m, int part) {
+  const int step = m.kind == MK_TF32X3 ? 2 : 1;
+  return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * step)) * p->slot_size;
+}
+
+int part_dtype(const Mat& m) { return m.kind == MK_16 ? m.dt16 : m.kind == MK_BF16X3 ? DT_BF16X3 : DT_TF32X3; }
 
 GemmParams base_params(const Plan* p) {
   GemmParams g{};
@@ -202,63 +238,115 @@ GemmParams base_params(const Plan* p) {
   g.k_blocks = static_cast<int>((p->n + 63) / 64);
   g.num_tiles = p->ntiles;
   g.tiles = p->d_tiles;
-  const uint32_t fmt = p->dtype == DT_BF16 ? 1u : 0u;
-  g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(256 >> 3) << 17) |
-            (static_cast<uint32_t>(128 >> 4) << 24);
   g.ep.status = &p->d_state->status;
   return g;
+}
+
+// One product C = epi(A * B).  A and B have the same kind; `out` is the
+// output matrix (ignored for EPI_FINAL), `Y` the EPI_POLY operand.
+cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, const Mat* Y, float a, float b,
+                 float c, float sc, unsigned* absmax, cudaStream_t s) {
+  GemmParams g = base_params(p);
+  const int64_t n = p->n, ldm = p->ldm;
+  // K-blocks of 128 bytes: 64 16-bit or 32 TF32 elements
+  if (A.kind == MK_TF32X3) g.k_blocks = static_cast<int>((n + 31) / 32);
+  g.ep.a = a;
+  g.ep.b = b;
+  g.ep.c = c;
+  g.ep.s = sc;
+  g.ep.absmax = absmax;
+  if (epi == EPI_FINAL) {
+    g.ep.args = p->d_args;
+    g.ep.st = p->d_state;
+  } else {
+    g.ep.C = part_ptr(p, *out, 0);
+    g.ep.C_lo = out->kind == MK_16 ? nullptr : part_ptr(p, *out, 1);
+    g.ep.ldc = ldm;
+  }
+  if (epi == EPI_POLY) {
+    g.ep.Y = part_ptr(p, *Y, 0);
+    g.ep.Y_lo = Y->kind == MK_16 ? nullptr : part_ptr(p, *Y, 1);
+    g.ep.ldy = ldm;
+  }
+  const int grid = num_sms();
+  if (A.kind == MK_16) {
+    CUtensorMap ta, tb;
+    if (!encode_tmap(&ta, A.dt16, part_ptr(p, A, 0), n, ldm, 128) ||
+        !encode_tmap(&tb, B.dt16, part_ptr(p, B, 0), n, ldm, 256))
+      return cudaErrorInvalidValue;
+    const uint32_t fmt = A.dt16 == DT_BF16 ? 1u : 0u;
+    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (32u << 17) | (8u << 24);
+    return launch_symgemm(A.dt16, epi, ta, tb, g, grid, s);
+  }
+  const int dt = part_dtype(A);
+  CUtensorMap tm[4];
+  if (!encode_tmap(&tm[0], dt, part_ptr(p, A, 0), n, ldm, 128) ||
+      !encode_tmap(&tm[1], dt, part_ptr(p, A, 1), n, ldm, 128) ||
+      !encode_tmap(&tm[2], dt, part_ptr(p, B, 0), n, ldm, 256) ||
+      !encode_tmap(&tm[3], dt, part_ptr(p, B, 1), n, ldm, 256))
+    return cudaErrorInvalidValue;
+  const int out_mode = epi == EPI_FINAL ? 2 : (out->kind == MK_16 ? 1 : 0);
+  return launch_symgemm_x3(A.kind == MK_TF32X3, epi, out_mode, tm, g, grid, s);
 }
 
 // Enqueue the whole projection (used for graph capture and for direct launch).
 cudaError_t enqueue_projection(Plan* p, cudaStream_t s) {
   cudaError_t e;
   if ((e = enqueue_norm_bound(p->L, p->d_args, p->d_state, s)) != cudaSuccess) return e;
-  if ((e = enqueue_scale_cast(p->dtype, p->d_args, p->d_state, p->n, p->M[0], p->Mlo[0], p->ldm, s)) !=
+  SlotPool pool;
+  pool.nslots = p->nslots;
+  const int T = p->sched.T;
+  auto kind_of_stage = [&](int t) {
+    if (p->prec == PSD_PREC_FP32) return static_cast<int>(MK_TF32X3);
+    if (p->prec == PSD_PREC_MIXED && t < kMixedSplit) return static_cast<int>(MK_BF16X3);
+    return static_cast<int>(MK_16);
+  };
+  const int dt16 = dtype16_of(p->prec);
+  auto make = [&](int kind) {
+    Mat m;
+    m.kind = kind;
+    m.dt16 = dt16;
+    m.slot = pool.alloc(kind_slots(kind));
+    return m;
+  };
+  // X_0 in the first stage's storage (and an FP16 copy for the mixed final product)
+  Mat X0 = make(kind_of_stage(0));
+  Mat X0f16;
+  if (p->prec == PSD_PREC_MIXED) X0f16 = make(MK_16);
+  if (X0.slot < 0 || (p->prec == PSD_PREC_MIXED && X0f16.slot < 0)) return cudaErrorMemoryAllocation;
+  if ((e = enqueue_scale_cast(part_dtype(X0), p->d_args, p->d_state, p->n, part_ptr(p, X0, 0),
+                              X0.kind == MK_16 ? nullptr : part_ptr(p, X0, 1),
+                              p->prec == PSD_PREC_MIXED ? part_ptr(p, X0f16, 0) : nullptr, p->ldm, s)) !=
       cudaSuccess)
     return e;
-  const int grid = num_sms();
-  int cur = 0;
-  for (int t = 0; t < p->sched.T; ++t) {
-    int a, b;
-    if (cur == 0) {
-      a = 1;
-      b = 2;
-    } else {
-      int o[2], k = 0;
-      for (int i = 1; i <= 3; ++i)
-        if (i != cur) o[k++] = i;
-      a = o[0];
-      b = o[1];
-    }
-    // Y = X_{t-1}^2 -> a
-    GemmParams g = base_params(p);
-    g.ep.C = p->M[a];
-    g.ep.ldc = p->ldm;
-    if ((e = launch_symgemm(p->dtype, EPI_COPY, p->tmA[cur], p->tmB[cur], g, grid, s)) != cudaSuccess) return e;
-    // P = a_t I + b_t Y + c_t Y^2 -> b
-    g = base_params(p);
-    g.ep.C = p->M[b];
-    g.ep.ldc = p->ldm;
-    g.ep.Y = p->M[a];
-    g.ep.ldy = p->ldm;
-    g.ep.a = static_cast<float>(p->sched.coef[t][0]);
-    g.ep.b = static_cast<float>(p->sched.coef[t][1]);
-    g.ep.c = static_cast<float>(p->sched.coef[t][2]);
-    if ((e = launch_symgemm(p->dtype, EPI_POLY, p->tmA[a], p->tmB[a], g, grid, s)) != cudaSuccess) return e;
-    // X_t = X_{t-1} P / s_t -> a
-    g = base_params(p);
-    g.ep.C = p->M[a];
-    g.ep.ldc = p->ldm;
-    g.ep.s = static_cast<float>(1.0 / p->sched.post[t]);
-    if (t == p->sched.T - 1) g.ep.absmax = &p->d_state->absmax_bits;
-    if ((e = launch_symgemm(p->dtype, EPI_SCALE, p->tmA[cur], p->tmB[b], g, grid, s)) != cudaSuccess) return e;
-    cur = a;
+  Mat cur = X0;
+  for (int t = 0; t < T; ++t) {
+    const int k = kind_of_stage(t);
+    const int knext = t + 1 < T ? kind_of_stage(t + 1) : static_cast<int>(MK_16);
+    const int kout = (p->prec == PSD_PREC_FP32) ? static_cast<int>(MK_TF32X3) : knext;
+    Mat Y = make(k);
+    if (Y.slot < 0) return cudaErrorMemoryAllocation;
+    if ((e = gemm(p, EPI_COPY, cur, cur, &Y, nullptr, 0.f, 0.f, 0.f, 1.f, nullptr, s)) != cudaSuccess) return e;
+    Mat P = make(k);
+    if (P.slot < 0) return cudaErrorMemoryAllocation;
+    if ((e = gemm(p, EPI_POLY, Y, Y, &P, &Y, static_cast<float>(p->sched.coef[t][0]),
+                  static_cast<float>(p->sched.coef[t][1]), static_cast<float>(p->sched.coef[t][2]), 1.f, nullptr,
+                  s)) != cudaSuccess)
+      return e;
+    pool.release(Y.slot, kind_slots(Y.kind));
+    Mat Xn = make(kout);
+    if (Xn.slot < 0) return cudaErrorMemoryAllocation;
+    unsigned* amax = (t == T - 1) ? &p->d_state->absmax_bits : nullptr;
+    if ((e = gemm(p, EPI_SCALE, cur, P, &Xn, nullptr, 0.f, 0.f, 0.f, static_cast<float>(1.0 / p->sched.post[t]),
+                  amax, s)) != cudaSuccess)
+      return e;
+    pool.release(P.slot, kind_slots(P.kind));
+    if (cur.slot != X0.slot) pool.release(cur.slot, kind_slots(cur.kind));
+    cur = Xn;
   }
   // out = (X + lam~ X_0 X_T) / 2
-  GemmParams g = base_params(p);
-  g.ep.args = p->d_args;
-  g.ep.st = p->d_state;
-  if ((e = launch_symgemm(p->dtype, EPI_FINAL, p->tmA[0], p->tmB[cur], g, grid, s)) != cudaSuccess) return e;
+  const Mat& A0 = (p->prec == PSD_PREC_MIXED) ? X0f16 : X0;
+  if ((e = gemm(p, EPI_FINAL, A0, cur, nullptr, nullptr, 0.f, 0.f, 0.f, 1.f, nullptr, s)) != cudaSuccess) return e;
   return enqueue_finalize(p->d_args, p->d_state, s);
 }
 
@@ -298,6 +386,9 @@ void ensure_graph(Plan* p) {
     cudaError_t e = enqueue_projection(p, cs);
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess && e2 == cudaSuccess && graph) {
+      size_t nodes = 0;
+      cudaGraphGetNodes(graph, nullptr, &nodes);
+      p->launches = static_cast<int>(nodes) + 1;
       if (cudaGraphInstantiate(&p->exec, graph, 0) != cudaSuccess) p->exec = nullptr;
     }
     if (graph) cudaGraphDestroy(graph);
@@ -518,6 +609,14 @@ psd_status_t psd_schedule(psd_precision_t precision, int32_t* T, double* coef, d
     post_scale[t] = s.post[t];
   }
   return PSD_OK;
+}
+
+int32_t psd_kernel_launches(int64_t n, psd_precision_t precision, psd_stream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_plans.find(PlanKey{dev, reinterpret_cast<cudaStream_t>(stream), n, static_cast<int>(precision), nullptr});
+  return it == g_plans.end() ? 0 : it->second->launches;
 }
 
 int32_t psd_gemm_count(psd_precision_t precision) {

@@ -43,9 +43,13 @@ constexpr int kABytes16 = kBM * kBK16 * 2;          // 16 KB
 constexpr int kBBytes16 = kBN * kBK16 * 2;          // 32 KB
 constexpr int kStageBytes16 = kABytes16 + kBBytes16;  // 48 KB
 
-// Epilogue staging per warp: 32 rows x 33 words (covers FP32 and 16-bit).
+// Epilogue staging per warp.  16-bit outputs: the chunk row-major (S),
+// transposed (ST) and the prefetched Y chunk (YB), each 32 x 40 halves (80-byte
+// rows keep 16-byte accesses aligned and spread over the banks).  FP32 output:
+// 32 x 33 words, in the same space.
 constexpr int kStgWords = 33;
-constexpr int kEpiWarpBytes = 32 * kStgWords * 4;
+constexpr int kH = 40;
+constexpr int kEpiWarpBytes = 3 * 32 * kH * 2;  // 7680 >= 32 * 33 * 4
 
 constexpr int kTmemCols = 512;
 
@@ -54,10 +58,6 @@ __host__ __device__ constexpr int smem_bytes16() {
          8 * (2 * kStages16 + 5) + 16;
 }
 
-__device__ __forceinline__ float ld16(const uint16_t* p, int64_t idx, bool bf16) {
-  const uint16_t u = p[idx];
-  return bf16 ? __bfloat162float(__ushort_as_bfloat16(u)) : __half2float(__ushort_as_half(u));
-}
 __device__ __forceinline__ uint16_t to16(float v, bool bf16) {
   return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
 }
@@ -69,28 +69,69 @@ __device__ __forceinline__ void raise_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Y chunk (r0..r0+31) x (c0..c0+31) of a symmetric 16-bit matrix, read as
+// memory rows c (32 contiguous halves at c * ldy + r0): lane l loads 16 bytes of
+// rows c0 + l/4 + 8k, k = 0..3.  Zeros outside n.
+__device__ __forceinline__ void load_y_chunk(const uint16_t* __restrict__ Y, int64_t ldy, int n, int r0, int c0,
+                                             int lane, uint4 (&y)[4]) {
+  const int r = r0 + 8 * (lane & 3);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = c0 + (lane >> 2) + 8 * k;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (c < n && r < n) {
+      const uint16_t* p = Y + static_cast<int64_t>(c) * ldy + r;
+      if (r + 7 < n) {
+        v = __ldg(reinterpret_cast<const uint4*>(p));
+      } else {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        for (int e = 0; e < 8 && r + e < n; ++e) w[e >> 1] |= static_cast<uint32_t>(p[e]) << (16 * (e & 1));
+        v = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    y[k] = v;
+  }
+}
+
+// 16 bytes (8 halves) of one staged row to global memory at dst[0..7], clipped at `limit`.
+__device__ __forceinline__ void store8(uint16_t* dst, const uint16_t* src, int first, int n) {
+  const uint4 v = *reinterpret_cast<const uint4*>(src);
+  if (first + 7 < n) {
+    *reinterpret_cast<uint4*>(dst) = v;
+  } else {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int e = 0; e < 8 && first + e < n; ++e) dst[e] = static_cast<uint16_t>(w[e >> 1] >> (16 * (e & 1)));
+  }
+}
+
 // One 32 x 32 chunk with 16-bit output.  Lane l holds row r0 + l, v[j] is the
 // accumulator at column c0 + j.  Diagonal chunks (r0 == c0) are symmetrised
-// from their upper part; off-diagonal chunks are written at both positions.
+// from their upper part; off-diagonal chunks are written at both positions,
+// (r, c) and (c, r), with 16-byte stores from the staged copies.
 template <int EPI>
 __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16, int r0, int c0,
-                                                 const uint32_t (&v)[32], uint32_t* stg, int lane,
-                                                 unsigned& amax_bits) {
+                                                 const uint32_t (&v)[32], uint8_t* wbuf, const uint4 (&y)[4],
+                                                 int lane, unsigned& amax_bits) {
+  uint16_t* S = reinterpret_cast<uint16_t*>(wbuf);  // [32][kH] row t = output row r0 + t
+  uint16_t* ST = S + 32 * kH;                        // [32][kH] row j = output column c0 + j
+  uint16_t* YB = ST + 32 * kH;                       // [32][kH] row j = Y column c0 + j
   const int n = p.n;
   const int r = r0 + lane;
   const bool diag = (r0 == c0);
-  const bool row_ok = r < n;
-  uint16_t h[32];
+  if (EPI == EPI_POLY) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      *reinterpret_cast<uint4*>(YB + ((lane >> 2) + 8 * k) * kH + 8 * (lane & 3)) = y[k];
+    __syncwarp();
+  }
+  uint32_t h[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const float acc = __uint_as_float(v[j]);
     float val;
     if (EPI == EPI_POLY) {
-      const int c = c0 + j;
-      float y = 0.f;
-      if (row_ok && c < n)
-        y = ld16(static_cast<const uint16_t*>(p.ep.Y), static_cast<int64_t>(c) * p.ep.ldy + r, bf16);
-      val = fmaf(p.ep.c, acc, p.ep.b * y);
+      const float yv = from16(YB[j * kH + lane], bf16);
+      val = fmaf(p.ep.c, acc, p.ep.b * yv);
       if (diag && j == lane) val += p.ep.a;
     } else if (EPI == EPI_SCALE) {
       val = acc * p.ep.s;
@@ -99,47 +140,63 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16,
     }
     h[j] = to16(val, bf16);
   }
+  uint16_t* row = S + lane * kH;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<uint4*>(row + 8 * q) =
+        make_uint4(h[8 * q] | (h[8 * q + 1] << 16), h[8 * q + 2] | (h[8 * q + 3] << 16),
+                   h[8 * q + 4] | (h[8 * q + 5] << 16), h[8 * q + 6] | (h[8 * q + 7] << 16));
   if (diag) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) stg[lane * kStgWords + j] = h[j];
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      if (j < lane) h[j] = static_cast<uint16_t>(stg[j * kStgWords + lane]);
+      if (j < lane) h[j] = S[j * kH + lane];
     __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<uint4*>(row + 8 * q) =
+          make_uint4(h[8 * q] | (h[8 * q + 1] << 16), h[8 * q + 2] | (h[8 * q + 3] << 16),
+                     h[8 * q + 4] | (h[8 * q + 5] << 16), h[8 * q + 6] | (h[8 * q + 7] << 16));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) ST[j * kH + lane] = static_cast<uint16_t>(h[j]);
   }
-  if (p.ep.absmax && row_ok) {
+  if (p.ep.absmax && r < n) {
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(from16(h[j], bf16))));
+      if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(from16(static_cast<uint16_t>(h[j]), bf16))));
   }
+  __syncwarp();
   uint16_t* C = static_cast<uint16_t*>(p.ep.C);
   const int64_t ldc = p.ep.ldc;
-  if (row_ok) {
+  const int seg = 8 * (lane & 3);
+  // memory rows c0 + j: output column c0 + j over rows r0..r0+31 (ST row j; S row j when symmetric)
+  const uint16_t* SA = diag ? S : ST;
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (c0 + j < n) C[static_cast<int64_t>(c0 + j) * ldc + r] = h[j];
+  for (int k = 0; k < 4; ++k) {
+    const int jj = (lane >> 2) + 8 * k;
+    const int c = c0 + jj;
+    if (c < n && r0 + seg < n) store8(C + static_cast<int64_t>(c) * ldc + r0 + seg, SA + jj * kH + seg, r0 + seg, n);
   }
   if (!diag) {
+    // memory rows r0 + t: output row r0 + t over columns c0..c0+31 (S row t)
 #pragma unroll
-    for (int j = 0; j < 32; ++j) stg[lane * kStgWords + j] = h[j];
-    __syncwarp();
-    const int c = c0 + lane;
-    if (c < n) {
-#pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr)
-        if (r0 + rr < n)
-          C[static_cast<int64_t>(r0 + rr) * ldc + c] = static_cast<uint16_t>(stg[rr * kStgWords + lane]);
+    for (int k = 0; k < 4; ++k) {
+      const int tt = (lane >> 2) + 8 * k;
+      const int rr = r0 + tt;
+      if (rr < n && c0 + seg < n)
+        store8(C + static_cast<int64_t>(rr) * ldc + c0 + seg, S + tt * kH + seg, c0 + seg, n);
     }
-    __syncwarp();
   }
+  __syncwarp();
 }
 
 // One 32 x 32 chunk of the final output out = (X + lam~ acc) / 2 in FP32,
 // reading only the upper triangle of the caller's X (column-major).
 __device__ __forceinline__ void epilogue_chunk_final(const GemmParams& p, int r0, int c0,
-                                                     const uint32_t (&v)[32], uint32_t* stg,
+                                                     const uint32_t (&v)[32], uint8_t* wbuf,
                                                      int lane, float lam) {
+  uint32_t* stg = reinterpret_cast<uint32_t*>(wbuf);
   const int n = p.n;
   const DevArgs* a = p.ep.args;
   const float* X = a->X;
@@ -195,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* stages = smem;
-  uint32_t* epi_stg = reinterpret_cast<uint32_t*>(smem + kStages16 * kStageBytes16);
+  uint8_t* epi_stg = smem + kStages16 * kStageBytes16;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages16 * kStageBytes16 + 4 * kEpiWarpBytes);
   // bars: full[S] | empty[S] | tfull[2] | tempty[2] | drain
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStages16 + 5);
@@ -317,26 +374,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     const int ew = warp & 3;
-    uint32_t* stg = epi_stg + ew * (kEpiWarpBytes / 4);
+    uint8_t* wbuf = epi_stg + ew * kEpiWarpBytes;
     uint32_t acc = 0, acc_ph = 0;
     unsigned amax_bits = 0;
     float lam = 0.f;
     if (EPI == EPI_FINAL) lam = static_cast<float>(p.ep.st->lambda);
+    const uint16_t* Y = static_cast<const uint16_t*>(p.ep.Y);
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
       const int2 tc = p.tiles[t];
+      const int r0 = tc.x + 32 * ew;
+      // chunks of this warp's 32 rows that lie on or above the diagonal and inside n
+      const int ch_begin = max(0, (r0 - tc.y) >> 5);
+      const int ch_end = r0 < p.n ? min(kBN / 32, (p.n - tc.y + 31) >> 5) : ch_begin;
+      uint4 ynext[4] = {};
+      if (EPI == EPI_POLY && ch_begin < ch_end)
+        load_y_chunk(Y, p.ep.ldy, p.n, r0, tc.y + 32 * ch_begin, lane, ynext);
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
-      const int r0 = tc.x + 32 * ew;
 #pragma unroll 1
-      for (int ch = 0; ch < kBN / 32; ++ch) {
+      for (int ch = ch_begin; ch < ch_end; ++ch) {
         const int c0 = tc.y + 32 * ch;
-        if (r0 > c0 || r0 >= p.n || c0 >= p.n) continue;  // warp-uniform
+        uint4 ycur[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ycur[k] = ynext[k];
+        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y_chunk(Y, p.ep.ldy, p.n, r0, c0 + 32, lane, ynext);
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
         if (EPI == EPI_FINAL)
-          epilogue_chunk_final(p, r0, c0, v, stg, lane, lam);
+          epilogue_chunk_final(p, r0, c0, v, wbuf, lane, lam);
         else
-          epilogue_chunk16<EPI>(p, bf16, r0, c0, v, stg, lane, amax_bits);
+          epilogue_chunk16<EPI>(p, bf16, r0, c0, v, wbuf, ycur, lane, amax_bits);
       }
       tc_fence_before();
       __syncwarp();
@@ -411,9 +478,9 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
   EncodeFn fn = get_encode();
   if (!fn) return false;
   const int esz = dtype == DT_TF32X3 ? 4 : 2;
-  const CUtensorMapDataType dt = dtype == DT_F16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                 : dtype == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = dtype == DT_F16                          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : (dtype == DT_BF16 || dtype == DT_BF16X3) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};

@@ -1,0 +1,444 @@
+// Split-operand symmetric product: C = A B with each operand stored as a pair
+// (hi, lo), hi = RN(v), lo = RN(v - hi), and the product formed on the tensor
+// cores as A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in one FP32 tensor
+// memory accumulator (the lo * lo term is below the accumulation error).
+//   TF32 pairs (kind::tf32): the FP32 path; three-term TF32 splitting as in
+//     Ootomo & Yokota, "Recovering single precision accuracy from Tensor Cores
+//     while surpassing the FP32 theoretical peak performance" (IJHPCA 2022).
+//   BF16 pairs (kind::f16): about 16 significant bits at three BF16 products,
+//     the early stages of the mixed-precision chain (a split in the manner of
+//     Henry, Tang & Heinecke, "Leveraging the bfloat16 artificial intelligence
+//     datatype for higher-precision computations", ARITH 2019).
+// Same symmetric tiling, warp roles and fused stage epilogues as the 16-bit
+// kernel (symgemm.cu); the output is again a pair, or a single FP16 matrix
+// (the last split stage hands over to FP16), or the FP32 final result.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace psd {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 256;
+constexpr int kThreads = 192;
+constexpr int kStages = 2;
+constexpr int kABytes = kBM * 128;  // one 128-byte swizzle row of K per operand row
+constexpr int kBBytes = kBN * 128;
+constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;  // 96 KB: A_hi | A_lo | B_hi | B_lo
+constexpr int kSW = 33;                                 // staging row stride (words)
+constexpr int kEpiWarpBytes = 2 * 32 * kSW * 4;         // values + Y chunk
+constexpr int kTmemCols = 512;
+
+__host__ __device__ constexpr int smem_bytes_x3() {
+  return 1024 + kStages * kStageBytes + 4 * kEpiWarpBytes + 8 * (2 * kStages + 5) + 16;
+}
+
+template <bool TF32>
+__device__ __forceinline__ float ld_elem(const void* p, int64_t idx) {
+  if (TF32) return static_cast<const float*>(p)[idx];
+  return __bfloat162float(__ushort_as_bfloat16(static_cast<const uint16_t*>(p)[idx]));
+}
+
+__device__ __forceinline__ float tf32_rn(float v) {
+  if (!isfinite(v)) return v;
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ float bf16_rn(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// 4 consecutive elements of a staged column (col = true: S[t..t+3][j]) or row
+// (S[t][j..j+3]) to global memory as FP32, BF16 or FP16, clipped at `valid`.
+template <int KIND>  // 0 = FP32 words, 1 = BF16, 2 = FP16
+__device__ __forceinline__ void store4(void* base, int64_t pos, const float (&v)[4], int valid, bool vec_ok) {
+  if (KIND == 0) {
+    float* d = static_cast<float*>(base) + pos;
+    if (valid == 4 && vec_ok) {
+      *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      for (int e = 0; e < valid; ++e) d[e] = v[e];
+    }
+  } else {
+    uint16_t u[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      u[e] = KIND == 1 ? __bfloat16_as_ushort(__float2bfloat16_rn(v[e])) : __half_as_ushort(__float2half_rn(v[e]));
+    uint16_t* d = static_cast<uint16_t*>(base) + pos;
+    if (valid == 4 && vec_ok) {
+      *reinterpret_cast<uint2*>(d) = make_uint2(u[0] | (static_cast<uint32_t>(u[1]) << 16),
+                                                u[2] | (static_cast<uint32_t>(u[3]) << 16));
+    } else {
+      for (int e = 0; e < valid; ++e) d[e] = u[e];
+    }
+  }
+}
+
+// Writes the staged 32 x 32 chunk S (S[t][j] = value at (r0 + t, c0 + j)) to
+// positions (r, c) -- memory rows c0 + j -- and, unless diagonal, (c, r) --
+// memory rows r0 + t.  Lane l handles 4 consecutive elements of memory row
+// l / 8 + 4 i.  Vector stores only when the row stride and base allow them
+// (the caller's FP32 output may have any leading dimension).
+template <int KIND>
+__device__ __forceinline__ void store_chunk(void* C, int64_t ldc, int n, int r0, int c0, bool diag,
+                                            const float* S, int lane) {
+  const int q = lane & 7;
+  const int64_t esz = KIND == 0 ? 4 : 2;
+  const bool vec_ok = ((ldc * esz) % (4 * esz)) == 0 && (reinterpret_cast<uintptr_t>(C) % (4 * esz)) == 0;
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int jj = (lane >> 3) + 4 * it;
+    const int c = c0 + jj, rs = r0 + 4 * q;
+    if (c < n && rs < n) {
+      const float v[4] = {S[(4 * q) * kSW + jj], S[(4 * q + 1) * kSW + jj], S[(4 * q + 2) * kSW + jj],
+                          S[(4 * q + 3) * kSW + jj]};
+      store4<KIND>(C, static_cast<int64_t>(c) * ldc + rs, v, min(4, n - rs), vec_ok);
+    }
+  }
+  if (!diag) {
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int tt = (lane >> 3) + 4 * it;
+      const int r = r0 + tt, cs = c0 + 4 * q;
+      if (r < n && cs < n) {
+        const float v[4] = {S[tt * kSW + 4 * q], S[tt * kSW + 4 * q + 1], S[tt * kSW + 4 * q + 2],
+                            S[tt * kSW + 4 * q + 3]};
+        store4<KIND>(C, static_cast<int64_t>(r) * ldc + cs, v, min(4, n - cs), vec_ok);
+      }
+    }
+  }
+}
+
+// OUT: 0 = split pair of the operand kind, 1 = single FP16, 2 = FP32 final output.
+template <bool TF32, int EPI, int OUT>
+__device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, int c0, const uint32_t (&v)[32],
+                                                  float* S, float* YB, int lane, float lam, unsigned& amax_bits) {
+  const int n = p.n;
+  const int r = r0 + lane;
+  const bool diag = (r0 == c0);
+  const bool row_ok = r < n;
+  float o[32];
+  if (EPI == EPI_POLY) {
+    // Y chunk (value = hi + lo), read coalesced as memory rows c0 + j
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      const int c = c0 + j;
+      float y = 0.f;
+      if (row_ok && c < n) {
+        const int64_t idx = static_cast<int64_t>(c) * p.ep.ldy + r;
+        y = ld_elem<TF32>(p.ep.Y, idx) + ld_elem<TF32>(p.ep.Y_lo, idx);
+      }
+      YB[j * kSW + lane] = y;
+    }
+  }
+  const float* X = nullptr;
+  int64_t ldx = 0;
+  if (EPI == EPI_FINAL) {
+    X = p.ep.args->X;
+    ldx = p.ep.args->ld;
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float acc = __uint_as_float(v[j]);
+    float val;
+    if (EPI == EPI_POLY) {
+      val = fmaf(p.ep.c, acc, p.ep.b * YB[j * kSW + lane]);
+      if (diag && j == lane) val += p.ep.a;
+    } else if (EPI == EPI_SCALE) {
+      val = acc * p.ep.s;
+    } else if (EPI == EPI_FINAL) {
+      const int c = c0 + j;
+      float x = 0.f;
+      if (row_ok && c < n && (!diag || j >= lane)) x = X[static_cast<int64_t>(c) * ldx + r];
+      val = 0.5f * fmaf(lam, acc, x);
+    } else {
+      val = acc;
+    }
+    o[j] = val;
+  }
+  // symmetrise diagonal chunks from their upper part (values before splitting)
+#pragma unroll
+  for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
+  __syncwarp();
+  if (diag) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < lane) o[j] = S[j * kSW + lane];
+    __syncwarp();
+  }
+  if constexpr (OUT == 2) {
+    if (diag) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
+      __syncwarp();
+    }
+    store_chunk<0>(p.ep.args->out, p.ep.args->ld_out, n, r0, c0, diag, S, lane);
+    __syncwarp();
+  } else if constexpr (OUT == 1) {
+    if (p.ep.absmax && row_ok) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(__half2float(__float2half_rn(o[j])))));
+    }
+    if (diag) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
+      __syncwarp();
+    }
+    store_chunk<2>(p.ep.C, p.ep.ldc, n, r0, c0, diag, S, lane);
+    __syncwarp();
+  } else {
+  // split pair: hi first, then lo, through the same staging buffer
+  float lo[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float hi = TF32 ? tf32_rn(o[j]) : bf16_rn(o[j]);
+    lo[j] = TF32 ? tf32_rn(o[j] - hi) : bf16_rn(o[j] - hi);
+    o[j] = hi;
+  }
+  if (p.ep.absmax && row_ok) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(o[j] + lo[j])));
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
+  __syncwarp();
+  store_chunk<TF32 ? 0 : 1>(p.ep.C, p.ep.ldc, n, r0, c0, diag, S, lane);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 32; ++j) S[lane * kSW + j] = lo[j];
+  __syncwarp();
+  store_chunk<TF32 ? 0 : 1>(p.ep.C_lo, p.ep.ldc, n, r0, c0, diag, S, lane);
+  __syncwarp();
+  }
+}
+
+template <bool TF32, int EPI, int OUT>
+__global__ void __launch_bounds__(kThreads, 1)
+    symgemm_x3_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                      const GemmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* stages = smem;
+  uint8_t* epi = smem + kStages * kStageBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi + 4 * kEpiWarpBytes);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + kStages + s); };
+  auto tfull_bar = [&](int a) { return smem_u32(bars + 2 * kStages + a); };
+  auto tempty_bar = [&](int a) { return smem_u32(bars + 2 * kStages + 2 + a); };
+  const uint32_t drain_bar = smem_u32(bars + 2 * kStages + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 4);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&tmAh);
+    tma_prefetch_desc(&tmAl);
+    tma_prefetch_desc(&tmBh);
+    tma_prefetch_desc(&tmBl);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  constexpr int kKElems = TF32 ? 32 : 64;  // K elements per 128-byte row
+  constexpr int kKStep = TF32 ? 8 : 16;    // K per MMA instruction (32 bytes)
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int last_parity[kStages];
+      for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
+      uint32_t s = 0, ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+        const int2 tc = p.tiles[t];
+        for (int kb = 0; kb < p.k_blocks; ++kb) {
+          if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full_bar(s), kStageBytes);
+          const uint32_t base = smem_u32(stages + s * kStageBytes);
+          tma_load_2d(base, &tmAh, kb * kKElems, tc.x, full_bar(s));
+          tma_load_2d(base + kABytes, &tmAl, kb * kKElems, tc.x, full_bar(s));
+          tma_load_2d(base + 2 * kABytes, &tmBh, kb * kKElems, tc.y, full_bar(s));
+          tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, tc.y, full_bar(s));
+          last_parity[s] = static_cast<int>(ph);
+          if (++s == kStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        for (int q = 0; q < kStages; ++q)
+          if (last_parity[q] >= 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(full_bar(q), static_cast<uint32_t>(last_parity[q])) &&
+                   globaltimer_ns() - t0 < kWaitLimitNs) {
+            }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+      if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + acc * kBN;
+      for (int kb = 0; kb < p.k_blocks; ++kb) {
+        if (!wait_bounded(full_bar(s), ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t ah = smem_u32(stages + s * kStageBytes);
+          const uint32_t al = ah + kABytes, bh = ah + 2 * kABytes, bl = bh + kBBytes;
+#pragma unroll
+          for (int k = 0; k < kKElems / kKStep; ++k) {
+            const uint32_t off = 32 * k;
+            const uint32_t first = (kb | k) == 0 ? 0u : 1u;
+            if (TF32) {
+              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), p.idesc, first);
+              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), p.idesc, 1u);
+              mma_tf32(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), p.idesc, 1u);
+            } else {
+              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), p.idesc, first);
+              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), p.idesc, 1u);
+              mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), p.idesc, 1u);
+            }
+          }
+          mma_commit(empty_bar(s));
+        }
+        __syncwarp();
+        if (++s == kStages) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(tfull_bar(acc));
+      __syncwarp();
+      acc ^= 1u;
+      if (acc == 0) acc_ph ^= 1u;
+    }
+    if (!ok && lane == 0) {
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+    __syncwarp();
+  } else {
+    const int ew = warp & 3;
+    float* S = reinterpret_cast<float*>(epi + ew * kEpiWarpBytes);
+    float* YB = S + 32 * kSW;
+    uint32_t acc = 0, acc_ph = 0;
+    unsigned amax_bits = 0;
+    float lam = 0.f;
+    if (EPI == EPI_FINAL) lam = static_cast<float>(p.ep.st->lambda);
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+      const int2 tc = p.tiles[t];
+      if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
+      tc_fence_after();
+      const int r0 = tc.x + 32 * ew;
+      const int ch_begin = max(0, (r0 - tc.y) >> 5);
+      const int ch_end = r0 < p.n ? min(kBN / 32, (p.n - tc.y + 31) >> 5) : ch_begin;
+#pragma unroll 1
+      for (int ch = ch_begin; ch < ch_end; ++ch) {
+        uint32_t v[32];
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
+        epilogue_chunk_x3<TF32, EPI, OUT>(p, r0, tc.y + 32 * ch, v, S, YB, lane, lam, amax_bits);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      acc ^= 1u;
+      if (acc == 0) acc_ph ^= 1u;
+    }
+    if (p.ep.absmax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
+      if (lane == 0 && amax_bits) atomicMax(p.ep.absmax, amax_bits);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag && p.ep.status) atomicCAS(p.ep.status, 0, PSD_ERR_TIMEOUT);
+}
+
+using KernelX3 = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
+                          const GemmParams);
+
+template <bool TF32>
+KernelX3 pick(int epi, int out) {
+  if (epi == EPI_FINAL) return symgemm_x3_kernel<TF32, EPI_FINAL, 2>;
+  if (out == 1) {
+    if (epi == EPI_COPY) return symgemm_x3_kernel<TF32, EPI_COPY, 1>;
+    if (epi == EPI_POLY) return symgemm_x3_kernel<TF32, EPI_POLY, 1>;
+    return symgemm_x3_kernel<TF32, EPI_SCALE, 1>;
+  }
+  if (epi == EPI_COPY) return symgemm_x3_kernel<TF32, EPI_COPY, 0>;
+  if (epi == EPI_POLY) return symgemm_x3_kernel<TF32, EPI_POLY, 0>;
+  return symgemm_x3_kernel<TF32, EPI_SCALE, 0>;
+}
+
+}  // namespace
+
+// tm: A_hi, A_lo, B_hi, B_lo.  out: 0 = split pair, 1 = FP16 (EPI_FINAL: FP32 to args->out).
+cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm, const GemmParams& p, int grid,
+                              cudaStream_t stream) {
+  if (p.num_tiles == 0) return cudaSuccess;
+  KernelX3 k = tf32 ? pick<true>(epi, out) : pick<false>(epi, out);
+  const int smem = smem_bytes_x3();
+  static KernelX3 done[32];
+  static int ndone = 0;
+  bool set = false;
+  for (int i = 0; i < ndone; ++i) set = set || done[i] == k;
+  if (!set) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (ndone < 32) done[ndone++] = k;
+  }
+  GemmParams q = p;
+  const uint32_t fmt = tf32 ? 2u : 1u;
+  q.idesc = make_idesc(fmt, kBM, kBN);
+  const int g = std::max(1, std::min(grid, p.num_tiles));
+  k<<<g, kThreads, smem, stream>>>(tm[0], tm[1], tm[2], tm[3], q);
+  return cudaGetLastError();
+}
+
+}  // namespace psd
