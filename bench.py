@@ -36,9 +36,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=10000)
-    ap.add_argument("--precision", default="fp16")
+    ap.add_argument("--precision", default="mixed",
+                    help="mixed (BF16x3 early stages + FP16, meets rel err <= 1e-3), fp16, bf16, fp32")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the full-size accuracy check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-fp32-path", action="store_true", help="skip timing the FP32 comparator path")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     return ap.parse_args()
 
 
@@ -233,7 +236,7 @@ def run_ours(args):
 
     # end to end through the public call: pinned host X -> device, project, result -> pinned host
     out_h = torch.empty_like(Xh).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
     torch.cuda.synchronize(dev)
     barrier()
     ev0.record(s)
@@ -244,33 +247,53 @@ def run_ours(args):
     ev1.record(s)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_ms = ev0.elapsed_time(ev1) / e2e_steps
-    if world > 1:
+    e2e_ms = ev0.elapsed_time(ev1) / e2e_steps if e2e_steps else None
+    if world > 1 and e2e_ms is not None:
         t = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
-    # dominant kernel: the symmetric tensor-core product, same kernel and shape as in the chain
+    # dominant kernel: the symmetric tensor-core product of the chain, same kernel and shape
+    # (mixed: the BF16x3 split product of stages 1-3; fp16/bf16: the 16-bit product;
+    #  fp32: the TF32x3 split product), timed alone with CUDA events on the launching stream
     ld = (n + 63) // 64 * 64
-    g16 = torch.float16 if prec != "bf16" else torch.bfloat16
-    A = (torch.randn(n, ld, device=dev) / math.sqrt(n)).to(g16)
+    kprec = {"mixed": "mixed", "fp32": "fp32", "bf16": "bf16"}.get(prec, "fp16")
+    parts, et = {"mixed": (2, torch.bfloat16), "fp32": (2, torch.float32),
+                 "bf16": (1, torch.bfloat16)}.get(prec, (1, torch.float16))
+    A = (torch.randn(parts, n, ld, device=dev) / math.sqrt(n)).to(et)
+    if parts == 2:
+        A[1].mul_(1.0 / 256)
     C = torch.empty_like(A)
-    gprec = "bf16" if prec == "bf16" else "fp16"
     for _ in range(3):
-        b.psd_symm_product(n, A, A, ld, C, 0, gprec, 0, stream=s)
-    reps = 20
+        b.psd_symm_product(n, A, A, ld, C, 0, kprec, 0, stream=s)
+    reps = 20 if parts == 1 else 8
     ev0.record(s)
     for _ in range(reps):
-        b.psd_symm_product(n, A, A, ld, C, 0, gprec, 0, stream=s)
+        b.psd_symm_product(n, A, A, ld, C, 0, kprec, 0, stream=s)
     ev1.record(s)
     torch.cuda.synchronize(dev)
     gemm_ms = ev0.elapsed_time(ev1) / reps
     del A, C
     peaks, peak_src = measured_peaks()
-    alg_flops = n ** 3 * (1 + 256 / n)  # symmetric product, 256-wide tiles: n^3 (1 + b/n)
+    products = 3 if parts == 2 else 1  # the split product runs three tensor-core products
+    alg_flops = products * n ** 3 * (1 + 256 / n)  # symmetric product, 256-wide tiles: n^3 (1 + b/n)
     achieved = alg_flops / (gemm_ms * 1e-3) / 1e12
-    peak = peaks["bf16_tflops"]
+    # dense peaks: bf16/fp16 measured; tf32 nominally half of that rate
+    peak = peaks["bf16_tflops"] * (0.5 if prec == "fp32" else 1.0)
 
+    # the comparator of the metric: the same library's FP32 path on the same matrix
+    fp32_ms = None
+    if prec != "fp32" and not args.no_fp32_path:
+        for _ in range(2):
+            b.psd_project(n, Xd, n, out, "fp32", s)
+        k32 = max(1, min(args.steps, 5))
+        torch.cuda.synchronize(dev)
+        ev0.record(s)
+        for _ in range(k32):
+            b.psd_project(n, Xd, n, out, "fp32", s)
+        ev1.record(s)
+        torch.cuda.synchronize(dev)
+        fp32_ms = ev0.elapsed_time(ev1) / k32
     acc = None
     if rank == 0 and not args.no_accuracy:
         acc = accuracy_check(n, prec, dev)
@@ -290,12 +313,17 @@ def run_ours(args):
                              % (b.psd_workspace_size(n, prec) // 2 ** 20)},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "symgemm16 (one symmetric product, %s, timed alone: %.4f ms)" % (gprec, gemm_ms),
-                         "peak_source": "%s bf16 burst (MEASURED_PEAKS.json)" % peak_src,
+                         "kernel": "%s symmetric product (%d tensor-core product%s per launch), timed alone: %.4f ms"
+                                   % (kprec, products, "s" if products > 1 else "", gemm_ms),
+                         "peak_source": "%s bf16 burst (MEASURED_PEAKS.json)%s"
+                                        % (peak_src, ", x0.5 nominal tf32/bf16 ratio" if prec == "fp32" else ""),
                          "algorithmic_flops_per_launch": alg_flops},
-            "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": n * n * 4,
-                    "d2h_bytes_per_step": n * n * 4},
+            "e2e": None if e2e_ms is None else {"value": e2e_ms / world, "unit": "ms",
+                                                "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": n * n * 4},
             "gpu_launches": launches * args.steps,
+            "fp32_path": None if fp32_ms is None else {
+                "ms": fp32_ms, "speedup": fp32_ms / ms_step,
+                "what": "same library, precision fp32 (TF32x3 products, f~*_single, 31 products), same matrix"},
             "clocks": clocks,
             "cpu_baseline": cpu,
             "accuracy": acc,

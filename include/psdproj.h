@@ -138,13 +138,18 @@ psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
                                  psd_precision_t precision, psd_stream_t stream);
 
 /* ---- Building block exposed for tests and users ------------------------- */
-/* Symmetric product C = epi(A * B) of two n x n symmetric 16-bit matrices
- * (A, B, C share the leading dimension ld, a multiple of 8; pointers 16-byte
- * aligned; FP16 or BF16 by `precision`).  Only the upper tiles of A * B are
- * formed on the tensor cores and mirrored, so C is exactly symmetric.
- *   epi 0: C = A B                       (16-bit out)
- *   epi 1: C = a I + b Y + c A B          (16-bit out, Y = aux, ld)
- *   epi 2: C = (A B) * s                  (16-bit out)
+/* Symmetric product C = epi(A * B) of two n x n symmetric matrices in the
+ * chain's storage (A, B, C share the leading dimension ld, a multiple of 8;
+ * pointers 16-byte aligned).  Only the upper tiles of A * B are formed on the
+ * tensor cores and mirrored, so C is exactly symmetric.
+ *   precision FP16 / BF16: single 16-bit matrices;
+ *   precision MIXED: BF16 pairs, precision FP32: TF32 pairs (FP32 containers):
+ *     every operand (A, B, C, Y) is two matrices stored back to back, hi at
+ *     M and lo at M + n*ld elements, value = hi + lo; the product is
+ *     A_hi B_hi + A_hi B_lo + A_lo B_hi in one FP32 accumulator.
+ *   epi 0: C = A B
+ *   epi 1: C = a I + b Y + c A B          (Y = aux, same storage and ld)
+ *   epi 2: C = (A B) * s
  *   epi 3: C = (Xf + lam * A B) / 2       (FP32 out with leading dim ld_out,
  *                                          Xf = aux FP32 upper triangle, ld_aux)
  * params: {a, b, c} for epi 1, {s} for epi 2, {lam} for epi 3.

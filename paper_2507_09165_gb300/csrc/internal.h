@@ -94,7 +94,8 @@ struct LanczosBufs {
   int64_t n, npad;
   int nb;                // 128-blocks
   int ntiles;            // symv tiles nb (nb + 1) / 2
-  int nvec_ctas;         // CTAs of the vector kernels
+  int nvec_ctas;         // CTAs of the vector kernels (kVecThreads elements each)
+  int npart;             // CTAs of the partial-sum reductions (32 elements each)
   double* Qv;            // (kMaxSteps + 1) x npad Lanczos vectors
   double* u;             // npad
   double* w;             // npad
@@ -103,9 +104,9 @@ struct LanczosBufs {
   float* vl;             // npad  lo part
   float2* P1;            // nb x npad row partials
   float2* P2;            // nb x npad column partials
-  double* dots;          // nvec_ctas x 32 partial dot products
+  double* dots;          // npart x 32 partial dot products
   double* dots2;         // nvec_ctas x 32
-  double* norms;         // nvec_ctas
+  double* norms;         // npart (>= nvec_ctas)
   double* tile_fro;      // ntiles
 };
 size_t lanczos_bytes(int64_t n);

@@ -14,13 +14,13 @@
 // adds its rows' dot products (X(i,j) v_j, i <= j) and its columns' dot
 // products (X(i,j) v_i, i < j) into per-tile partial sums, reduced afterwards
 // in a fixed order (deterministic).  GB300's FP64 pipe is narrow, so the
-// element-level arithmetic uses the error-free transformations of Ogita,
-// Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005,
-// algorithm Dot2: TwoProduct by FMA, TwoSum) in FP32, which returns the dot
-// product as accurately as if it were computed in twice the working precision;
-// v enters as an FP64 value split into two FP32 parts.  Partial sums cross to
-// FP64 per tile row/column; every reduction over the vector (dot products,
-// norms) is FP64 with a fixed order.
+// element level runs in FP32: each thread forms 8-term FP32 FMA sums, which
+// are combined exactly into double-float (FP32 pair) partial sums with the
+// TwoSum error-free transformation (Knuth; Ogita, Rump & Oishi, "Accurate sum
+// and dot product", SIAM J. Sci. Comput. 2005), converted to FP64 per vector
+// element.  A mat-vec is thus accurate to a few FP32 roundings of the 8-term
+// runs (~1e-7 relative); every operation on vectors -- the recurrences, dot
+// products, re-orthogonalisation and norms -- is FP64 in a fixed order.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -43,16 +43,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float z = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
-}
-// acc += x * (vh + vl)   (Dot2 step: TwoProduct + TwoSum, error terms carried in l)
-__device__ __forceinline__ void dot2(F2& acc, float x, float vh, float vl) {
-  const float p = __fmul_rn(x, vh);
-  float e = __fmaf_rn(x, vh, -p);
-  e = __fmaf_rn(x, vl, e);
-  float s, q;
-  two_sum(acc.h, p, s, q);
-  acc.h = s;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(q, e));
 }
 __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
   float s, e;
@@ -153,77 +143,71 @@ __global__ void lanczos_norm0_kernel(int n, double* Qv, float* vh, float* vl, co
 // One tile of y = X v over the upper triangle (see file comment).  Thread
 // (tr, tc) = (lane & 15, 2 warp + lane / 16) owns rows i0 + 8 tr .. +7 and
 // columns j0 + 8 tc .. +7: each column's 128 rows are read by a half-warp as
-// 512 contiguous bytes.  STATS adds the tile's share of ||X||_F^2 and
-// max |X_ii| (first product only).
-template <bool STATS>
-__global__ void __launch_bounds__(256, 3) symv_upper_kernel(const DevArgs* __restrict__ args, int n,
-                                                         const float* __restrict__ vh,
-                                                         const float* __restrict__ vl,
-                                                         float2* __restrict__ P1, float2* __restrict__ P2,
-                                                         int64_t ps, double* __restrict__ tile_fro,
-                                                         DevState* __restrict__ st, int skip_if_done) {
-  if (skip_if_done && st->done) return;
-  __shared__ float2 red[8][kSymvTile];
-  __shared__ double fro_sh[8];
-  const float* __restrict__ X = args->X;
-  const int64_t ld = args->ld;
-  int bi, bj;
-  tile_of(blockIdx.x, bi, bj);
+// 512 contiguous bytes.  DIAG tiles mask to i <= j (rows) and i < j
+// (columns).  STATS adds the tile's share of ||X||_F^2 and max |X_ii|.
+template <bool STATS, bool DIAG>
+__device__ __forceinline__ void symv_tile(const float* __restrict__ X, int64_t ld, int n, int bi, int bj,
+                                          const float* __restrict__ vh, float2* __restrict__ P1,
+                                          float2* __restrict__ P2, int64_t ps, double* __restrict__ tile_fro,
+                                          DevState* __restrict__ st, float2 (*red)[kSymvTile], double* fro_sh) {
   const int i0 = bi * kSymvTile, j0 = bj * kSymvTile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tr = lane & 15, tcol = 2 * warp + (lane >> 4);
   const int ib = i0 + 8 * tr;
   const int jb = j0 + 8 * tcol;
-  const bool diag = bi == bj;
-
-  float vih[8], vil[8];
+  const bool full = (ib + 7 < n) && (jb + 7 < n);
+  const bool vec = full && ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  float vi[8], vj[8], x[8][8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const int i = ib + k;
-    vih[k] = i < n ? vh[i] : 0.f;
-    vil[k] = i < n ? vl[i] : 0.f;
+    vi[k] = (ib + k < n) ? __ldg(vh + ib + k) : 0.f;
+    vj[k] = (jb + k < n) ? __ldg(vh + jb + k) : 0.f;
   }
-  F2 rs[8], cs[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) rs[k] = cs[k] = F2{0.f, 0.f};
-  F2 fro{0.f, 0.f};
-  unsigned mdiag = 0;
-  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ib + 7 < n);
+  // all 64 elements first: 16 independent 16-byte loads in flight per thread
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int j = jb + c;
-    if (j >= n) continue;
-    const float* col = X + static_cast<int64_t>(j) * ld + ib;
-    float x[8];
+    const float* col = X + static_cast<int64_t>(jb + c) * ld + ib;
     if (vec) {
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(col));
       const float4 b4 = __ldg(reinterpret_cast<const float4*>(col + 4));
-      x[0] = a4.x; x[1] = a4.y; x[2] = a4.z; x[3] = a4.w;
-      x[4] = b4.x; x[5] = b4.y; x[6] = b4.z; x[7] = b4.w;
+      x[c][0] = a4.x; x[c][1] = a4.y; x[c][2] = a4.z; x[c][3] = a4.w;
+      x[c][4] = b4.x; x[c][5] = b4.y; x[c][6] = b4.z; x[c][7] = b4.w;
     } else {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) x[k] = (ib + k < n) ? __ldg(col + k) : 0.f;
-    }
-    const float vjh = vh[j], vjl = vl[j];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = ib + k;
-      const bool up = (!diag || i <= j) && i < n;
-      const bool strict = (!diag || i < j) && i < n;
-      const float xu = up ? x[k] : 0.f;
-      dot2(rs[k], xu, vjh, vjl);
-      if (strict) dot2(cs[c], x[k], vih[k], vil[k]);
-      if (STATS) {
-        dot2(fro, xu, strict ? 2.f * xu : xu, 0.f);
-        if (diag && i == j) mdiag = max(mdiag, __float_as_uint(fabsf(x[k])));
-      }
+      for (int k = 0; k < 8; ++k) x[c][k] = (jb + c < n && ib + k < n) ? __ldg(col + k) : 0.f;
     }
   }
-  // rows: the two column groups of a warp, then the 8 warps through shared memory
+  float rsum[8], csum[8];
+  float fro = 0.f;
+  unsigned mdiag = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) rsum[k] = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    csum[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float xr = x[c][k], xc = x[c][k];
+      if (DIAG) {
+        const int i = ib + k, j = jb + c;
+        xr = (i <= j) ? xr : 0.f;
+        xc = (i < j) ? xc : 0.f;
+        if (STATS && i == j && i < n) mdiag = max(mdiag, __float_as_uint(fabsf(x[c][k])));
+      }
+      rsum[k] = fmaf(xr, vj[c], rsum[k]);
+      csum[c] = fmaf(xc, vi[k], csum[c]);
+      if (STATS) fro = fmaf(xr, xc + xr, fro);  // x^2 on the diagonal, 2 x^2 above it
+    }
+  }
+  // rows: the two column groups of a warp (exact TwoSum), then the 8 warps
+  F2 rs[8], cs[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const F2 o = shfl_xor_f2(rs[k], 16);
-    rs[k] = (lane < 16) ? f2_add(rs[k], o) : f2_add(o, rs[k]);
+    const float o = __shfl_xor_sync(0xffffffffu, rsum[k], 16);
+    float h, e;
+    if (lane < 16) two_sum(rsum[k], o, h, e); else two_sum(o, rsum[k], h, e);
+    rs[k] = F2{h, e};
+    cs[k] = F2{csum[k], 0.f};
   }
   if (lane < 16) {
 #pragma unroll
@@ -255,7 +239,7 @@ __global__ void __launch_bounds__(256, 3) symv_upper_kernel(const DevArgs* __res
     if (i0 + r < n) P1[static_cast<int64_t>(bj) * ps + i0 + r] = make_float2(a.h, a.l);
   }
   if (STATS) {
-    double f = f2_to_d(fro);
+    double f = static_cast<double>(fro);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
     if (lane == 0) fro_sh[warp] = f;
@@ -271,6 +255,25 @@ __global__ void __launch_bounds__(256, 3) symv_upper_kernel(const DevArgs* __res
   }
 }
 
+template <bool STATS>
+__global__ void __launch_bounds__(256, 2) symv_upper_kernel(const DevArgs* __restrict__ args, int n,
+                                                            const float* __restrict__ vh,
+                                                            const float* __restrict__ vl,
+                                                            float2* __restrict__ P1, float2* __restrict__ P2,
+                                                            int64_t ps, double* __restrict__ tile_fro,
+                                                            DevState* __restrict__ st, int skip_if_done) {
+  if (skip_if_done && st->done) return;
+  __shared__ float2 red[8][kSymvTile];
+  __shared__ double fro_sh[8];
+  (void)vl;
+  int bi, bj;
+  tile_of(blockIdx.x, bi, bj);
+  if (bi == bj)
+    symv_tile<STATS, true>(args->X, args->ld, n, bi, bj, vh, P1, P2, ps, tile_fro, st, red, fro_sh);
+  else
+    symv_tile<STATS, false>(args->X, args->ld, n, bi, bj, vh, P1, P2, ps, tile_fro, st, red, fro_sh);
+}
+
 // ||X||_F from the per-tile sums of the first product (one warp, fixed order).
 __global__ void fro_kernel(const double* tile_fro, int ntiles, DevState* st) {
   double f = 0.0;
@@ -280,55 +283,55 @@ __global__ void fro_kernel(const double* tile_fro, int ntiles, DevState* st) {
   if (threadIdx.x == 0) st->fro = sqrt(f);
 }
 
-// y_e = sum_{bj >= b(e)} P1[bj][e] + sum_{bi <= b(e)} P2[bi][e] in double-float,
-// four interleaved accumulators (loads in flight), combined in a fixed order.
-__device__ __forceinline__ double reduce_partials(int e, int nb, const float2* __restrict__ P1,
-                                                  const float2* __restrict__ P2, int64_t ps) {
-  const int b = e / kSymvTile;
-  F2 a[4] = {F2{0.f, 0.f}, F2{0.f, 0.f}, F2{0.f, 0.f}, F2{0.f, 0.f}};
-  int q = 0;
-  auto take = [&](const float2* P, int blk) {
-    const float2 t = __ldg(P + static_cast<int64_t>(blk) * ps + e);
-    a[q & 3] = f2_add(a[q & 3], F2{t.x, t.y});
-    ++q;
-  };
-  int bj = b;
-  for (; bj + 3 < nb; bj += 4) {
-    const float2 t0 = __ldg(P1 + static_cast<int64_t>(bj) * ps + e);
-    const float2 t1 = __ldg(P1 + static_cast<int64_t>(bj + 1) * ps + e);
-    const float2 t2 = __ldg(P1 + static_cast<int64_t>(bj + 2) * ps + e);
-    const float2 t3 = __ldg(P1 + static_cast<int64_t>(bj + 3) * ps + e);
-    a[0] = f2_add(a[0], F2{t0.x, t0.y});
-    a[1] = f2_add(a[1], F2{t1.x, t1.y});
-    a[2] = f2_add(a[2], F2{t2.x, t2.y});
-    a[3] = f2_add(a[3], F2{t3.x, t3.y});
+// y_e = sum_{bj >= b(e)} P1[bj][e] + sum_{bi <= b(e)} P2[bi][e] for the 32
+// elements e of this CTA (kRedThreads threads): warp w adds the blocks
+// congruent to w mod 8 in double-float, then warp 0 combines the 8 warp sums
+// in a fixed order.  Returns y_e (FP64) in warp 0; other warps return 0.
+constexpr int kRedThreads = 256;
+__device__ __forceinline__ double reduce_partials_cta(int n, int nb, const float2* __restrict__ P1,
+                                                      const float2* __restrict__ P2, int64_t ps, float2 (*sh)[32]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  F2 a{0.f, 0.f}, c{0.f, 0.f};
+  if (e < n) {
+    const int b = e / kSymvTile;
+#pragma unroll 4
+    for (int bj = b + w; bj < nb; bj += 8) {
+      const float2 t = __ldg(P1 + static_cast<int64_t>(bj) * ps + e);
+      a = f2_add(a, F2{t.x, t.y});
+    }
+#pragma unroll 4
+    for (int bi = w; bi <= b; bi += 8) {
+      const float2 t = __ldg(P2 + static_cast<int64_t>(bi) * ps + e);
+      c = f2_add(c, F2{t.x, t.y});
+    }
   }
-  for (; bj < nb; ++bj) take(P1, bj);
-  int bi = 0;
-  for (; bi + 3 <= b; bi += 4) {
-    const float2 t0 = __ldg(P2 + static_cast<int64_t>(bi) * ps + e);
-    const float2 t1 = __ldg(P2 + static_cast<int64_t>(bi + 1) * ps + e);
-    const float2 t2 = __ldg(P2 + static_cast<int64_t>(bi + 2) * ps + e);
-    const float2 t3 = __ldg(P2 + static_cast<int64_t>(bi + 3) * ps + e);
-    a[0] = f2_add(a[0], F2{t0.x, t0.y});
-    a[1] = f2_add(a[1], F2{t1.x, t1.y});
-    a[2] = f2_add(a[2], F2{t2.x, t2.y});
-    a[3] = f2_add(a[3], F2{t3.x, t3.y});
+  const F2 t = f2_add(a, c);
+  sh[w][lane] = make_float2(t.h, t.l);
+  __syncthreads();
+  double y = 0.0;
+  if (w == 0) {
+    F2 acc{sh[0][lane].x, sh[0][lane].y};
+#pragma unroll
+    for (int q = 1; q < kRedThreads / 32; ++q) acc = f2_add(acc, F2{sh[q][lane].x, sh[q][lane].y});
+    y = f2_to_d(acc);
   }
-  for (; bi <= b; ++bi) take(P2, bi);
-  return f2_to_d(f2_add(f2_add(a[0], a[1]), f2_add(a[2], a[3])));
+  return y;
 }
 
 // u = X v (first product of X (X v)); split u for the second product.
-__global__ void reduce_split_kernel(int n, int nb, const float2* P1, const float2* P2, int64_t ps,
-                                    double* u, float* vh, float* vl, const DevState* st,
-                                    int skip_if_done) {
+__global__ void __launch_bounds__(kRedThreads) reduce_split_kernel(int n, int nb, const float2* P1,
+                                                                   const float2* P2, int64_t ps, double* u,
+                                                                   float* vh, float* vl, const DevState* st,
+                                                                   int skip_if_done) {
   if (skip_if_done && st->done) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const double y = reduce_partials(e, nb, P1, P2, ps);
-  u[e] = y;
-  split_d(y, vh[e], vl[e]);
+  __shared__ float2 sh[kRedThreads / 32][32];
+  const double y = reduce_partials_cta(n, nb, P1, P2, ps, sh);
+  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (threadIdx.x < 32 && e < n) {
+    u[e] = y;
+    split_d(y, vh[e], vl[e]);
+  }
 }
 
 // Recursive-halving sum of cnt (<= 32) FP64 values over a warp; on return
@@ -348,30 +351,22 @@ __device__ __forceinline__ double warp_multi_sum(double (&v)[32], int lane) {
   return v[0];
 }
 
-// w = X u; partial dots h_k = q_k . w (k = 0..j) per CTA.
-__global__ void reduce_dots_kernel(int n, int nb, const float2* P1, const float2* P2, int64_t ps,
-                                   double* w, const double* Qv, int64_t npad, int j, double* dots,
-                                   const DevState* st) {
+// w = X u; partial dots h_k = q_k . w (k = 0..j) over this CTA's 32 elements.
+__global__ void __launch_bounds__(kRedThreads) reduce_dots_kernel(int n, int nb, const float2* P1,
+                                                                  const float2* P2, int64_t ps, double* w,
+                                                                  const double* Qv, int64_t npad, int j,
+                                                                  double* dots, const DevState* st) {
   if (st->done) return;
-  __shared__ double sh[kVecThreads / 32][32];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  double y = 0.0;
-  if (e < n) {
-    y = reduce_partials(e, nb, P1, P2, ps);
-    w[e] = y;
-  }
+  __shared__ float2 sh[kRedThreads / 32][32];
+  const double y = reduce_partials_cta(n, nb, P1, P2, ps, sh);
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const int e = blockIdx.x * 32 + lane;
+  if (e < n) w[e] = y;
   double v[32];
 #pragma unroll
   for (int k = 0; k < 32; ++k) v[k] = (k <= j && e < n) ? Qv[static_cast<int64_t>(k) * npad + e] * y : 0.0;
-  const double s = warp_multi_sum(v, lane);
-  sh[wp][lane] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int q = 0; q < kVecThreads / 32; ++q) t += sh[q][threadIdx.x];
-    dots[blockIdx.x * 32 + threadIdx.x] = t;
-  }
+  dots[blockIdx.x * 32 + lane] = warp_multi_sum(v, lane);
 }
 
 // Classical Gram-Schmidt pass: h = sum over CTAs of the partial dots (same
@@ -619,14 +614,19 @@ __global__ void ritz_norm_kernel(int n, double* q, const double* norms, int ncta
   }
 }
 
-// r = X (X q) - sigma q, partial ||r||^2.
-__global__ void resid_kernel(int n, int nb, const float2* P1, const float2* P2, int64_t ps, const double* q,
-                             double* norms, const DevState* st) {
-  __shared__ double sh[kVecThreads / 32];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+// r = X (X q) - sigma q, partial ||r||^2 over this CTA's 32 elements.
+__global__ void __launch_bounds__(kRedThreads) resid_kernel(int n, int nb, const float2* P1, const float2* P2,
+                                                            int64_t ps, const double* q, double* norms,
+                                                            const DevState* st) {
+  __shared__ float2 sh[kRedThreads / 32][32];
+  const double y = reduce_partials_cta(n, nb, P1, P2, ps, sh);
+  if (threadIdx.x >= 32) return;
+  const int e = blockIdx.x * 32 + threadIdx.x;
   double r = 0.0;
-  if (e < n) r = reduce_partials(e, nb, P1, P2, ps) - st->sigma * q[e];
-  const double t = block_sum64(r * r, sh);
+  if (e < n) r = y - st->sigma * q[e];
+  double t = r * r;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   if (threadIdx.x == 0) norms[blockIdx.x] = t;
 }
 
@@ -825,14 +825,16 @@ size_t lanczos_bytes(int64_t n) {
   const int64_t nb = (n + kSymvTile - 1) / kSymvTile;
   const int64_t ntiles = nb * (nb + 1) / 2;
   const int64_t nctas = (n + kVecThreads - 1) / kVecThreads;
+  const int64_t npart = (n + 31) / 32;
   size_t b = 0;
   auto add = [&](size_t bytes) { b += (bytes + 255) / 256 * 256; };
   add(sizeof(double) * (kMaxSteps + 1) * npad);  // Qv
   add(sizeof(double) * npad * 3);                // u, w, q
   add(sizeof(float) * npad * 2);                 // vh, vl
   add(sizeof(float2) * nb * npad * 2);           // P1, P2
-  add(sizeof(double) * nctas * 32 * 2);          // dots, dots2
-  add(sizeof(double) * nctas);                   // norms
+  add(sizeof(double) * npart * 32);              // dots
+  add(sizeof(double) * nctas * 32);              // dots2
+  add(sizeof(double) * npart);                   // norms
   add(sizeof(double) * ntiles);                  // tile_fro
   return b;
 }
@@ -843,6 +845,7 @@ void lanczos_carve(LanczosBufs& L, int64_t n, uint8_t* base) {
   L.nb = static_cast<int>((n + kSymvTile - 1) / kSymvTile);
   L.ntiles = L.nb * (L.nb + 1) / 2;
   L.nvec_ctas = static_cast<int>((n + kVecThreads - 1) / kVecThreads);
+  L.npart = static_cast<int>((n + 31) / 32);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     uint8_t* p = base + off;
@@ -860,16 +863,15 @@ void lanczos_carve(LanczosBufs& L, int64_t n, uint8_t* base) {
   float2* P = reinterpret_cast<float2*>(take(sizeof(float2) * L.nb * L.npad * 2));
   L.P1 = P;
   L.P2 = P + static_cast<int64_t>(L.nb) * L.npad;
-  double* d2 = reinterpret_cast<double*>(take(sizeof(double) * L.nvec_ctas * 32 * 2));
-  L.dots = d2;
-  L.dots2 = d2 + L.nvec_ctas * 32;
-  L.norms = reinterpret_cast<double*>(take(sizeof(double) * L.nvec_ctas));
+  L.dots = reinterpret_cast<double*>(take(sizeof(double) * L.npart * 32));
+  L.dots2 = reinterpret_cast<double*>(take(sizeof(double) * L.nvec_ctas * 32));
+  L.norms = reinterpret_cast<double*>(take(sizeof(double) * L.npart));
   L.tile_fro = reinterpret_cast<double*>(take(sizeof(double) * L.ntiles));
 }
 
 cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevState* st, cudaStream_t s) {
   const int n = static_cast<int>(L.n);
-  const int vb = L.nvec_ctas, vt = kVecThreads;
+  const int vb = L.nvec_ctas, vt = kVecThreads, rb = L.npart, rt = kRedThreads;
   const int64_t ps = L.npad;
   lanczos_init_kernel<<<vb, vt, 0, s>>>(n, L.npad, L.Qv, L.vh, L.vl, st, L.norms);
   lanczos_norm0_kernel<<<vb, vt, 0, s>>>(n, L.Qv, L.vh, L.vl, L.norms, vb);
@@ -877,12 +879,13 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
     if (j == 0) {
       symv_upper_kernel<true><<<L.ntiles, 256, 0, s>>>(args, n, L.vh, L.vl, L.P1, L.P2, ps, L.tile_fro, st, 0);
       fro_kernel<<<1, 32, 0, s>>>(L.tile_fro, L.ntiles, st);
-    } else
+    } else {
       symv_upper_kernel<false><<<L.ntiles, 256, 0, s>>>(args, n, L.vh, L.vl, L.P1, L.P2, ps, L.tile_fro, st, 1);
-    reduce_split_kernel<<<vb, vt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.u, L.vh, L.vl, st, 1);
+    }
+    reduce_split_kernel<<<rb, rt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.u, L.vh, L.vl, st, 1);
     symv_upper_kernel<false><<<L.ntiles, 256, 0, s>>>(args, n, L.vh, L.vl, L.P1, L.P2, ps, L.tile_fro, st, 1);
-    reduce_dots_kernel<<<vb, vt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.w, L.Qv, L.npad, j, L.dots, st);
-    orth_kernel<1><<<vb, vt, 0, s>>>(n, L.w, L.Qv, L.npad, j, L.dots, vb, L.dots2, st);
+    reduce_dots_kernel<<<rb, rt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.w, L.Qv, L.npad, j, L.dots, st);
+    orth_kernel<1><<<vb, vt, 0, s>>>(n, L.w, L.Qv, L.npad, j, L.dots, rb, L.dots2, st);
     orth_kernel<2><<<vb, vt, 0, s>>>(n, L.w, L.Qv, L.npad, j, L.dots2, vb, L.norms, st);
     lanczos_next_kernel<<<vb, vt, 0, s>>>(n, L.w, L.Qv, L.npad, j, L.norms, vb, L.vh, L.vl, st);
   }
@@ -890,10 +893,10 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
   ritz_kernel<<<vb, vt, 0, s>>>(n, L.Qv, L.npad, L.q, L.norms, st);
   ritz_norm_kernel<<<vb, vt, 0, s>>>(n, L.q, L.norms, vb, L.vh, L.vl);
   symv_upper_kernel<false><<<L.ntiles, 256, 0, s>>>(args, n, L.vh, L.vl, L.P1, L.P2, ps, L.tile_fro, st, 0);
-  reduce_split_kernel<<<vb, vt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.u, L.vh, L.vl, st, 0);
+  reduce_split_kernel<<<rb, rt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.u, L.vh, L.vl, st, 0);
   symv_upper_kernel<false><<<L.ntiles, 256, 0, s>>>(args, n, L.vh, L.vl, L.P1, L.P2, ps, L.tile_fro, st, 0);
-  resid_kernel<<<vb, vt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.q, L.norms, st);
-  bound_final_kernel<<<1, 32, 0, s>>>(n, L.norms, vb, st, args);
+  resid_kernel<<<rb, rt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.q, L.norms, st);
+  bound_final_kernel<<<1, 32, 0, s>>>(n, L.norms, rb, st, args);
   return cudaGetLastError();
 }
 

@@ -522,12 +522,15 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
                               psd_precision_t precision, int32_t epi, const double* params, const void* aux,
                               int64_t ld_aux, float* d_absmax, psd_stream_t stream) {
   if (n <= 0 || n > kMaxOrder || !A || !B || !C || ld < n || (ld % 8) != 0) return PSD_ERR_INVALID_ARG;
-  if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16) return PSD_ERR_INVALID_ARG;
+  const bool split = precision == PSD_PREC_MIXED || precision == PSD_PREC_FP32;
+  if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16 && !split) return PSD_ERR_INVALID_ARG;
   if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;
   if ((epi == 1 || epi == 2 || epi == 3) && !params) return PSD_ERR_INVALID_ARG;
   if ((epi == 1 || epi == 3) && !aux) return PSD_ERR_INVALID_ARG;
   if (epi == 3 && (ld_aux < n || ld_out < n)) return PSD_ERR_INVALID_ARG;
-  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return PSD_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) ||
+      (reinterpret_cast<uintptr_t>(C) & 15))
+    return PSD_ERR_INVALID_ARG;
   psd_status_t st = check_device();
   if (st != PSD_OK) return st;
   int dev = 0;
@@ -552,22 +555,25 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     ps.tiles[n] = d;
     ps.ntiles[n] = static_cast<int>(tl.size());
   }
-  const int dtype = precision == PSD_PREC_BF16 ? DT_BF16 : DT_F16;
-  CUtensorMap ta, tb;
-  if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 256)) return PSD_ERR_CUDA;
+  const int dtype = precision == PSD_PREC_BF16    ? DT_BF16
+                    : precision == PSD_PREC_MIXED ? DT_BF16X3
+                    : precision == PSD_PREC_FP32  ? DT_TF32X3
+                                                  : DT_F16;
+  const size_t esz = dtype == DT_TF32X3 ? 4 : 2;
+  const size_t pair = static_cast<size_t>(n) * static_cast<size_t>(ld) * esz;  // byte offset of the lo part
   GemmParams g{};
   g.n = static_cast<int>(n);
-  g.k_blocks = static_cast<int>((n + 63) / 64);
+  g.k_blocks = static_cast<int>(dtype == DT_TF32X3 ? (n + 31) / 32 : (n + 63) / 64);
   g.num_tiles = ps.ntiles[n];
   g.tiles = ps.tiles[n];
-  const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;
-  g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (32u << 17) | (8u << 24);
   g.ep.C = C;
+  g.ep.C_lo = split ? static_cast<uint8_t*>(C) + pair : nullptr;
   g.ep.ldc = ld;
   g.ep.status = &ps.d_state->status;
   g.ep.absmax = reinterpret_cast<unsigned*>(d_absmax);
   if (epi == 1) {
     g.ep.Y = aux;
+    g.ep.Y_lo = split ? static_cast<const uint8_t*>(aux) + pair : nullptr;
     g.ep.ldy = ld;
     g.ep.a = static_cast<float>(params[0]);
     g.ep.b = static_cast<float>(params[1]);
@@ -582,7 +588,22 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     g.ep.st = ps.d_state;
     g.ep.absmax = nullptr;
   }
-  cudaError_t e = launch_symgemm(dtype, epi, ta, tb, g, num_sms(), s);
+  cudaError_t e;
+  if (!split) {
+    CUtensorMap ta, tb;
+    if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 256)) return PSD_ERR_CUDA;
+    const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;
+    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (32u << 17) | (8u << 24);
+    e = launch_symgemm(dtype, epi, ta, tb, g, num_sms(), s);
+  } else {
+    CUtensorMap tm[4];
+    const uint8_t* a8 = static_cast<const uint8_t*>(A);
+    const uint8_t* b8 = static_cast<const uint8_t*>(B);
+    if (!encode_tmap(&tm[0], dtype, a8, n, ld, 128) || !encode_tmap(&tm[1], dtype, a8 + pair, n, ld, 128) ||
+        !encode_tmap(&tm[2], dtype, b8, n, ld, 256) || !encode_tmap(&tm[3], dtype, b8 + pair, n, ld, 256))
+      return PSD_ERR_CUDA;
+    e = launch_symgemm_x3(dtype == DT_TF32X3, epi, epi == 3 ? 2 : 0, tm, g, num_sms(), s);
+  }
   return e == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
 }
 

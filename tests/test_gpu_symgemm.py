@@ -150,6 +150,59 @@ def test_product_rejects_bad_arguments():
     with pytest.raises(b.PsdError):
         b.psd_symm_product(8, A, A, 7, A, 0, "fp16", 0)  # ld not a multiple of 8
     with pytest.raises(b.PsdError):
-        b.psd_symm_product(8, A, A, 8, A, 0, "fp32", 0)  # 16-bit only
+        b.psd_symm_product(8, A, A, 8, A, 0, "fp8_early", 0)  # no product for this precision
     with pytest.raises(b.PsdError):
         b.psd_symm_product(8, A, A, 8, A, 0, "fp16", 9)  # unknown epilogue
+
+
+def split_pair(A64, prec, n, ld):
+    """(hi, lo) storage of A64 as BF16 pairs (mixed) or TF32 pairs (fp32), rows of ld elements."""
+    if prec == "mixed":
+        hi = torch.from_numpy(A64).to(torch.bfloat16)
+        lo = (torch.from_numpy(A64) - hi.double()).to(torch.bfloat16)
+        dt = torch.bfloat16
+    else:
+        a = torch.from_numpy(A64.astype(np.float32)).view(torch.int32).numpy().astype(np.int64)
+        hb = ((a + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32)
+        rem = (A64.astype(np.float32) - hb).astype(np.float32).view(np.int32).astype(np.int64)
+        lb = ((rem + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32)
+        hi, lo = torch.from_numpy(hb.copy()), torch.from_numpy(lb.copy())
+        dt = torch.float32
+    t = torch.zeros((2, n, ld), dtype=dt)
+    t[0, :, :n] = hi
+    t[1, :, :n] = lo
+    return t
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("n", [64, 255, 300, 513])
+def test_split_product(n, prec):
+    # value = hi + lo; product = A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation,
+    # output split again: BF16 pairs keep ~16 bits, TF32 pairs ~22 bits.
+    ld = (n + 7) // 8 * 8
+    rng = np.random.default_rng(n)
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    A64 = 0.5 * (G + G.T)
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    B64 = 0.5 * (G + G.T)
+    A, B = split_pair(A64, prec, n, ld), split_pair(B64, prec, n, ld)
+    dev = torch.device("cuda")
+    Ad, Bd = A.to(dev), B.to(dev)
+    Cd = torch.full_like(Ad, float("nan"))
+    b.psd_symm_product(n, Ad, Bd, ld, Cd, 0, prec, 0)
+    torch.cuda.synchronize()
+    Cc = Cd.cpu().double().numpy()
+    C = Cc[0, :, :n] + Cc[1, :, :n]
+    Av = A.double().numpy()[0, :, :n] + A.double().numpy()[1, :, :n]
+    Bv = B.double().numpy()[0, :, :n] + B.double().numpy()[1, :, :n]
+    D = Av @ Bv
+    assert np.array_equal(C, C.T)
+    # A B of two different symmetric matrices is not symmetric: the kernel forms
+    # the upper triangle and mirrors it, so compare the upper triangle
+    iu = np.triu_indices(n)
+    rel = 2.0 ** -14 if prec == "mixed" else 2.0 ** -20
+    acc = 4 * n * 2.0 ** -24 * (np.abs(Av) @ np.abs(Bv))
+    err, tol = np.abs(C - D)[iu], (rel * np.abs(D) + acc)[iu]
+    assert np.all(err <= tol), np.max(err / tol)
+    # far more accurate than one 16-bit product
+    assert np.linalg.norm(err) / np.linalg.norm(D[iu]) < (4e-5 if prec == "mixed" else 1e-6)
