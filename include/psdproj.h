@@ -116,6 +116,21 @@ psd_status_t psd_release_workspaces(void);
 psd_status_t psd_norm_bound(int64_t n, const float *X, int64_t ld, psd_info_t *d_info,
                             psd_stream_t stream);
 
+/* Norm bound that allocates nothing (no counterpart in the paper: an addition
+ * of this library).  For callers that must not allocate device memory while
+ * they run, e.g. a loop whose device memory is reserved up front by a pool,
+ * or a latency-critical loop that cannot take the implicit synchronisation of
+ * cudaMalloc.  Same computation and report as psd_norm_bound, for
+ * 1 <= n <= 4096 (larger n: PSD_ERR_INVALID_ARG); the scratch lives in a
+ * static device array of about 3 MB that every GPU loading the library holds
+ * until exit.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * (different streams) race and must not be issued; calls on one stream are
+ * ordered.  X, d_info: caller-owned device memory as in psd_norm_bound. */
+psd_status_t psd_norm_bound_noalloc(int64_t n, const float *X, int64_t ld, psd_info_t *d_info,
+                                    psd_stream_t stream);
+
 /* ---- Batched projection of a block-diagonal cone ------------------------ */
 /* One block: X, out column-major device matrices of order n (1 <= n <= 1024),
  * upper triangle of X read; info may be NULL. */

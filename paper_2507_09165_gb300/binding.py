@@ -53,6 +53,7 @@ _SIGS = {
     "psd_last_info": ([_VP, ctypes.POINTER(psd_info_t)], _I32),
     "psd_release_workspaces": ([], _I32),
     "psd_norm_bound": ([_I64, _VP, _I64, _VP, _VP], _I32),
+    "psd_norm_bound_noalloc": ([_I64, _VP, _I64, _VP, _VP], _I32),
     "psd_project_batched": ([_I32, _VP, _I32, _VP], _I32),
     "psd_symm_product": ([_I64, _VP, _VP, _I64, _VP, _I64, _I32, _I32, ctypes.POINTER(_D), _VP, _I64, _VP,
                           _VP], _I32),
@@ -139,6 +140,11 @@ def psd_release_workspaces():
 
 def psd_norm_bound(n, X, ld, d_info, stream=None):
     _check(lib().psd_norm_bound(n, _ptr(X), ld, _ptr(d_info), _stream(stream)), "psd_norm_bound")
+
+
+def psd_norm_bound_noalloc(n, X, ld, d_info, stream=None):
+    _check(lib().psd_norm_bound_noalloc(n, _ptr(X), ld, _ptr(d_info), _stream(stream)),
+           "psd_norm_bound_noalloc")
 
 
 def psd_project_batched(count, d_descs, precision="bf16", stream=None):
