@@ -152,8 +152,32 @@ def psd_project_batched(count, d_descs, precision="bf16", stream=None):
            "psd_project_batched")
 
 
+_PRODUCT_BYTES = {"fp16": (1, 2), "bf16": (1, 2), "mixed": (2, 2), "fp32": (2, 4)}
+
+
+def _check_extent(t, need, what):
+    """Refuse a tensor smaller than the bytes the C ABI will touch (raw pointers carry no size)."""
+    if hasattr(t, "numel") and hasattr(t, "element_size"):
+        have = t.numel() * t.element_size()
+        if have < need:
+            raise ValueError("%s holds %d bytes, the product needs %d" % (what, have, need))
+
+
 def psd_symm_product(n, A, B, ld, C, ld_out=0, precision="fp16", epi=0, params=(), aux=None, ld_aux=0,
                      d_absmax=None, stream=None):
+    pname = precision if isinstance(precision, str) else {v: k for k, v in PRECISION.items()}.get(precision)
+    if pname in _PRODUCT_BYTES and n > 0:
+        parts, esz = _PRODUCT_BYTES[pname]
+        need = ((parts - 1) * n * ld + (n - 1) * ld + n) * esz  # pairs: hi, then lo at + n * ld
+        _check_extent(A, need, "A")
+        _check_extent(B, need, "B")
+        if epi == 3:
+            _check_extent(C, ((n - 1) * ld_out + n) * 4, "C (FP32 output)")
+            _check_extent(aux, ((n - 1) * ld_aux + n) * 4, "aux (FP32 input)")
+        else:
+            _check_extent(C, need, "C")
+            if epi == 1:
+                _check_extent(aux, need, "aux (Y)")
     arr = (ctypes.c_double * max(1, len(params)))(*params) if params else None
     _check(lib().psd_symm_product(n, _ptr(A), _ptr(B), ld, _ptr(C), ld_out, _prec(precision), epi, arr,
                                   _ptr(aux), ld_aux, _ptr(d_absmax), _stream(stream)), "psd_symm_product")

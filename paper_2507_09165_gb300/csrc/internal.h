@@ -29,6 +29,8 @@ struct DevArgs {
   psd_info_t* info;
 };
 
+struct BlockRec;
+
 // Device-resident state of one projection.
 struct DevState {
   double alpha[kMaxSteps];
@@ -55,32 +57,48 @@ enum Epi : int { EPI_COPY = 0, EPI_POLY = 1, EPI_SCALE = 2, EPI_FINAL = 3 };
 // (FP32 containers), BF16 hi/lo pairs.
 enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_BF16X3 = 3 };
 
+// One symmetric matrix of a product launch.  A launch covers one matrix
+// (single projection) or many (block-diagonal cone, served requests); the
+// iterates of block b occupy rows off .. off + n - 1 of the stacked buffers.
+struct BlockRec {
+  int64_t off;          // first row in the stacked iterate buffers
+  int n;                // order
+  int pad;
+  const float* X;       // EPI_FINAL: caller input (upper triangle), column-major
+  int64_t ld;
+  float* out;           // EPI_FINAL: caller output
+  int64_t ld_out;
+  DevState* st;         // lam~, and the max |X_T| of the last stage
+};
+
 struct EpiParams {
-  void* C;               // 16-bit output (ld = ldc) for EPI_COPY/POLY/SCALE
+  void* C;               // output iterate (ld = ldc), hi part of a pair
   int64_t ldc;
-  void* C_lo;            // TF32x3: low parts of the output
+  void* C_lo;            // lo part of a pair output
   const void* Y;         // EPI_POLY: the stage's X^2 (same storage as C)
   const void* Y_lo;
   int64_t ldy;
   float a, b, c, s;      // EPI_POLY coefficients, EPI_SCALE factor
-  const DevArgs* args;   // EPI_FINAL: X, ld, out, ld_out
-  const DevState* st;    // EPI_FINAL: lam~
-  unsigned* absmax;      // optional: atomic max of |output|
+  int absmax_blocks;     // nonzero: atomic max of |output| into blocks[b].st->absmax_bits
+  unsigned* absmax;      // if set: atomic max of |output| into this word instead
   int* status;           // device status word for timeouts
 };
 
 struct GemmParams {
-  int n;
-  int k_blocks;
   int num_tiles;
-  const int2* tiles;     // (m0, n0) of each 128 x 256 output tile, upper triangle
-  uint32_t idesc;
+  const int4* tiles;     // (m0, n0, block, ncols) of each 128-row output tile, upper triangle
+  const BlockRec* blocks;
+  uint32_t idesc;        // instruction descriptor without its N field
   EpiParams ep;
 };
 
+// Upper-triangle tiles of one order-n matrix: 256 x 256 blocks (I <= J) split
+// into two 128-row tiles; the lower-right tile of a diagonal block starts at
+// its diagonal (128 columns); tile widths are trimmed at n (multiples of 16).
+std::vector<int4> make_tile_list(int64_t n, int block = 0);
+
 // --- host helpers (symgemm.cu) ---
 bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows);
-std::vector<int2> make_tile_list(int64_t n);
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const GemmParams& p, int grid, cudaStream_t stream);
 // split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
@@ -117,7 +135,9 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& b, const DevArgs* args, DevSta
 // additional FP16 copy (DT_BF16X3 only).
 cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n,
                                void* M, void* M_lo, void* M_f16, int64_t ldm, cudaStream_t stream);
-cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t stream);
+// Argument block of one replay (and the caller fields of a one-block record, if given).
+cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t stream, BlockRec* blk = nullptr);
+cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t stream);
 cudaError_t enqueue_state_reset(DevState* st, cudaStream_t stream);
 cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t stream);
 

@@ -798,7 +798,19 @@ __global__ void __launch_bounds__(256) scale_cast_kernel(const DevArgs* __restri
   }
 }
 
-__global__ void set_args_kernel(DevArgs* d, DevArgs h) { *d = h; }
+// Caller pointers of one replay: the argument block, and (single projection)
+// the caller-facing fields of the one block record.
+__global__ void set_args_kernel(DevArgs* d, DevArgs h, BlockRec* blk) {
+  *d = h;
+  if (blk) {
+    blk->X = h.X;
+    blk->ld = h.ld;
+    blk->out = h.out;
+    blk->ld_out = h.ld_out;
+  }
+}
+
+__global__ void set_block_kernel(BlockRec* dst, BlockRec v) { *dst = v; }
 
 // Status word and overshoot of the last stage into the report.
 __global__ void finalize_kernel(const DevArgs* args, DevState* st) {
@@ -915,8 +927,13 @@ cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* s
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t s) {
-  set_args_kernel<<<1, 1, 0, s>>>(d_args, h);
+cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t s, BlockRec* blk) {
+  set_args_kernel<<<1, 1, 0, s>>>(d_args, h, blk);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t s) {
+  set_block_kernel<<<1, 1, 0, s>>>(d_blk, v);
   return cudaGetLastError();
 }
 

@@ -133,7 +133,8 @@ struct Plan {
   DevArgs* d_args = nullptr;
   DevState* d_state = nullptr;
   psd_info_t* d_info = nullptr;  // default report
-  int2* d_tiles = nullptr;
+  BlockRec* d_block = nullptr;   // the one block of a single projection
+  int4* d_tiles = nullptr;
   int ntiles = 0;
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
@@ -177,12 +178,13 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   lanczos_carve(p->L, n, base + p->nslots * p->slot_size);
 
   // small library-owned records: args | state | info | tiles
-  std::vector<int2> tiles = make_tile_list(n);
+  std::vector<int4> tiles = make_tile_list(n);
   p->ntiles = static_cast<int>(tiles.size());
   const size_t o_state = round_up(sizeof(DevArgs), 256);
   const size_t o_info = o_state + round_up(sizeof(DevState), 256);
-  const size_t o_tiles = o_info + round_up(sizeof(psd_info_t), 256);
-  const size_t small = o_tiles + sizeof(int2) * std::max<size_t>(tiles.size(), 1);
+  const size_t o_block = o_info + round_up(sizeof(psd_info_t), 256);
+  const size_t o_tiles = o_block + round_up(sizeof(BlockRec), 256);
+  const size_t small = o_tiles + sizeof(int4) * std::max<size_t>(tiles.size(), 1);
   uint8_t* sm = nullptr;
   if (cudaMalloc(&sm, small) != cudaSuccess) {
     cudaGetLastError();
@@ -192,10 +194,16 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   p->d_args = reinterpret_cast<DevArgs*>(sm);
   p->d_state = reinterpret_cast<DevState*>(sm + o_state);
   p->d_info = reinterpret_cast<psd_info_t*>(sm + o_info);
-  p->d_tiles = reinterpret_cast<int2*>(sm + o_tiles);
+  p->d_block = reinterpret_cast<BlockRec*>(sm + o_block);
+  p->d_tiles = reinterpret_cast<int4*>(sm + o_tiles);
   if (!tiles.empty() &&
-      cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return PSD_ERR_CUDA;
+  BlockRec br{};
+  br.off = 0;
+  br.n = static_cast<int>(n);
+  br.st = p->d_state;
+  if (cudaMemcpy(p->d_block, &br, sizeof(br), cudaMemcpyHostToDevice) != cudaSuccess) return PSD_ERR_CUDA;
   return PSD_OK;
 }
 
@@ -234,10 +242,9 @@ int part_dtype(const Mat& m) { return m.kind == MK_16 ? m.dt16 : m.kind == MK_BF
 
 GemmParams base_params(const Plan* p) {
   GemmParams g{};
-  g.n = static_cast<int>(p->n);
-  g.k_blocks = static_cast<int>((p->n + 63) / 64);
   g.num_tiles = p->ntiles;
   g.tiles = p->d_tiles;
+  g.blocks = p->d_block;
   g.ep.status = &p->d_state->status;
   return g;
 }
@@ -248,17 +255,12 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
                  float c, float sc, unsigned* absmax, cudaStream_t s) {
   GemmParams g = base_params(p);
   const int64_t n = p->n, ldm = p->ldm;
-  // K-blocks of 128 bytes: 64 16-bit or 32 TF32 elements
-  if (A.kind == MK_TF32X3) g.k_blocks = static_cast<int>((n + 31) / 32);
   g.ep.a = a;
   g.ep.b = b;
   g.ep.c = c;
   g.ep.s = sc;
   g.ep.absmax = absmax;
-  if (epi == EPI_FINAL) {
-    g.ep.args = p->d_args;
-    g.ep.st = p->d_state;
-  } else {
+  if (epi != EPI_FINAL) {
     g.ep.C = part_ptr(p, *out, 0);
     g.ep.C_lo = out->kind == MK_16 ? nullptr : part_ptr(p, *out, 1);
     g.ep.ldc = ldm;
@@ -275,7 +277,7 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
         !encode_tmap(&tb, B.dt16, part_ptr(p, B, 0), n, ldm, 256))
       return cudaErrorInvalidValue;
     const uint32_t fmt = A.dt16 == DT_BF16 ? 1u : 0u;
-    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (32u << 17) | (8u << 24);
+    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);  // M = 128; N per tile
     return launch_symgemm(A.dt16, epi, ta, tb, g, grid, s);
   }
   const int dt = part_dtype(A);
@@ -424,7 +426,7 @@ psd_status_t project_impl(int64_t n, const float* X, int64_t ld, float* out, int
   if (!p) return st;
   ensure_graph(p);
   DevArgs h{X, ld, out, ld_out, d_info ? d_info : p->d_info};
-  if (enqueue_set_args(p->d_args, h, stream) != cudaSuccess) return PSD_ERR_CUDA;
+  if (enqueue_set_args(p->d_args, h, stream, p->d_block) != cudaSuccess) return PSD_ERR_CUDA;
   cudaError_t e = p->exec ? cudaGraphLaunch(p->exec, stream) : enqueue_projection(p, stream);
   if (e != cudaSuccess) return PSD_ERR_CUDA;
   if (!d_info) g_last[{dev, stream}] = p;
@@ -435,7 +437,8 @@ psd_status_t project_impl(int64_t n, const float* X, int64_t ld, float* out, int
 struct ProductScratch {
   DevArgs* d_args = nullptr;
   DevState* d_state = nullptr;
-  std::map<int64_t, int2*> tiles;
+  BlockRec* d_block = nullptr;
+  std::map<int64_t, int4*> tiles;
   std::map<int64_t, int> ntiles;
 };
 std::map<int, ProductScratch> g_prod;
@@ -540,18 +543,20 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   ProductScratch& ps = g_prod[dev];
   if (!ps.d_args) {
     const size_t o_state = round_up(sizeof(DevArgs), 256);
-    const size_t bytes = o_state + round_up(sizeof(DevState), 256);
+    const size_t o_block = o_state + round_up(sizeof(DevState), 256);
+    const size_t bytes = o_block + round_up(sizeof(BlockRec), 256);
     uint8_t* sm = nullptr;
     if (cudaMalloc(&sm, bytes) != cudaSuccess) return PSD_ERR_NO_MEMORY;
     cudaMemset(sm, 0, bytes);
     ps.d_args = reinterpret_cast<DevArgs*>(sm);
     ps.d_state = reinterpret_cast<DevState*>(sm + o_state);
+    ps.d_block = reinterpret_cast<BlockRec*>(sm + o_block);
   }
   if (!ps.tiles.count(n)) {
-    std::vector<int2> tl = make_tile_list(n);
-    int2* d = nullptr;
-    if (cudaMalloc(&d, sizeof(int2) * tl.size()) != cudaSuccess) return PSD_ERR_NO_MEMORY;
-    cudaMemcpy(d, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+    std::vector<int4> tl = make_tile_list(n);
+    int4* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int4) * tl.size()) != cudaSuccess) return PSD_ERR_NO_MEMORY;
+    cudaMemcpy(d, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice);
     ps.tiles[n] = d;
     ps.ntiles[n] = static_cast<int>(tl.size());
   }
@@ -562,10 +567,9 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   const size_t esz = dtype == DT_TF32X3 ? 4 : 2;
   const size_t pair = static_cast<size_t>(n) * static_cast<size_t>(ld) * esz;  // byte offset of the lo part
   GemmParams g{};
-  g.n = static_cast<int>(n);
-  g.k_blocks = static_cast<int>(dtype == DT_TF32X3 ? (n + 31) / 32 : (n + 63) / 64);
   g.num_tiles = ps.ntiles[n];
   g.tiles = ps.tiles[n];
+  g.blocks = ps.d_block;
   g.ep.C = C;
   g.ep.C_lo = split ? static_cast<uint8_t*>(C) + pair : nullptr;
   g.ep.ldc = ld;
@@ -581,19 +585,26 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   } else if (epi == 2) {
     g.ep.s = static_cast<float>(params[0]);
   } else if (epi == 3) {
-    DevArgs h{static_cast<const float*>(aux), ld_aux, static_cast<float*>(C), ld_out, nullptr};
-    if (enqueue_set_args(ps.d_args, h, s) != cudaSuccess) return PSD_ERR_CUDA;
     set_lambda_kernel<<<1, 1, 0, s>>>(ps.d_state, params[0]);
-    g.ep.args = ps.d_args;
-    g.ep.st = ps.d_state;
     g.ep.absmax = nullptr;
   }
+  BlockRec br{};
+  br.off = 0;
+  br.n = static_cast<int>(n);
+  br.st = ps.d_state;
+  if (epi == 3) {
+    br.X = static_cast<const float*>(aux);
+    br.ld = ld_aux;
+    br.out = static_cast<float*>(C);
+    br.ld_out = ld_out;
+  }
+  if (enqueue_set_block(ps.d_block, br, s) != cudaSuccess) return PSD_ERR_CUDA;
   cudaError_t e;
   if (!split) {
     CUtensorMap ta, tb;
     if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 256)) return PSD_ERR_CUDA;
     const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;
-    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (32u << 17) | (8u << 24);
+    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);  // M = 128; N per tile
     e = launch_symgemm(dtype, epi, ta, tb, g, num_sms(), s);
   } else {
     CUtensorMap tm[4];

@@ -109,13 +109,13 @@ __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t* src, int f
 // from their upper part; off-diagonal chunks are written at both positions,
 // (r, c) and (c, r), with 16-byte stores from the staged copies.
 template <int EPI>
-__device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16, int r0, int c0,
-                                                 const uint32_t (&v)[32], uint8_t* wbuf, const uint4 (&y)[4],
-                                                 int lane, unsigned& amax_bits) {
+__device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16, int n, uint16_t* C, int r0,
+                                                 int c0, const uint32_t (&v)[32], uint8_t* wbuf,
+                                                 const uint4 (&y)[4], int lane, bool track,
+                                                 unsigned& amax_bits) {
   uint16_t* S = reinterpret_cast<uint16_t*>(wbuf);  // [32][kH] row t = output row r0 + t
   uint16_t* ST = S + 32 * kH;                        // [32][kH] row j = output column c0 + j
   uint16_t* YB = ST + 32 * kH;                       // [32][kH] row j = Y column c0 + j
-  const int n = p.n;
   const int r = r0 + lane;
   const bool diag = (r0 == c0);
   if (EPI == EPI_POLY) {
@@ -161,13 +161,12 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16,
 #pragma unroll
     for (int j = 0; j < 32; ++j) ST[j * kH + lane] = static_cast<uint16_t>(h[j]);
   }
-  if (p.ep.absmax && r < n) {
+  if (track && r < n) {
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(from16(static_cast<uint16_t>(h[j]), bf16))));
   }
   __syncwarp();
-  uint16_t* C = static_cast<uint16_t*>(p.ep.C);
   const int64_t ldc = p.ep.ldc;
   const int seg = 8 * (lane & 3);
   // memory rows c0 + j: output column c0 + j over rows r0..r0+31 (ST row j; S row j when symmetric)
@@ -193,16 +192,15 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16,
 
 // One 32 x 32 chunk of the final output out = (X + lam~ acc) / 2 in FP32,
 // reading only the upper triangle of the caller's X (column-major).
-__device__ __forceinline__ void epilogue_chunk_final(const GemmParams& p, int r0, int c0,
+__device__ __forceinline__ void epilogue_chunk_final(const BlockRec& br, int r0, int c0,
                                                      const uint32_t (&v)[32], uint8_t* wbuf,
                                                      int lane, float lam) {
   uint32_t* stg = reinterpret_cast<uint32_t*>(wbuf);
-  const int n = p.n;
-  const DevArgs* a = p.ep.args;
-  const float* X = a->X;
-  const int64_t ld = a->ld;
-  float* out = a->out;
-  const int64_t ldo = a->ld_out;
+  const int n = br.n;
+  const float* X = br.X;
+  const int64_t ld = br.ld;
+  float* out = br.out;
+  const int64_t ldo = br.ld_out;
   const int r = r0 + lane;
   const bool diag = (r0 == c0);
   const bool row_ok = r < n;
@@ -298,16 +296,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t s = 0, ph = 0;
       bool ok = true;
       for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
-        const int2 tc = p.tiles[t];
-        for (int kb = 0; kb < p.k_blocks; ++kb) {
+        const int4 tc = p.tiles[t];
+        const int64_t off = p.blocks[tc.z].off;
+        const int kbn = (p.blocks[tc.z].n + kBK16 - 1) / kBK16;
+        const int ya = static_cast<int>(off + tc.x), yb = static_cast<int>(off + tc.y);
+        for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
           mbar_arrive_expect_tx(full_bar(s), kStageBytes16);
           const uint32_t a_dst = smem_u32(stages + s * kStageBytes16);
-          tma_load_2d(a_dst, &tmA, kb * kBK16, tc.x, full_bar(s));
-          tma_load_2d(a_dst + kABytes16, &tmB, kb * kBK16, tc.y, full_bar(s));
+          tma_load_2d(a_dst, &tmA, kb * kBK16, ya, full_bar(s));
+          tma_load_2d(a_dst + kABytes16, &tmB, kb * kBK16, yb, full_bar(s));
           last_parity[s] = static_cast<int>(ph);
           if (++s == kStages16) {
             s = 0;
@@ -330,13 +331,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
     bool ok = true;
     for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+      const int4 tc = p.tiles[t];
+      const int kbn = (p.blocks[tc.z].n + kBK16 - 1) / kBK16;
+      const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
       if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + acc * kBN;
-      for (int kb = 0; kb < p.k_blocks; ++kb) {
+      for (int kb = 0; kb < kbn; ++kb) {
         if (!wait_bounded(full_bar(s), ph, abort_flag)) {
           ok = false;
           break;
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < kBK16 / 16; ++k) {
             mma_f16(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
-                    p.idesc, (kb | k) != 0 ? 1u : 0u);
+                    idesc, (kb | k) != 0 ? 1u : 0u);
           }
           mma_commit(empty_bar(s));
         }
@@ -376,34 +380,51 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ew = warp & 3;
     uint8_t* wbuf = epi_stg + ew * kEpiWarpBytes;
     uint32_t acc = 0, acc_ph = 0;
-    unsigned amax_bits = 0;
-    float lam = 0.f;
-    if (EPI == EPI_FINAL) lam = static_cast<float>(p.ep.st->lambda);
-    const uint16_t* Y = static_cast<const uint16_t*>(p.ep.Y);
+    unsigned amax_bits = 0;  // max |output| of the current block (absmax_blocks) or of the launch
+    int amax_block = -1;
+    const bool track = p.ep.absmax_blocks != 0 || p.ep.absmax != nullptr;
+    auto flush_amax = [&](int blk) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
+      if (lane == 0 && amax_bits) {
+        unsigned* dst = p.ep.absmax ? p.ep.absmax : &p.blocks[blk].st->absmax_bits;
+        atomicMax(dst, amax_bits);
+      }
+      amax_bits = 0;
+    };
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
-      const int2 tc = p.tiles[t];
+      const int4 tc = p.tiles[t];
+      const BlockRec& br = p.blocks[tc.z];
+      const int n = br.n;
+      const int64_t off = br.off;
+      uint16_t* C = static_cast<uint16_t*>(p.ep.C) + off * p.ep.ldc;
+      const uint16_t* Y = static_cast<const uint16_t*>(p.ep.Y) + off * p.ep.ldy;
+      if (track && amax_block != tc.z) {
+        if (amax_block >= 0) flush_amax(amax_block);
+        amax_block = tc.z;
+      }
       const int r0 = tc.x + 32 * ew;
       // chunks of this warp's 32 rows that lie on or above the diagonal and inside n
       const int ch_begin = max(0, (r0 - tc.y) >> 5);
-      const int ch_end = r0 < p.n ? min(kBN / 32, (p.n - tc.y + 31) >> 5) : ch_begin;
+      const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
       uint4 ynext[4] = {};
-      if (EPI == EPI_POLY && ch_begin < ch_end)
-        load_y_chunk(Y, p.ep.ldy, p.n, r0, tc.y + 32 * ch_begin, lane, ynext);
+      if (EPI == EPI_POLY && ch_begin < ch_end) load_y_chunk(Y, p.ep.ldy, n, r0, tc.y + 32 * ch_begin, lane, ynext);
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
+      const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
 #pragma unroll 1
       for (int ch = ch_begin; ch < ch_end; ++ch) {
         const int c0 = tc.y + 32 * ch;
         uint4 ycur[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) ycur[k] = ynext[k];
-        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y_chunk(Y, p.ep.ldy, p.n, r0, c0 + 32, lane, ynext);
+        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y_chunk(Y, p.ep.ldy, n, r0, c0 + 32, lane, ynext);
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
         if (EPI == EPI_FINAL)
-          epilogue_chunk_final(p, r0, c0, v, wbuf, lane, lam);
+          epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam);
         else
-          epilogue_chunk16<EPI>(p, bf16, r0, c0, v, wbuf, ycur, lane, amax_bits);
+          epilogue_chunk16<EPI>(p, bf16, n, C, r0, c0, v, wbuf, ycur, lane, track, amax_bits);
       }
       tc_fence_before();
       __syncwarp();
@@ -411,11 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       acc ^= 1u;
       if (acc == 0) acc_ph ^= 1u;
     }
-    if (EPI != EPI_FINAL && p.ep.absmax) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
-      if (lane == 0 && amax_bits) atomicMax(p.ep.absmax, amax_bits);
-    }
+    if (EPI != EPI_FINAL && track && amax_block >= 0) flush_amax(amax_block);
   }
 
   tc_fence_before();
@@ -494,11 +511,14 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
 // Upper-triangle tiles of 256 x 256 blocks, each split into two 128-row
 // tiles, in a grouped raster: block rows are taken in groups of 8, and inside
 // a group the columns advance first so that the tiles resident at one time
-// share their operand panels in L2.
-std::vector<int2> make_tile_list(int64_t n) {
-  std::vector<int2> tiles;
+// share their operand panels in L2.  The lower tile of a diagonal block only
+// needs its right half (columns >= its first row), and every tile is trimmed
+// to the columns below n (rounded up to 16, the MMA's N granularity).
+std::vector<int4> make_tile_list(int64_t n, int block) {
+  std::vector<int4> tiles;
   const int nb = static_cast<int>((n + kBN - 1) / kBN);
   const int G = 8;
+  auto width = [&](int n0, int w) { return std::min(w, static_cast<int>((n - n0 + 15) / 16 * 16)); };
   for (int g0 = 0; g0 < nb; g0 += G) {
     for (int J = g0; J < nb; ++J) {
       const int iend = std::min(g0 + G, J + 1);
@@ -506,7 +526,10 @@ std::vector<int2> make_tile_list(int64_t n) {
         for (int h = 0; h < 2; ++h) {
           const int m0 = I * kBN + h * kBM;
           if (m0 >= n) continue;
-          tiles.push_back(make_int2(m0, J * kBN));
+          if (I == J && h == 1)
+            tiles.push_back(make_int4(m0, m0, block, width(m0, kBM)));
+          else
+            tiles.push_back(make_int4(m0, J * kBN, block, width(J * kBN, kBN)));
         }
       }
     }

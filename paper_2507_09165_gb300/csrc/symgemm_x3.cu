@@ -114,9 +114,17 @@ __device__ __forceinline__ void store_chunk(void* C, int64_t ldc, int n, int r0,
 
 // OUT: 0 = split pair of the operand kind, 1 = single FP16, 2 = FP32 final output.
 template <bool TF32, int EPI, int OUT>
-__device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, int c0, const uint32_t (&v)[32],
-                                                  float* S, float* YB, int lane, float lam, unsigned& amax_bits) {
-  const int n = p.n;
+__device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const BlockRec& br, int r0, int c0,
+                                                  const uint32_t (&v)[32], float* S, float* YB, int lane, float lam,
+                                                  bool track, unsigned& amax_bits) {
+  const int n = br.n;
+  const int64_t off = br.off;
+  const int64_t esz = OUT == 1 ? 2 : (TF32 ? 4 : 2);  // element size of the iterate output
+  void* C = static_cast<uint8_t*>(p.ep.C) + off * p.ep.ldc * esz;
+  void* C_lo = p.ep.C_lo ? static_cast<uint8_t*>(p.ep.C_lo) + off * p.ep.ldc * esz : nullptr;
+  const int64_t ysz = TF32 ? 4 : 2;
+  const void* Yh = p.ep.Y ? static_cast<const uint8_t*>(p.ep.Y) + off * p.ep.ldy * ysz : nullptr;
+  const void* Yl = p.ep.Y_lo ? static_cast<const uint8_t*>(p.ep.Y_lo) + off * p.ep.ldy * ysz : nullptr;
   const int r = r0 + lane;
   const bool diag = (r0 == c0);
   const bool row_ok = r < n;
@@ -129,7 +137,7 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, i
       float y = 0.f;
       if (row_ok && c < n) {
         const int64_t idx = static_cast<int64_t>(c) * p.ep.ldy + r;
-        y = ld_elem<TF32>(p.ep.Y, idx) + ld_elem<TF32>(p.ep.Y_lo, idx);
+        y = ld_elem<TF32>(Yh, idx) + ld_elem<TF32>(Yl, idx);
       }
       YB[j * kSW + lane] = y;
     }
@@ -137,8 +145,8 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, i
   const float* X = nullptr;
   int64_t ldx = 0;
   if (EPI == EPI_FINAL) {
-    X = p.ep.args->X;
-    ldx = p.ep.args->ld;
+    X = br.X;
+    ldx = br.ld;
   }
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
@@ -175,10 +183,10 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, i
       for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
       __syncwarp();
     }
-    store_chunk<0>(p.ep.args->out, p.ep.args->ld_out, n, r0, c0, diag, S, lane);
+    store_chunk<0>(br.out, br.ld_out, n, r0, c0, diag, S, lane);
     __syncwarp();
   } else if constexpr (OUT == 1) {
-    if (p.ep.absmax && row_ok) {
+    if (track && row_ok) {
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(__half2float(__float2half_rn(o[j])))));
@@ -188,7 +196,7 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, i
       for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
       __syncwarp();
     }
-    store_chunk<2>(p.ep.C, p.ep.ldc, n, r0, c0, diag, S, lane);
+    store_chunk<2>(C, p.ep.ldc, n, r0, c0, diag, S, lane);
     __syncwarp();
   } else {
   // split pair: hi first, then lo, through the same staging buffer
@@ -199,7 +207,7 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, i
     lo[j] = TF32 ? tf32_rn(o[j] - hi) : bf16_rn(o[j] - hi);
     o[j] = hi;
   }
-  if (p.ep.absmax && row_ok) {
+  if (track && row_ok) {
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(o[j] + lo[j])));
@@ -207,12 +215,12 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, int r0, i
 #pragma unroll
   for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
   __syncwarp();
-  store_chunk<TF32 ? 0 : 1>(p.ep.C, p.ep.ldc, n, r0, c0, diag, S, lane);
+  store_chunk<TF32 ? 0 : 1>(C, p.ep.ldc, n, r0, c0, diag, S, lane);
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < 32; ++j) S[lane * kSW + j] = lo[j];
   __syncwarp();
-  store_chunk<TF32 ? 0 : 1>(p.ep.C_lo, p.ep.ldc, n, r0, c0, diag, S, lane);
+  store_chunk<TF32 ? 0 : 1>(C_lo, p.ep.ldc, n, r0, c0, diag, S, lane);
   __syncwarp();
   }
 }
@@ -274,18 +282,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t s = 0, ph = 0;
       bool ok = true;
       for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
-        const int2 tc = p.tiles[t];
-        for (int kb = 0; kb < p.k_blocks; ++kb) {
+        const int4 tc = p.tiles[t];
+        const int64_t boff = p.blocks[tc.z].off;
+        const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
+        const int ya = static_cast<int>(boff + tc.x), yb = static_cast<int>(boff + tc.y);
+        for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
           mbar_arrive_expect_tx(full_bar(s), kStageBytes);
           const uint32_t base = smem_u32(stages + s * kStageBytes);
-          tma_load_2d(base, &tmAh, kb * kKElems, tc.x, full_bar(s));
-          tma_load_2d(base + kABytes, &tmAl, kb * kKElems, tc.x, full_bar(s));
-          tma_load_2d(base + 2 * kABytes, &tmBh, kb * kKElems, tc.y, full_bar(s));
-          tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, tc.y, full_bar(s));
+          tma_load_2d(base, &tmAh, kb * kKElems, ya, full_bar(s));
+          tma_load_2d(base + kABytes, &tmAl, kb * kKElems, ya, full_bar(s));
+          tma_load_2d(base + 2 * kABytes, &tmBh, kb * kKElems, yb, full_bar(s));
+          tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, yb, full_bar(s));
           last_parity[s] = static_cast<int>(ph);
           if (++s == kStages) {
             s = 0;
@@ -307,13 +318,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
     bool ok = true;
     for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+      const int4 tc = p.tiles[t];
+      const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
+      const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
       if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + acc * kBN;
-      for (int kb = 0; kb < p.k_blocks; ++kb) {
+      for (int kb = 0; kb < kbn; ++kb) {
         if (!wait_bounded(full_bar(s), ph, abort_flag)) {
           ok = false;
           break;
@@ -327,13 +341,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t off = 32 * k;
             const uint32_t first = (kb | k) == 0 ? 0u : 1u;
             if (TF32) {
-              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), p.idesc, first);
-              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), p.idesc, 1u);
-              mma_tf32(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), p.idesc, 1u);
+              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
+              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
+              mma_tf32(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
             } else {
-              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), p.idesc, first);
-              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), p.idesc, 1u);
-              mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), p.idesc, 1u);
+              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
+              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
+              mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
             }
           }
           mma_commit(empty_bar(s));
@@ -363,20 +377,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* YB = S + 32 * kSW;
     uint32_t acc = 0, acc_ph = 0;
     unsigned amax_bits = 0;
-    float lam = 0.f;
-    if (EPI == EPI_FINAL) lam = static_cast<float>(p.ep.st->lambda);
+    int amax_block = -1;
+    const bool track = p.ep.absmax_blocks != 0 || p.ep.absmax != nullptr;
+    auto flush_amax = [&](int blk) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
+      if (lane == 0 && amax_bits) {
+        unsigned* dst = p.ep.absmax ? p.ep.absmax : &p.blocks[blk].st->absmax_bits;
+        atomicMax(dst, amax_bits);
+      }
+      amax_bits = 0;
+    };
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
-      const int2 tc = p.tiles[t];
+      const int4 tc = p.tiles[t];
+      const BlockRec& br = p.blocks[tc.z];
+      const int n = br.n;
+      if (track && amax_block != tc.z) {
+        if (amax_block >= 0) flush_amax(amax_block);
+        amax_block = tc.z;
+      }
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
+      const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
       const int r0 = tc.x + 32 * ew;
       const int ch_begin = max(0, (r0 - tc.y) >> 5);
-      const int ch_end = r0 < p.n ? min(kBN / 32, (p.n - tc.y + 31) >> 5) : ch_begin;
+      const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
 #pragma unroll 1
       for (int ch = ch_begin; ch < ch_end; ++ch) {
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
-        epilogue_chunk_x3<TF32, EPI, OUT>(p, r0, tc.y + 32 * ch, v, S, YB, lane, lam, amax_bits);
+        epilogue_chunk_x3<TF32, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
       }
       tc_fence_before();
       __syncwarp();
@@ -384,11 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       acc ^= 1u;
       if (acc == 0) acc_ph ^= 1u;
     }
-    if (p.ep.absmax) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
-      if (lane == 0 && amax_bits) atomicMax(p.ep.absmax, amax_bits);
-    }
+    if (track && amax_block >= 0) flush_amax(amax_block);
   }
 
   tc_fence_before();
@@ -435,7 +461,7 @@ cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm
   }
   GemmParams q = p;
   const uint32_t fmt = tf32 ? 2u : 1u;
-  q.idesc = make_idesc(fmt, kBM, kBN);
+  q.idesc = make_idesc(fmt, kBM, 0);  // N comes from each tile
   const int g = std::max(1, std::min(grid, p.num_tiles));
   k<<<g, kThreads, smem, stream>>>(tm[0], tm[1], tm[2], tm[3], q);
   return cudaGetLastError();
