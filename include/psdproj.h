@@ -143,12 +143,14 @@ typedef struct {
   psd_info_t *info;
 } psd_block_desc_t;
 
-/* Projects `count` independent blocks.  d_descs is an array of `count`
- * descriptors in DEVICE memory.  The library reads the block orders back to
- * the host once per call (a synchronous 8*count-byte copy) to pick the cached
- * plan for that size signature; all compute is then enqueued on `stream`.
- * Results are bit-identical to projecting each block alone with the same
- * precision. */
+/* Projects `count` independent blocks with one sequence of grouped launches
+ * (norm bound, cast and each of the 3T + 1 products is one launch over all
+ * blocks), captured in a CUDA graph per (device, stream, precision, block
+ * orders).  d_descs is an array of `count` descriptors in DEVICE memory; the
+ * library reads it back once per call (a synchronous copy of count * 48
+ * bytes) to find the plan for the block orders.  Every block's result depends
+ * only on that block: it is bit-identical to a batched call with that block
+ * alone.  Orders 1..1024; precisions FP16, BF16, MIXED, FP32. */
 psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
                                  psd_precision_t precision, psd_stream_t stream);
 

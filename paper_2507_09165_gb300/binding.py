@@ -208,6 +208,21 @@ def psd_version():
     return lib().psd_version().decode()
 
 
+def block_descs(blocks, device="cuda"):
+    """Device array of psd_block_desc_t for psd_project_batched.
+
+    blocks: list of (n, X, ld, out, ld_out, info) with X, out, info device
+    pointers (integers or tensors; info may be None).  Returns a uint8 torch
+    tensor on `device` holding the descriptors (keep it alive for the call).
+    """
+    import torch
+    arr = (psd_block_desc_t * len(blocks))()
+    for i, (n, X, ld, out, ld_out, info) in enumerate(blocks):
+        arr[i] = psd_block_desc_t(n, _ptr(X), ld, _ptr(out), ld_out, _ptr(info))
+    raw = bytes(arr)
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
 INFO_BYTES = ctypes.sizeof(psd_info_t)
 DESC_BYTES = ctypes.sizeof(psd_block_desc_t)
 

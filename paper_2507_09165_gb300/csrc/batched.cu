@@ -1,39 +1,399 @@
-// Batched projection of a block-diagonal cone and the request server.
+// Batched projection of a block-diagonal cone: psd_project_batched.
 //
-// psd_project_batched: the descriptors live in device memory; their orders
-// are read back once per call, then every block is projected on `stream`
-// through the same per-order plan as psd_project_ex, so a block's result is
-// bit-identical alone and in the batch.
-#include <condition_variable>
-#include <deque>
+// All blocks are projected by one sequence of grouped launches captured in a
+// CUDA graph per (device, stream, precision, block orders): the grouped norm
+// bound and cast (batched_kernels.cu) and the 3T + 1 tensor-core products,
+// each ONE launch over the upper tiles of every block (tiles ordered from the
+// largest blocks down).  Iterates are stacked: block b occupies rows
+// off_b .. off_b + n_b - 1 of buffers with a common row length ldm =
+// round_up(max n_b, 64); the columns n_b .. ldm - 1 of its rows are zeroed once
+// and never written, so a tile's K range and its valid outputs only involve
+// the block's own entries -- a block's result is bit-identical alone and in
+// any batch.
+#include <algorithm>
 #include <map>
 #include <mutex>
-#include <thread>
 #include <vector>
 
 #include "internal.h"
 
-extern "C" psd_status_t psd_project_ex(int64_t n, const float* X, int64_t ld, float* out, int64_t ld_out,
-                                       psd_precision_t precision, psd_info_t* d_info, void* workspace,
-                                       size_t ws_bytes, psd_stream_t stream);
+namespace psd {
+namespace {
+
+constexpr int kMixedSplitB = 3;  // mixed: BF16 pairs for stages 1..3, then FP16
+
+enum Kind : int { K16 = 0, KB3 = 1, KT3 = 2 };
+int kslots(int k) { return k == K16 ? 1 : k == KB3 ? 2 : 4; }
+
+struct BMat {
+  int kind = K16;
+  int slot = -1;
+  int dt16 = DT_F16;
+};
+
+struct BatchPlan {
+  psd_precision_t prec = PSD_PREC_BF16;
+  int count = 0;
+  std::vector<int> sizes;
+  Schedule sched{};
+  int64_t R = 0;     // stacked rows
+  int64_t ldm = 0;   // row length of the stacked buffers
+  size_t slot_size = 0;
+  int nslots = 0;
+  uint8_t* ws = nullptr;
+  uint8_t* slots = nullptr;
+  BatchLanczos L{};
+  BlockRec* d_rec = nullptr;
+  BatchBlock* d_bb = nullptr;
+  DevState* d_st = nullptr;
+  int* d_status = nullptr;
+  int4* d_tiles = nullptr;
+  int ntiles = 0;
+  int4* d_symv = nullptr;
+  int nsymv = 0;
+  int4* d_cast = nullptr;
+  int ncast = 0;
+  uint8_t* small = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_tried = false;
+};
+
+std::mutex g_bmu;
+std::map<std::tuple<int, cudaStream_t, int, std::vector<int>>, BatchPlan*> g_bplans;
+
+int64_t rup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+int nslots_for(psd_precision_t prec) { return prec == PSD_PREC_FP32 ? 16 : prec == PSD_PREC_MIXED ? 9 : 4; }
+
+int dt16_for(psd_precision_t prec) { return prec == PSD_PREC_BF16 ? DT_BF16 : DT_F16; }
+
+__global__ void batch_args_kernel(const psd_block_desc_t* __restrict__ d, BlockRec* rec, BatchBlock* bb,
+                                  int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const psd_block_desc_t x = d[b];
+  rec[b].X = x.X;
+  rec[b].ld = x.ld;
+  rec[b].out = x.out;
+  rec[b].ld_out = x.ld_out;
+  bb[b].X = x.X;
+  bb[b].ld = x.ld;
+  bb[b].info = x.info;
+}
+
+void free_bplan(BatchPlan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->ws) cudaFree(p->ws);
+  if (p->small) cudaFree(p->small);
+  delete p;
+}
+
+psd_status_t build_bplan(BatchPlan* p) {
+  if (!get_schedule(p->prec, p->sched)) return PSD_ERR_INVALID_ARG;
+  const int count = p->count;
+  int maxn = 1;
+  for (int n : p->sizes) maxn = std::max(maxn, n);
+  p->ldm = rup(maxn, 64);
+  // host records
+  std::vector<BlockRec> rec(count);
+  std::vector<BatchBlock> bb(count);
+  int64_t off = 0, voff = 0, poff = 0, toff = 0;
+  std::vector<int4> symv, cast;
+  for (int b = 0; b < count; ++b) {
+    const int n = p->sizes[b];
+    const int nb = (n + kSymvTile - 1) / kSymvTile;
+    rec[b] = BlockRec{};
+    rec[b].off = off;
+    rec[b].n = n;
+    bb[b] = BatchBlock{};
+    bb[b].n = n;
+    bb[b].ntiles = nb * (nb + 1) / 2;
+    bb[b].off = off;
+    bb[b].voff = voff;
+    bb[b].poff = poff;
+    bb[b].toff = toff;
+    int t = 0;
+    for (int j = 0; j < nb; ++j)
+      for (int i = 0; i <= j; ++i) symv.push_back(make_int4(b, i, j, static_cast<int>(toff + t++)));
+    const int nc = (n + 63) / 64;
+    for (int j = 0; j < nc; ++j)
+      for (int i = 0; i <= j; ++i) cast.push_back(make_int4(b, i, j, 0));
+    off += n;
+    voff += n;
+    poff += 2LL * nb * n;
+    toff += bb[b].ntiles;
+  }
+  p->R = off;
+  // product tiles of all blocks, largest blocks first (their tiles carry the most K-steps)
+  std::vector<int> order(count);
+  for (int b = 0; b < count; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p->sizes[x] > p->sizes[y]; });
+  std::vector<int4> tiles;
+  for (int b : order) {
+    std::vector<int4> tl = make_tile_list(p->sizes[b], b);
+    tiles.insert(tiles.end(), tl.begin(), tl.end());
+  }
+  p->ntiles = static_cast<int>(tiles.size());
+  p->nsymv = static_cast<int>(symv.size());
+  p->ncast = static_cast<int>(cast.size());
+  // device memory: stacked slots + Lanczos vectors (one allocation, zeroed once)
+  p->slot_size = static_cast<size_t>(rup(p->R * p->ldm * 2, 1024));
+  p->nslots = nslots_for(p->prec);
+  const size_t b_slots = p->nslots * p->slot_size;
+  const size_t b_vec64 = rup(sizeof(double) * (kMaxSteps + 4) * voff, 256);
+  const size_t b_vec32 = rup(sizeof(float) * 2 * voff, 256);
+  const size_t b_part = rup(sizeof(float2) * poff, 256);
+  const size_t b_fro = rup(sizeof(double) * std::max<int64_t>(toff, 1), 256);
+  const size_t total = 1024 + b_slots + b_vec64 + b_vec32 + b_part + b_fro;
+  if (cudaMalloc(&p->ws, total) != cudaSuccess) {
+    cudaGetLastError();
+    p->ws = nullptr;
+    return PSD_ERR_NO_MEMORY;
+  }
+  if (cudaMemset(p->ws, 0, total) != cudaSuccess) return PSD_ERR_CUDA;
+  uint8_t* base = reinterpret_cast<uint8_t*>(rup(reinterpret_cast<int64_t>(p->ws), 1024));
+  p->slots = base;
+  uint8_t* q = base + b_slots;
+  p->L.vec64 = reinterpret_cast<double*>(q);
+  q += b_vec64;
+  p->L.vec32 = reinterpret_cast<float*>(q);
+  q += b_vec32;
+  p->L.part = reinterpret_cast<float2*>(q);
+  q += b_part;
+  p->L.tile_fro = reinterpret_cast<double*>(q);
+  // small records: BlockRec | BatchBlock | DevState | status | tiles | symv items | cast items
+  const size_t o_bb = rup(sizeof(BlockRec) * count, 256);
+  const size_t o_st = o_bb + rup(sizeof(BatchBlock) * count, 256);
+  const size_t o_status = o_st + rup(sizeof(DevState) * count, 256);
+  const size_t o_tiles = o_status + 256;
+  const size_t o_symv = o_tiles + rup(sizeof(int4) * tiles.size(), 256);
+  const size_t o_cast = o_symv + rup(sizeof(int4) * symv.size(), 256);
+  const size_t smallb = o_cast + rup(sizeof(int4) * cast.size(), 256);
+  if (cudaMalloc(&p->small, smallb) != cudaSuccess) {
+    cudaGetLastError();
+    p->small = nullptr;
+    return PSD_ERR_NO_MEMORY;
+  }
+  cudaMemset(p->small, 0, smallb);
+  p->d_rec = reinterpret_cast<BlockRec*>(p->small);
+  p->d_bb = reinterpret_cast<BatchBlock*>(p->small + o_bb);
+  p->d_st = reinterpret_cast<DevState*>(p->small + o_st);
+  p->d_status = reinterpret_cast<int*>(p->small + o_status);
+  p->d_tiles = reinterpret_cast<int4*>(p->small + o_tiles);
+  p->d_symv = reinterpret_cast<int4*>(p->small + o_symv);
+  p->d_cast = reinterpret_cast<int4*>(p->small + o_cast);
+  for (int b = 0; b < count; ++b) rec[b].st = p->d_st + b;
+  bool ok = cudaMemcpy(p->d_rec, rec.data(), sizeof(BlockRec) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(p->d_bb, bb.data(), sizeof(BatchBlock) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaMemcpy(p->d_symv, symv.data(), sizeof(int4) * symv.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(p->d_cast, cast.data(), sizeof(int4) * cast.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) return PSD_ERR_CUDA;
+  p->L.blk = p->d_bb;
+  p->L.st = p->d_st;
+  p->L.skip_done = 0;
+  return PSD_OK;
+}
+
+struct Pool {
+  uint32_t used = 0;
+  int n = 0;
+  int alloc(int k) {
+    for (int s = 0; s + k <= n; ++s) {
+      const uint32_t m = ((1u << k) - 1u) << s;
+      if (!(used & m)) {
+        used |= m;
+        return s;
+      }
+    }
+    return -1;
+  }
+  void release(const BMat& m) { used &= ~(((1u << kslots(m.kind)) - 1u) << m.slot); }
+};
+
+void* bpart(const BatchPlan* p, const BMat& m, int part) {
+  const int step = m.kind == KT3 ? 2 : 1;
+  return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * step)) * p->slot_size;
+}
+int bdtype(const BMat& m) { return m.kind == K16 ? m.dt16 : m.kind == KB3 ? DT_BF16X3 : DT_TF32X3; }
+
+cudaError_t bgemm(BatchPlan* p, int epi, const BMat& A, const BMat& B, const BMat* out, const BMat* Y, float a,
+                  float b, float c, float sc, bool track, cudaStream_t s) {
+  GemmParams g{};
+  g.num_tiles = p->ntiles;
+  g.tiles = p->d_tiles;
+  g.blocks = p->d_rec;
+  g.ep.status = p->d_status;
+  g.ep.a = a;
+  g.ep.b = b;
+  g.ep.c = c;
+  g.ep.s = sc;
+  g.ep.absmax_blocks = track ? 1 : 0;
+  if (epi != EPI_FINAL) {
+    g.ep.C = bpart(p, *out, 0);
+    g.ep.C_lo = out->kind == K16 ? nullptr : bpart(p, *out, 1);
+    g.ep.ldc = p->ldm;
+  }
+  if (epi == EPI_POLY) {
+    g.ep.Y = bpart(p, *Y, 0);
+    g.ep.Y_lo = Y->kind == K16 ? nullptr : bpart(p, *Y, 1);
+    g.ep.ldy = p->ldm;
+  }
+  const int grid = num_sms();
+  const int64_t cols = p->ldm, rows = p->R;
+  if (A.kind == K16) {
+    CUtensorMap ta, tb;
+    if (!encode_tmap_rows(&ta, A.dt16, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
+        !encode_tmap_rows(&tb, B.dt16, bpart(p, B, 0), cols, rows, p->ldm, 256))
+      return cudaErrorInvalidValue;
+    const uint32_t fmt = A.dt16 == DT_BF16 ? 1u : 0u;
+    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);
+    return launch_symgemm(A.dt16, epi, ta, tb, g, grid, s);
+  }
+  const int dt = bdtype(A);
+  CUtensorMap tm[4];
+  if (!encode_tmap_rows(&tm[0], dt, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
+      !encode_tmap_rows(&tm[1], dt, bpart(p, A, 1), cols, rows, p->ldm, 128) ||
+      !encode_tmap_rows(&tm[2], dt, bpart(p, B, 0), cols, rows, p->ldm, 256) ||
+      !encode_tmap_rows(&tm[3], dt, bpart(p, B, 1), cols, rows, p->ldm, 256))
+    return cudaErrorInvalidValue;
+  const int out_mode = epi == EPI_FINAL ? 2 : (out->kind == K16 ? 1 : 0);
+  return launch_symgemm_x3(A.kind == KT3, epi, out_mode, tm, g, grid, s);
+}
+
+cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = enqueue_batch_norm_bound(p->L, p->count, p->d_symv, p->nsymv, s)) != cudaSuccess) return e;
+  Pool pool;
+  pool.n = p->nslots;
+  const int T = p->sched.T;
+  const int dt16 = dt16_for(p->prec);
+  auto kind_of = [&](int t) {
+    if (p->prec == PSD_PREC_FP32) return static_cast<int>(KT3);
+    if (p->prec == PSD_PREC_MIXED && t < kMixedSplitB) return static_cast<int>(KB3);
+    return static_cast<int>(K16);
+  };
+  auto make = [&](int k) {
+    BMat m;
+    m.kind = k;
+    m.dt16 = dt16;
+    m.slot = pool.alloc(kslots(k));
+    return m;
+  };
+  BMat X0 = make(kind_of(0)), X0f16;
+  if (p->prec == PSD_PREC_MIXED) X0f16 = make(K16);
+  if (X0.slot < 0 || (p->prec == PSD_PREC_MIXED && X0f16.slot < 0)) return cudaErrorMemoryAllocation;
+  BatchCast bc{bpart(p, X0, 0), X0.kind == K16 ? nullptr : bpart(p, X0, 1),
+               p->prec == PSD_PREC_MIXED ? bpart(p, X0f16, 0) : nullptr, p->ldm};
+  if ((e = enqueue_batch_cast(bdtype(X0), bc, p->d_bb, p->d_st, p->d_cast, p->ncast, s)) != cudaSuccess) return e;
+  BMat cur = X0;
+  for (int t = 0; t < T; ++t) {
+    const int k = kind_of(t);
+    const int kout = p->prec == PSD_PREC_FP32 ? static_cast<int>(KT3) : (t + 1 < T ? kind_of(t + 1) : static_cast<int>(K16));
+    BMat Y = make(k);
+    if (Y.slot < 0) return cudaErrorMemoryAllocation;
+    if ((e = bgemm(p, EPI_COPY, cur, cur, &Y, nullptr, 0.f, 0.f, 0.f, 1.f, false, s)) != cudaSuccess) return e;
+    BMat P = make(k);
+    if (P.slot < 0) return cudaErrorMemoryAllocation;
+    if ((e = bgemm(p, EPI_POLY, Y, Y, &P, &Y, static_cast<float>(p->sched.coef[t][0]),
+                   static_cast<float>(p->sched.coef[t][1]), static_cast<float>(p->sched.coef[t][2]), 1.f, false,
+                   s)) != cudaSuccess)
+      return e;
+    pool.release(Y);
+    BMat Xn = make(kout);
+    if (Xn.slot < 0) return cudaErrorMemoryAllocation;
+    if ((e = bgemm(p, EPI_SCALE, cur, P, &Xn, nullptr, 0.f, 0.f, 0.f, static_cast<float>(1.0 / p->sched.post[t]),
+                   t == T - 1, s)) != cudaSuccess)
+      return e;
+    pool.release(P);
+    if (cur.slot != X0.slot) pool.release(cur);
+    cur = Xn;
+  }
+  const BMat& A0 = p->prec == PSD_PREC_MIXED ? X0f16 : X0;
+  if ((e = bgemm(p, EPI_FINAL, A0, cur, nullptr, nullptr, 0.f, 0.f, 0.f, 1.f, false, s)) != cudaSuccess) return e;
+  return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, s);
+}
+
+void ensure_bgraph(BatchPlan* p) {
+  if (p->graph_tried) return;
+  p->graph_tried = true;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaError_t e = enqueue_batch(p, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess && e2 == cudaSuccess && graph) {
+      if (cudaGraphInstantiate(&p->exec, graph, 0) != cudaSuccess) p->exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  cudaGetLastError();
+  cudaStreamDestroy(cs);
+}
+
+}  // namespace
+}  // namespace psd
+
+using namespace psd;
 
 extern "C" psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t* d_descs,
                                             psd_precision_t precision, psd_stream_t stream) {
   if (count < 0 || (count > 0 && !d_descs)) return PSD_ERR_INVALID_ARG;
+  if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16 && precision != PSD_PREC_FP32 &&
+      precision != PSD_PREC_MIXED)
+    return precision == PSD_PREC_FP8_EARLY ? PSD_ERR_UNSUPPORTED : PSD_ERR_INVALID_ARG;
   if (count == 0) return PSD_OK;
-  std::vector<psd_block_desc_t> h(static_cast<size_t>(count));
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PSD_ERR_CUDA;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return PSD_ERR_UNSUPPORTED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<psd_block_desc_t> h(static_cast<size_t>(count));
   if (cudaMemcpyAsync(h.data(), d_descs, sizeof(psd_block_desc_t) * h.size(), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return PSD_ERR_CUDA;
-  for (const auto& d : h)
-    if (d.n < 0 || d.n > 1024 || (d.n > 0 && (!d.X || !d.out || d.ld < d.n || d.ld_out < d.n)))
+  std::vector<int> sizes(static_cast<size_t>(count));
+  for (int b = 0; b < count; ++b) {
+    const psd_block_desc_t& d = h[b];
+    if (d.n < 1 || d.n > kMaxBatchOrder || !d.X || !d.out || d.ld < d.n || d.ld_out < d.n)
       return PSD_ERR_INVALID_ARG;
-  for (const auto& d : h) {
-    if (d.n == 0) continue;
-    psd_status_t st = psd_project_ex(d.n, d.X, d.ld, d.out, d.ld_out, precision, d.info, nullptr, 0, stream);
-    if (st != PSD_OK) return st;
+    const char* x0 = reinterpret_cast<const char*>(d.X);
+    const char* x1 = reinterpret_cast<const char*>(d.X + (d.n - 1) * d.ld + d.n);
+    const char* o0 = reinterpret_cast<const char*>(d.out);
+    const char* o1 = reinterpret_cast<const char*>(d.out + (d.n - 1) * d.ld_out + d.n);
+    if (x0 < o1 && o0 < x1 && !(x0 == o0 && d.ld == d.ld_out)) return PSD_ERR_INVALID_ARG;
+    sizes[b] = static_cast<int>(d.n);
   }
-  return PSD_OK;
+  std::lock_guard<std::mutex> lk(g_bmu);
+  auto key = std::make_tuple(dev, s, static_cast<int>(precision), sizes);
+  BatchPlan* p = nullptr;
+  auto it = g_bplans.find(key);
+  if (it != g_bplans.end()) {
+    p = it->second;
+  } else {
+    p = new BatchPlan();
+    p->prec = precision;
+    p->count = count;
+    p->sizes = sizes;
+    psd_status_t st = build_bplan(p);
+    if (st != PSD_OK) {
+      free_bplan(p);
+      return st;
+    }
+    g_bplans[key] = p;
+  }
+  ensure_bgraph(p);
+  batch_args_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_descs, p->d_rec, p->d_bb, count);
+  if (cudaGetLastError() != cudaSuccess) return PSD_ERR_CUDA;
+  cudaError_t e = p->exec ? cudaGraphLaunch(p->exec, s) : enqueue_batch(p, s);
+  return e == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
 }

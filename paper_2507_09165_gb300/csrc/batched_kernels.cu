@@ -1,0 +1,738 @@
+// Grouped kernels of the batched projection of a block-diagonal cone: the
+// norm bound of every block (Sec. 3.4, Theorem 2) in one sequence of launches,
+// and the scaled cast of every block into the stacked iterate buffers.
+//
+// The mat-vec is one launch over the 128 x 128 upper tiles of all blocks
+// (same per-tile arithmetic as the single-matrix kernel: 8-term FP32 FMA runs
+// combined exactly into double-float partial sums); every vector operation of
+// a block -- the Lanczos recurrence with full re-orthogonalisation, the Ritz
+// vector, the residual and the bound -- runs in one CTA per block in FP64 with
+// a fixed reduction order, so a block's result does not depend on the other
+// blocks of the batch.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace psd {
+
+namespace {
+
+constexpr uint64_t kSeed = 0x243F6A8885A308D3ull;  // Lanczos start vector seed
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+constexpr int kBT = 256;  // threads of a per-block CTA
+constexpr int kEPT = kMaxBatchOrder / kBT;  // elements per thread
+
+struct F2 {
+  float h, l;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return F2{s, __fadd_rn(__fadd_rn(a.l, b.l), e)};
+}
+__device__ __forceinline__ double f2_to_d(F2 a) { return static_cast<double>(a.h) + static_cast<double>(a.l); }
+__device__ __forceinline__ void split_d(double v, float& h, float& l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(v - static_cast<double>(h));
+}
+__device__ __forceinline__ F2 shfl_xor_f2(F2 a, int m) {
+  return F2{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
+}
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * kGolden;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Fixed-order sum over the CTA (kBT threads) of one FP64 value per thread.
+__device__ __forceinline__ double cta_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kBT / 32; ++k) s += sh[k];
+  return s;
+}
+
+// Per-block views of the batched Lanczos buffers.
+struct BView {
+  int n, nb;
+  double* Q;   // (kMaxSteps + 1) x n
+  double* u;   // n
+  double* w;   // n
+  double* q;   // n
+  float* vh;   // n
+  float* vl;   // n
+  float2* P1;  // nb x n
+  float2* P2;  // nb x n
+};
+__device__ __forceinline__ BView view(const BatchLanczos& L, int b) {
+  const BatchBlock& bb = L.blk[b];
+  BView v;
+  v.n = bb.n;
+  v.nb = (bb.n + kSymvTile - 1) / kSymvTile;
+  double* base = L.vec64 + bb.voff * (kMaxSteps + 4);
+  v.Q = base;
+  v.u = base + static_cast<int64_t>(kMaxSteps + 1) * bb.n;
+  v.w = v.u + bb.n;
+  v.q = v.w + bb.n;
+  v.vh = L.vec32 + bb.voff * 2;
+  v.vl = v.vh + bb.n;
+  v.P1 = L.part + bb.poff;
+  v.P2 = v.P1 + static_cast<int64_t>(v.nb) * bb.n;
+  return v;
+}
+
+// ------------------------------------------------------------ grouped mat-vec
+// One 128 x 128 upper tile of block `blk`: same arithmetic as the single-matrix
+// kernel (see normbound.cu), partial sums into the block's P1 / P2.
+template <bool STATS, bool DIAG>
+__device__ __forceinline__ void bsymv_tile(const float* __restrict__ X, int64_t ld, int n, int bi, int bj,
+                                           const float* __restrict__ vh, float2* __restrict__ P1,
+                                           float2* __restrict__ P2, double* __restrict__ tile_fro,
+                                           int tile_slot, unsigned* maxdiag, float2 (*red)[kSymvTile],
+                                           double* fro_sh) {
+  const int i0 = bi * kSymvTile, j0 = bj * kSymvTile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tr = lane & 15, tcol = 2 * warp + (lane >> 4);
+  const int ib = i0 + 8 * tr;
+  const int jb = j0 + 8 * tcol;
+  const bool full = (ib + 7 < n) && (jb + 7 < n);
+  const bool vec = full && ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  float vi[8], vj[8], x[8][8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    vi[k] = (ib + k < n) ? __ldg(vh + ib + k) : 0.f;
+    vj[k] = (jb + k < n) ? __ldg(vh + jb + k) : 0.f;
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float* col = X + static_cast<int64_t>(jb + c) * ld + ib;
+    if (vec) {
+      const float4 a4 = __ldg(reinterpret_cast<const float4*>(col));
+      const float4 b4 = __ldg(reinterpret_cast<const float4*>(col + 4));
+      x[c][0] = a4.x; x[c][1] = a4.y; x[c][2] = a4.z; x[c][3] = a4.w;
+      x[c][4] = b4.x; x[c][5] = b4.y; x[c][6] = b4.z; x[c][7] = b4.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[c][k] = (jb + c < n && ib + k < n) ? __ldg(col + k) : 0.f;
+    }
+  }
+  float rsum[8], csum[8];
+  float fro = 0.f;
+  unsigned mdiag = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) rsum[k] = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    csum[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float xr = x[c][k], xc = x[c][k];
+      if (DIAG) {
+        const int i = ib + k, j = jb + c;
+        xr = (i <= j) ? xr : 0.f;
+        xc = (i < j) ? xc : 0.f;
+        if (STATS && i == j && i < n) mdiag = max(mdiag, __float_as_uint(fabsf(x[c][k])));
+      }
+      rsum[k] = fmaf(xr, vj[c], rsum[k]);
+      csum[c] = fmaf(xc, vi[k], csum[c]);
+      if (STATS) fro = fmaf(xr, xc + xr, fro);
+    }
+  }
+  F2 cs[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float o = __shfl_xor_sync(0xffffffffu, rsum[k], 16);
+    float h, e;
+    if (lane < 16) two_sum(rsum[k], o, h, e); else two_sum(o, rsum[k], h, e);
+    if (lane < 16) red[warp][8 * tr + k] = make_float2(h, e);
+    cs[k] = F2{csum[k], 0.f};
+  }
+#pragma unroll
+  for (int half = 4, m = 8; half >= 1; half >>= 1, m >>= 1) {
+    const bool upper = (tr & m) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const F2 send = upper ? cs[i] : cs[i + half];
+      const F2 keep = upper ? cs[i + half] : cs[i];
+      cs[i] = f2_add(keep, shfl_xor_f2(send, m));
+    }
+  }
+  {
+    const F2 o = shfl_xor_f2(cs[0], 1);
+    cs[0] = (tr & 1) ? f2_add(o, cs[0]) : f2_add(cs[0], o);
+    const int j = jb + (tr >> 1);
+    if ((tr & 1) == 0 && j < n) P2[static_cast<int64_t>(bi) * n + j] = make_float2(cs[0].h, cs[0].l);
+  }
+  __syncthreads();
+  if (threadIdx.x < kSymvTile) {
+    const int r = threadIdx.x;
+    F2 a{red[0][r].x, red[0][r].y};
+#pragma unroll
+    for (int w = 1; w < 8; ++w) a = f2_add(a, F2{red[w][r].x, red[w][r].y});
+    if (i0 + r < n) P1[static_cast<int64_t>(bj) * n + i0 + r] = make_float2(a.h, a.l);
+  }
+  if (STATS) {
+    double f = static_cast<double>(fro);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) fro_sh[warp] = f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mdiag = max(mdiag, __shfl_xor_sync(0xffffffffu, mdiag, o));
+    if (lane == 0 && mdiag) atomicMax(maxdiag, mdiag);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < 8; ++w) sum += fro_sh[w];
+      tile_fro[tile_slot] = sum;
+    }
+  }
+}
+
+// work item: (block, bi, bj, tile slot of the block's tile_fro entries)
+template <bool STATS>
+__global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int4* __restrict__ items) {
+  __shared__ float2 red[8][kSymvTile];
+  __shared__ double fro_sh[8];
+  const int4 it = items[blockIdx.x];
+  const int b = it.x;
+  if (L.st[b].done && !STATS && L.skip_done) return;
+  const BatchBlock& bb = L.blk[b];
+  const BView v = view(L, b);
+  if (it.y == it.z)
+    bsymv_tile<STATS, true>(bb.X, bb.ld, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
+                            &L.st[b].maxdiag_bits, red, fro_sh);
+  else
+    bsymv_tile<STATS, false>(bb.X, bb.ld, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
+                             &L.st[b].maxdiag_bits, red, fro_sh);
+}
+
+// y_e of block b from its partial sums (fixed order, double-float), e < n.
+__device__ __forceinline__ double bred(const BView& v, int e) {
+  const int bk = e / kSymvTile;
+  F2 a{0.f, 0.f};
+  for (int bj = bk; bj < v.nb; ++bj) {
+    const float2 t = v.P1[static_cast<int64_t>(bj) * v.n + e];
+    a = f2_add(a, F2{t.x, t.y});
+  }
+  for (int bi = 0; bi <= bk; ++bi) {
+    const float2 t = v.P2[static_cast<int64_t>(bi) * v.n + e];
+    a = f2_add(a, F2{t.x, t.y});
+  }
+  return f2_to_d(a);
+}
+
+// ------------------------------------------------------------ per-block CTAs
+// Start vector (SplitMix64, normalised), state reset, split for the first product.
+__global__ void __launch_bounds__(kBT) binit_kernel(BatchLanczos L) {
+  __shared__ double sh[kBT / 32];
+  const int b = blockIdx.x;
+  const BView v = view(L, b);
+  double loc[kEPT];
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) {
+    const int e = threadIdx.x + k * kBT;
+    double x = 0.0;
+    if (e < v.n) {
+      const uint64_t z = splitmix64(kSeed, static_cast<uint64_t>(e));
+      x = 2.0 * (static_cast<double>(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+    loc[k] = x;
+    s += x * x;
+  }
+  const double nrm2 = cta_sum(s, sh);
+  const double inv = 1.0 / sqrt(nrm2);
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) {
+    const int e = threadIdx.x + k * kBT;
+    if (e < v.n) {
+      const double q = loc[k] * inv;
+      v.Q[e] = q;
+      split_d(q, v.vh[e], v.vl[e]);
+    }
+  }
+  if (threadIdx.x == 0) {
+    DevState* st = &L.st[b];
+    st->m = 0;
+    st->done = 0;
+    st->status = 0;
+    st->maxdiag_bits = 0;
+    st->absmax_bits = 0;
+    st->sigma = st->resid = st->lambda = st->fro = st->maxdiag = st->inv_lambda = 0.0;
+  }
+}
+
+// ||X_b||_F from the block's tile sums (after the first product).
+__global__ void bfro_kernel(BatchLanczos L) {
+  const int b = blockIdx.x;
+  const BatchBlock& bb = L.blk[b];
+  double f = 0.0;
+  for (int t = threadIdx.x; t < bb.ntiles; t += 32) f += L.tile_fro[bb.toff + t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if (threadIdx.x == 0) L.st[b].fro = sqrt(f);
+}
+
+// u = X v: reduce, store, split for the second product.  MODE 1: Ritz pass (no done check).
+__global__ void __launch_bounds__(kBT) breduce_kernel(BatchLanczos L, int mode) {
+  const int b = blockIdx.x;
+  if (mode == 0 && L.st[b].done) return;
+  const BView v = view(L, b);
+  for (int e = threadIdx.x; e < v.n; e += kBT) {
+    const double y = bred(v, e);
+    v.u[e] = y;
+    split_d(y, v.vh[e], v.vl[e]);
+  }
+}
+
+// Lanczos step j after w = X u: alpha_j, two classical Gram-Schmidt passes,
+// beta_j, breakdown test, q_{j+1} = w / beta_j and its split.
+__global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
+  __shared__ double sh[kBT / 32];
+  __shared__ double h[kMaxSteps + 1];
+  const int b = blockIdx.x;
+  DevState* st = &L.st[b];
+  if (st->done) return;
+  const BView v = view(L, b);
+  double w[kEPT];
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) {
+    const int e = threadIdx.x + k * kBT;
+    w[k] = e < v.n ? bred(v, e) : 0.0;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int kk = 0; kk <= j; ++kk) {
+      double d = 0.0;
+#pragma unroll
+      for (int k = 0; k < kEPT; ++k) {
+        const int e = threadIdx.x + k * kBT;
+        if (e < v.n) d += v.Q[static_cast<int64_t>(kk) * v.n + e] * w[k];
+      }
+      const double t = cta_sum(d, sh);
+      if (threadIdx.x == 0) h[kk] = t;
+    }
+    __syncthreads();
+    if (pass == 0 && threadIdx.x == 0) st->alpha[j] = h[j];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+      const int e = threadIdx.x + k * kBT;
+      if (e < v.n)
+        for (int kk = 0; kk <= j; ++kk) w[k] -= h[kk] * v.Q[static_cast<int64_t>(kk) * v.n + e];
+    }
+    __syncthreads();
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) s += w[k] * w[k];
+  const double beta = sqrt(cta_sum(s, sh));
+  const double fro = st->fro;
+  const bool brk = !(beta > kBreakdown * fro * fro);
+  if (brk || j == kMaxSteps - 1) {
+    if (threadIdx.x == 0) {
+      st->beta[j] = beta;
+      st->m = j + 1;
+      st->done = 1;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    st->beta[j] = beta;
+    st->m = j + 1;
+  }
+  const double inv = 1.0 / beta;
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) {
+    const int e = threadIdx.x + k * kBT;
+    if (e < v.n) {
+      const double q = w[k] * inv;
+      v.Q[static_cast<int64_t>(j + 1) * v.n + e] = q;
+      split_d(q, v.vh[e], v.vl[e]);
+    }
+  }
+}
+
+// Sturm count (division-free leading minors) on the unit-scaled tridiagonal.
+__device__ int bsturm(const double* a, const double* b, int m, double x) {
+  double pm = 1.0, p = a[0] - x;
+  int cnt = (p < 0.0) ? 1 : 0;
+  for (int k = 1; k < m; ++k) {
+    const double pn = (a[k] - x) * p - b[k - 1] * b[k - 1] * pm;
+    const bool change = (pn == 0.0) ? (p > 0.0) : ((pn < 0.0) != (p < 0.0));
+    if (p != 0.0 || pn != 0.0) cnt += change ? 1 : 0;
+    pm = p;
+    p = pn;
+    if (fabs(p) + fabs(pm) > 1e150) {
+      p *= 1e-150;
+      pm *= 1e-150;
+    }
+  }
+  return cnt;
+}
+
+// Largest Ritz pair of each block's tridiagonal (one warp per block):
+// multisection on the Sturm count, inverse iteration with partial pivoting,
+// then q = Q_m y, normalised, split.
+__global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
+  __shared__ double a[kMaxSteps], bt[kMaxSteps], y[kMaxSteps];
+  __shared__ double lo_s, hi_s, scale_s;
+  __shared__ double sh[kBT / 32];
+  const int b = blockIdx.x;
+  DevState* st = &L.st[b];
+  const int m = st->m;
+  const int lane = threadIdx.x;
+  if (threadIdx.x < 32) {
+    if (lane == 0) {
+      double sc = 0.0;
+      for (int k = 0; k < m; ++k) sc = fmax(sc, fabs(st->alpha[k]) + (k < m - 1 ? fabs(st->beta[k]) : 0.0));
+      scale_s = sc > 0.0 ? sc : 1.0;
+    }
+    __syncwarp();
+    const double inv_sc = 1.0 / scale_s;
+    if (lane < m) {
+      a[lane] = st->alpha[lane] * inv_sc;
+      bt[lane] = lane < m - 1 ? st->beta[lane] * inv_sc : 0.0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      double lo = a[0], hi = a[0];
+      for (int k = 0; k < m; ++k) {
+        const double r = (k > 0 ? fabs(bt[k - 1]) : 0.0) + (k < m - 1 ? fabs(bt[k]) : 0.0);
+        lo = fmin(lo, a[k] - r);
+        hi = fmax(hi, a[k] + r);
+      }
+      lo_s = lo;
+      hi_s = hi;
+    }
+    __syncwarp();
+    for (int round = 0; round < 24; ++round) {
+      const double lo = lo_s, hi = hi_s;
+      if (!(hi - lo > 4.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi)))) break;
+      const double x = lo + (hi - lo) * (lane + 1) / 33.0;
+      const int all_below = bsturm(a, bt, m, x) >= m;
+      const unsigned mask = __ballot_sync(0xffffffffu, all_below);
+      __syncwarp();
+      if (lane == 0) {
+        const int first = mask ? __ffs(mask) - 1 : 32;
+        lo_s = first == 0 ? lo : lo + (hi - lo) * first / 33.0;
+        hi_s = first == 32 ? hi : lo + (hi - lo) * (first + 1) / 33.0;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const double sigma = 0.5 * (lo_s + hi_s);
+      const double tiny = 1e-15;
+      double d[kMaxSteps], du[kMaxSteps], du2[kMaxSteps], l[kMaxSteps], rd[kMaxSteps], yy[kMaxSteps];
+      bool piv[kMaxSteps];
+      for (int k = 0; k < m; ++k) {
+        d[k] = a[k] - sigma;
+        du[k] = k < m - 1 ? bt[k] : 0.0;
+        du2[k] = 0.0;
+        piv[k] = false;
+      }
+      for (int k = 0; k < m - 1; ++k) {
+        const double dl = bt[k];
+        if (fabs(d[k]) >= fabs(dl)) {
+          if (d[k] == 0.0) d[k] = tiny;
+          l[k] = dl / d[k];
+          d[k + 1] -= l[k] * du[k];
+        } else {
+          piv[k] = true;
+          l[k] = d[k] / dl;
+          d[k] = dl;
+          const double t = d[k + 1];
+          d[k + 1] = du[k] - l[k] * t;
+          du[k] = t;
+          if (k < m - 2) {
+            du2[k] = du[k + 1];
+            du[k + 1] = -l[k] * du[k + 1];
+          }
+        }
+      }
+      if (d[m - 1] == 0.0) d[m - 1] = tiny;
+      for (int k = 0; k < m; ++k) rd[k] = 1.0 / d[k];
+      for (int k = 0; k < m; ++k) yy[k] = 1.0;
+      for (int it = 0; it < 3; ++it) {
+        for (int k = 0; k < m - 1; ++k) {
+          if (piv[k]) {
+            const double t = yy[k];
+            yy[k] = yy[k + 1];
+            yy[k + 1] = t - l[k] * yy[k];
+          } else {
+            yy[k + 1] -= l[k] * yy[k];
+          }
+        }
+        for (int k = m - 1; k >= 0; --k) {
+          double sacc = yy[k];
+          if (k + 1 < m) sacc -= du[k] * yy[k + 1];
+          if (k + 2 < m) sacc -= du2[k] * yy[k + 2];
+          yy[k] = sacc * rd[k];
+        }
+        double nrm = 0.0;
+        for (int k = 0; k < m; ++k) nrm += yy[k] * yy[k];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+          for (int k = 0; k < m; ++k) yy[k] = k == 0 ? 1.0 : 0.0;
+          break;
+        }
+        const double inv = 1.0 / nrm;
+        for (int k = 0; k < m; ++k) yy[k] *= inv;
+      }
+      for (int k = 0; k < m; ++k) y[k] = yy[k];
+      st->sigma = sigma * scale_s;
+      for (int k = 0; k < kMaxSteps; ++k) st->y[k] = k < m ? yy[k] : 0.0;
+    }
+  }
+  __syncthreads();
+  const BView v = view(L, b);
+  double qv[kEPT];
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) {
+    const int e = threadIdx.x + k * kBT;
+    double t = 0.0;
+    if (e < v.n)
+      for (int kk = 0; kk < m; ++kk) t += y[kk] * v.Q[static_cast<int64_t>(kk) * v.n + e];
+    qv[k] = t;
+    s += t * t;
+  }
+  const double nrm2 = cta_sum(s, sh);
+  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) {
+    const int e = threadIdx.x + k * kBT;
+    if (e < v.n) {
+      const double t = qv[k] * inv;
+      v.q[e] = t;
+      split_d(t, v.vh[e], v.vl[e]);
+    }
+  }
+}
+
+// r = ||X (X q) - sigma q||, lam~ = max(sqrt(sigma + r), ||X||_F / sqrt n, max |X_ii|), report.
+__global__ void __launch_bounds__(kBT) bbound_kernel(BatchLanczos L) {
+  __shared__ double sh[kBT / 32];
+  const int b = blockIdx.x;
+  DevState* st = &L.st[b];
+  const BView v = view(L, b);
+  double s = 0.0;
+  for (int e = threadIdx.x; e < v.n; e += kBT) {
+    const double r = bred(v, e) - st->sigma * v.q[e];
+    s += r * r;
+  }
+  const double r2 = cta_sum(s, sh);
+  if (threadIdx.x != 0) return;
+  const double r = sqrt(r2);
+  const double fro = st->fro;
+  const double md = static_cast<double>(__uint_as_float(st->maxdiag_bits));
+  const double sigma = st->sigma;
+  double lam = sqrt(fmax(sigma + r, 0.0));
+  lam = fmax(lam, fro / sqrt(static_cast<double>(v.n)));
+  lam = fmax(lam, md);
+  st->resid = r;
+  st->maxdiag = md;
+  if (!(isfinite(fro) && isfinite(lam) && isfinite(sigma))) {
+    atomicCAS(&st->status, 0, PSD_ERR_NONFINITE);
+    lam = 0.0;
+  }
+  st->lambda = lam;
+  st->inv_lambda = lam > 0.0 ? 1.0 / lam : 0.0;
+  psd_info_t* info = L.blk[b].info;
+  if (info) {
+    info->lambda_bound = lam;
+    info->lanczos_sigma = sigma;
+    info->lanczos_resid = r;
+    info->fro_X = fro;
+    info->max_diag = md;
+    info->lanczos_steps = st->m;
+    info->status = st->status;
+  }
+}
+
+// ------------------------------------------------------------ grouped cast
+__device__ __forceinline__ void put4_16(uint16_t* H, const uint16_t (&u)[4], int valid) {
+  if (valid == 4) {
+    *reinterpret_cast<uint2*>(H) =
+        make_uint2(u[0] | (static_cast<uint32_t>(u[1]) << 16), u[2] | (static_cast<uint32_t>(u[3]) << 16));
+  } else {
+    for (int k = 0; k < valid; ++k) H[k] = u[k];
+  }
+}
+__device__ __forceinline__ float tf32_round(float v) {
+  if (!isfinite(v)) return v;
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
+
+template <int DT>
+__device__ __forceinline__ void bstore4(const BatchCast& c, int64_t pos, const float (&v)[4], int valid) {
+  if (DT == DT_TF32X3) {
+    float* Mh = static_cast<float*>(c.M) + pos;
+    float* Ml = static_cast<float*>(c.M_lo) + pos;
+    for (int k = 0; k < valid; ++k) {
+      const float h = tf32_round(v[k]);
+      Mh[k] = h;
+      Ml[k] = tf32_round(v[k] - h);
+    }
+  } else if (DT == DT_BF16X3) {
+    uint16_t h[4], l[4], f[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat16 hb = __float2bfloat16_rn(v[k]);
+      h[k] = __bfloat16_as_ushort(hb);
+      l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k] - __bfloat162float(hb)));
+      f[k] = __half_as_ushort(__float2half_rn(v[k]));
+    }
+    put4_16(static_cast<uint16_t*>(c.M) + pos, h, valid);
+    put4_16(static_cast<uint16_t*>(c.M_lo) + pos, l, valid);
+    if (c.M_f16) put4_16(static_cast<uint16_t*>(c.M_f16) + pos, f, valid);
+  } else {
+    uint16_t u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      u[k] = DT == DT_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v[k])) : __half_as_ushort(__float2half_rn(v[k]));
+    put4_16(static_cast<uint16_t*>(c.M) + pos, u, valid);
+  }
+}
+
+// X_0 of every block into the stacked buffers (64 x 64 upper tiles, item =
+// (block, bi, bj)); same arithmetic as the single-matrix cast.
+template <int DT>
+__global__ void __launch_bounds__(256) bcast_kernel(BatchCast c, const BatchBlock* __restrict__ blk,
+                                                    const DevState* __restrict__ st, const int4* __restrict__ items) {
+  __shared__ float s[64][65];
+  const int4 it = items[blockIdx.x];
+  const BatchBlock& bb = blk[it.x];
+  const int n = bb.n;
+  const int i0 = it.y * 64, j0 = it.z * 64;
+  const float* __restrict__ X = bb.X;
+  const int64_t ld = bb.ld;
+  const float inv = static_cast<float>(st[it.x].inv_lambda);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool diag = it.y == it.z;
+  const int ib = i0 + 4 * tx;
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc) {
+    const int jj = ty + 16 * cc, j = j0 + jj;
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    if (j < n) {
+      const float* col = X + static_cast<int64_t>(j) * ld + ib;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (ib + k < n) x[k] = __ldg(col + k);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int ii = 4 * tx + k;
+      s[ii][jj] = (!diag || ii <= jj) ? x[k] * inv : 0.f;
+    }
+  }
+  __syncthreads();
+  if (diag) {
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int jj = ty + 16 * cc;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ii = 4 * tx + k;
+        if (ii > jj) s[ii][jj] = s[jj][ii];
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t rowbase = bb.off;  // stacked rows of this block
+  const int valid_i = min(4, n - ib);
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc) {
+    const int jj = ty + 16 * cc, j = j0 + jj;
+    if (j < n && valid_i > 0) {
+      const float v[4] = {s[4 * tx][jj], s[4 * tx + 1][jj], s[4 * tx + 2][jj], s[4 * tx + 3][jj]};
+      bstore4<DT>(c, (rowbase + j) * c.ldm + ib, v, valid_i);
+    }
+    const int i = i0 + jj, jc = j0 + 4 * tx;
+    const int valid_j = min(4, n - jc);
+    if (!diag && i < n && valid_j > 0) {
+      const float v[4] = {s[jj][4 * tx], s[jj][4 * tx + 1], s[jj][4 * tx + 2], s[jj][4 * tx + 3]};
+      bstore4<DT>(c, (rowbase + i) * c.ldm + jc, v, valid_j);
+    }
+  }
+}
+
+// Status and overshoot of every block into its report.
+__global__ void bfinalize_kernel(const BatchBlock* __restrict__ blk, DevState* st, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const float amax = __uint_as_float(st[b].absmax_bits);
+  int status = st[b].status;
+  if (status == 0) {
+    if (!(amax == amax) || isinf(amax))
+      status = PSD_ERR_NONFINITE;
+    else if (amax > kOvershootLimit)
+      status = PSD_ERR_BOUND;
+    st[b].status = status;
+  }
+  psd_info_t* info = blk[b].info;
+  if (info) {
+    info->overshoot_max = static_cast<double>(amax);
+    info->status = status;
+  }
+}
+
+}  // namespace
+
+cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int4* symv_items, int nsymv,
+                                     cudaStream_t s) {
+  BatchLanczos Lk = L;
+  Lk.skip_done = 0;
+  binit_kernel<<<count, kBT, 0, s>>>(Lk);
+  for (int j = 0; j < kMaxSteps; ++j) {
+    Lk.skip_done = j == 0 ? 0 : 1;
+    if (j == 0) {
+      bsymv_kernel<true><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+      bfro_kernel<<<count, 32, 0, s>>>(Lk);
+    } else {
+      bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+    }
+    breduce_kernel<<<count, kBT, 0, s>>>(Lk, 0);
+    Lk.skip_done = 1;
+    bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+    bstep_kernel<<<count, kBT, 0, s>>>(Lk, j);
+  }
+  britz_kernel<<<count, kBT, 0, s>>>(Lk);
+  Lk.skip_done = 0;
+  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+  breduce_kernel<<<count, kBT, 0, s>>>(Lk, 1);
+  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+  bbound_kernel<<<count, kBT, 0, s>>>(Lk);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* blk, const DevState* st,
+                               const int4* items, int nitems, cudaStream_t s) {
+  switch (dtype) {
+    case DT_F16: bcast_kernel<DT_F16><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
+    case DT_BF16: bcast_kernel<DT_BF16><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
+    case DT_TF32X3: bcast_kernel<DT_TF32X3><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
+    default: bcast_kernel<DT_BF16X3><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, cudaStream_t s) {
+  bfinalize_kernel<<<(count + 127) / 128, 128, 0, s>>>(blk, st, count);
+  return cudaGetLastError();
+}
+
+}  // namespace psd

@@ -97,6 +97,15 @@ struct GemmParams {
 // its diagonal (128 columns); tile widths are trimmed at n (multiples of 16).
 std::vector<int4> make_tile_list(int64_t n, int block = 0);
 
+// Coefficients of the run-time filter (Tables 1 and 2) and the per-stage
+// divisors s_t of Sec. 3.4 for a precision (psdproj.cu).
+struct Schedule {
+  int T;
+  double coef[kMaxStages][3];
+  double post[kMaxStages];  // s_t
+};
+bool get_schedule(psd_precision_t prec, Schedule& s);
+
 // --- host helpers (symgemm.cu) ---
 bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows);
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
@@ -106,6 +115,46 @@ cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUt
 cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm, const GemmParams& p, int grid,
                               cudaStream_t stream);
 int num_sms();
+
+// --- batched projection of a block-diagonal cone (batched_kernels.cu) ---
+constexpr int kMaxBatchOrder = 1024;  // largest block order of a batched call
+
+struct BatchBlock {       // per-block record of the batched norm bound and cast
+  int n;
+  int ntiles;             // mat-vec tiles of the block
+  int64_t off;            // first row of the block in the stacked iterate buffers
+  int64_t voff;           // element offset of the block's vectors
+  int64_t poff;           // float2 offset of the block's partial sums
+  int64_t toff;           // offset of the block's per-tile Frobenius sums
+  const float* X;         // caller input (upper triangle), column-major
+  int64_t ld;
+  psd_info_t* info;       // caller report (may be null)
+};
+
+struct BatchLanczos {
+  const BatchBlock* blk;
+  DevState* st;           // one per block
+  double* vec64;          // per block: (kMaxSteps + 4) x n  (Lanczos vectors, u, w, q)
+  float* vec32;           // per block: 2 x n  (hi / lo of the mat-vec input)
+  float2* part;           // per block: 2 x nb x n  (row / column partial sums)
+  double* tile_fro;       // per mat-vec tile
+  int skip_done;
+};
+
+struct BatchCast {
+  void* M;                // X_0: stacked iterate buffer (hi part of a pair)
+  void* M_lo;
+  void* M_f16;            // mixed: the FP16 copy
+  int64_t ldm;
+};
+
+cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int4* symv_items, int nsymv,
+                                     cudaStream_t stream);
+cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* blk, const DevState* st,
+                               const int4* items, int nitems, cudaStream_t stream);
+cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, cudaStream_t stream);
+bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t cols, int64_t rows, int64_t ld,
+                      int box_rows);
 
 // --- norm bound and cast (normbound.cu) ---
 struct LanczosBufs {

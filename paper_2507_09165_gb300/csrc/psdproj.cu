@@ -41,11 +41,7 @@ const double kSingleCoef[10][3] = {
     {1.9220135179, -1.2812524618, 0.3707011753},   {1.8942192942, -1.2613293407, 0.3676616051},
 };
 
-struct Schedule {
-  int T;
-  double coef[kMaxStages][3];
-  double post[kMaxStages];  // s_t
-};
+}  // namespace
 
 // Sec. 3.4: half divides the iterate by 1.01 after every stage but the last;
 // single divides by 1.001 after each of the first eight stages.
@@ -71,6 +67,8 @@ bool get_schedule(psd_precision_t prec, Schedule& s) {
       return false;
   }
 }
+
+namespace {
 
 // Storage of the iterates per precision: 16-bit single matrices (FP16, BF16),
 // TF32 hi/lo pairs (FP32 path), or BF16 hi/lo pairs for the first kMixedSplit

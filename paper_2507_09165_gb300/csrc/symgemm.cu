@@ -508,6 +508,25 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
   return r == CUDA_SUCCESS;
 }
 
+// Tensor map of a stacked buffer of `rows` rows (row stride ld elements) of
+// which the first `cols` columns are addressed; same boxes as encode_tmap.
+bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t cols, int64_t rows, int64_t ld,
+                      int box_rows) {
+  EncodeFn fn = get_encode();
+  if (!fn) return false;
+  const int esz = dtype == DT_TF32X3 ? 4 : 2;
+  const CUtensorMapDataType dt = dtype == DT_F16                          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : (dtype == DT_BF16 || dtype == DT_BF16X3) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // Upper-triangle tiles of 256 x 256 blocks, each split into two 128-row
 // tiles, in a grouped raster: block rows are taken in groups of 8, and inside
 // a group the columns advance first so that the tiles resident at one time

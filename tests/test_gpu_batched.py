@@ -1,0 +1,130 @@
+"""GPU tests of the batched projection of a block-diagonal cone (grouped
+launches over all blocks), through the C ABI: parity of every block against
+the CPU FP64 oracle's filter output, bit-identity of a block alone and in the
+batch, caller leading dimensions and in-place outputs, argument checks."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2507_09165_gb300 import binding as b  # noqa: E402
+from paper_2507_09165_gb300 import synth  # noqa: E402
+
+DEV = torch.device("cuda")
+TOL_F = {"fp16": 2e-3, "bf16": 2.5e-2, "mixed": 1e-3, "fp32": 3e-8 * 1024}
+SCHED = {"fp16": "half", "bf16": "half", "mixed": "half", "fp32": "single"}
+SIZES = [1, 7, 33, 64, 100, 128, 129, 200, 256, 300, 513, 1024]
+
+
+class Batch:
+    def __init__(self, mats, ld_pad=0, out_pad=0, inplace=()):
+        self.n = [m.shape[0] for m in mats]
+        self.X, self.out, self.info, self.ld, self.ldo = [], [], [], [], []
+        for i, M in enumerate(mats):
+            n = M.shape[0]
+            ld = n + ld_pad
+            t = torch.zeros((n, ld), dtype=torch.float32)
+            t[:, :n] = torch.from_numpy(M)
+            Xd = t.to(DEV)
+            if i in inplace:
+                out, ldo = Xd, ld
+            else:
+                ldo = n + out_pad
+                out = torch.full((n, ldo), float("nan"), dtype=torch.float32, device=DEV)
+            self.X.append(Xd)
+            self.out.append(out)
+            self.ld.append(ld)
+            self.ldo.append(ldo)
+            self.info.append(torch.zeros(b.INFO_BYTES, dtype=torch.uint8, device=DEV))
+
+    def run(self, prec):
+        descs = b.block_descs([(n, X, ld, out, ldo, inf) for n, X, ld, out, ldo, inf in
+                               zip(self.n, self.X, self.ld, self.out, self.ldo, self.info)])
+        b.psd_project_batched(len(self.n), descs, prec)
+        torch.cuda.synchronize()
+        outs = [o.cpu().numpy()[:, :n].astype(np.float64) for o, n in zip(self.out, self.n)]
+        infos = [b.info_from_bytes(i.cpu().numpy()) for i in self.info]
+        return outs, infos
+
+
+@pytest.fixture(scope="module")
+def mats():
+    out = []
+    for i, n in enumerate(SIZES):
+        X = synth.gaussian_symmetric(n, 900 + i) if i % 2 else synth.wigner(n, 900 + i)
+        ref = oracle.oracle_project(X.astype(np.float64), "half")
+        coefs, scales = oracle.schedules.schedule("single")
+        ref["F_single"] = oracle.filter_from_eig(ref["lam"], ref["Q"], ref["lam_tilde"], coefs, scales)
+        out.append((X, ref))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "mixed", "fp32"])
+def test_batched_matches_oracle(mats, prec):
+    B = Batch([m for m, _ in mats])
+    outs, infos = B.run(prec)
+    for (X, ref), o, inf, n in zip(mats, outs, infos, SIZES):
+        assert inf["status"] == 0, (n, inf)
+        assert inf["lambda_bound"] == pytest.approx(ref["lam_tilde"], rel=1e-6)
+        assert np.array_equal(o, o.T)
+        F = ref["F_single"] if SCHED[prec] == "single" else ref["F"]
+        if n == 1:
+            assert abs(o[0, 0] - F[0, 0]) <= TOL_F[prec] * abs(X[0, 0]) + 1e-30
+            continue
+        rel = oracle.rel_err(o, F)
+        assert rel <= TOL_F[prec], (n, prec, rel)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "mixed"])
+def test_block_alone_and_in_batch_bitwise(mats, prec):
+    B = Batch([m for m, _ in mats])
+    outs, _ = B.run(prec)
+    for k in (0, 5, 8, 11):
+        A = Batch([mats[k][0]])
+        alone, _ = A.run(prec)
+        assert np.array_equal(alone[0], outs[k]), SIZES[k]
+    # a different batch composition (reversed order, some blocks dropped)
+    sub = [mats[k][0] for k in (11, 8, 5, 0)]
+    C = Batch(sub)
+    outs2, _ = C.run(prec)
+    for k, o in zip((11, 8, 5, 0), outs2):
+        assert np.array_equal(o, outs[k])
+
+
+def test_batched_leading_dims_and_inplace(mats):
+    sub = [mats[k][0] for k in (2, 7, 9)]
+    B1 = Batch(sub)
+    ref, _ = B1.run("fp16")
+    B2 = Batch(sub, ld_pad=5, out_pad=3, inplace=(1,))
+    got, infos = B2.run("fp16")
+    for a, c, inf in zip(ref, got, infos):
+        assert inf["status"] == 0
+        assert np.array_equal(a, c)
+
+
+def test_batched_config_workload_sampled():
+    # 512 Wigner blocks, orders log-uniform in [16, 1024] (seed 7); parity on a sample
+    sizes = synth.block_sizes(512, 7)
+    rng = np.random.default_rng(0)
+    mats = [synth.wigner(n, 7000 + i) for i, n in enumerate(sizes)]
+    B = Batch(mats)
+    outs, infos = B.run("bf16")
+    assert all(inf["status"] == 0 for inf in infos)
+    for i in rng.choice(512, size=4, replace=False):
+        X = mats[i].astype(np.float64)
+        ref = oracle.oracle_project(X, "half")
+        assert oracle.rel_err(outs[i], ref["F"]) <= TOL_F["bf16"]
+
+
+def test_batched_rejects_bad_blocks():
+    X = torch.zeros((1025, 1025), device=DEV)
+    with pytest.raises(b.PsdError):
+        b.psd_project_batched(1, b.block_descs([(1025, X, 1025, X, 1025, None)]), "bf16")
+    Y = torch.zeros((8, 8), device=DEV)
+    with pytest.raises(b.PsdError):
+        b.psd_project_batched(1, b.block_descs([(8, Y, 7, Y, 8, None)]), "bf16")
+    with pytest.raises(b.PsdError):
+        b.psd_project_batched(1, b.block_descs([(8, Y, 8, Y, 8, None)]), "fp8_early")
