@@ -299,11 +299,43 @@ __global__ void __launch_bounds__(kBT) breduce_kernel(BatchLanczos L, int mode) 
   }
 }
 
-// Lanczos step j after w = X u: alpha_j, two classical Gram-Schmidt passes,
-// beta_j, breakdown test, q_{j+1} = w / beta_j and its split.
+// Sum over the CTA of up to 32 values per thread (v[k] for k <= j), fixed
+// order: recursive halving inside each warp (lane l ends with value l), then
+// the 8 warp sums of value k added by thread k.  Result in h[0..j].
+__device__ __forceinline__ void cta_multi_sum(double (&v)[kMaxSteps + 1], int j, double (*sh)[32], double* h) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double t[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) t[k] = (k <= j && k <= kMaxSteps) ? v[k <= kMaxSteps ? k : 0] : 0.0;
+#pragma unroll
+  for (int half = 16, m = 16; half >= 1; half >>= 1, m >>= 1) {
+    const bool upper = (lane & m) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double send = upper ? t[i] : t[i + half];
+      const double keep = upper ? t[i + half] : t[i];
+      t[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  __syncthreads();
+  sh[w][lane] = t[0];
+  __syncthreads();
+  if (threadIdx.x <= j) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kBT / 32; ++q) s += sh[q][threadIdx.x];
+    h[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Lanczos step j after w = X u: alpha_j, two classical Gram-Schmidt passes
+// (all j + 1 projections of a pass reduced together), beta_j, breakdown test,
+// q_{j+1} = w / beta_j and its split.
 __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
-  __shared__ double sh[kBT / 32];
-  __shared__ double h[kMaxSteps + 1];
+  __shared__ double sh[kBT / 32][32];
+  __shared__ double h[32];
+  __shared__ double shs[kBT / 32];
   const int b = blockIdx.x;
   DevState* st = &L.st[b];
   if (st->done) return;
@@ -315,17 +347,19 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
     w[k] = e < v.n ? bred(v, e) : 0.0;
   }
   for (int pass = 0; pass < 2; ++pass) {
-    for (int kk = 0; kk <= j; ++kk) {
-      double d = 0.0;
+    double d[kMaxSteps + 1];
 #pragma unroll
-      for (int k = 0; k < kEPT; ++k) {
-        const int e = threadIdx.x + k * kBT;
-        if (e < v.n) d += v.Q[static_cast<int64_t>(kk) * v.n + e] * w[k];
+    for (int kk = 0; kk <= kMaxSteps; ++kk) d[kk] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+      const int e = threadIdx.x + k * kBT;
+      if (e < v.n) {
+#pragma unroll
+        for (int kk = 0; kk <= kMaxSteps; ++kk)
+          if (kk <= j) d[kk] += v.Q[static_cast<int64_t>(kk) * v.n + e] * w[k];
       }
-      const double t = cta_sum(d, sh);
-      if (threadIdx.x == 0) h[kk] = t;
     }
-    __syncthreads();
+    cta_multi_sum(d, j, sh, h);
     if (pass == 0 && threadIdx.x == 0) st->alpha[j] = h[j];
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) {
@@ -333,12 +367,11 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
       if (e < v.n)
         for (int kk = 0; kk <= j; ++kk) w[k] -= h[kk] * v.Q[static_cast<int64_t>(kk) * v.n + e];
     }
-    __syncthreads();
   }
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) s += w[k] * w[k];
-  const double beta = sqrt(cta_sum(s, sh));
+  const double beta = sqrt(cta_sum(s, shs));
   const double fro = st->fro;
   const bool brk = !(beta > kBreakdown * fro * fro);
   if (brk || j == kMaxSteps - 1) {
