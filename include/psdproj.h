@@ -58,7 +58,8 @@ typedef enum {
   PSD_ERR_BOUND = 5,       /* device: max |X_T(i,j)| exceeded 1 + 1e-2: the norm
                               bound was below ||X||_2 and the filter diverged */
   PSD_ERR_TIMEOUT = 6,     /* device: a bounded wait inside a kernel gave up */
-  PSD_ERR_UNSUPPORTED = 7  /* no sm_103 device, or precision not built */
+  PSD_ERR_UNSUPPORTED = 7, /* no sm_103 device, or precision not built */
+  PSD_ERR_CANCELED = 8     /* server: the request was canceled before it ran */
 } psd_status_t;
 
 typedef enum {
@@ -68,7 +69,9 @@ typedef enum {
   PSD_PREC_FP16 = 1,  /* f~*_half (Table 2), T = 7, 22 products, FP16 operands,
                          FP32 accumulation in tensor memory */
   PSD_PREC_BF16 = 2,  /* as FP16 with BF16 operands */
-  PSD_PREC_MIXED = 3, /* FP16 stages, final product in FP32 (TF32 split) */
+  PSD_PREC_MIXED = 3, /* f~*_half; stages 1-3 on BF16 hi/lo split operands
+                         (three BF16 products each), stages 4-7 and the final
+                         product in FP16; FP32 accumulation throughout */
   PSD_PREC_FP8_EARLY = 4 /* reserved: not built, returns PSD_ERR_UNSUPPORTED */
 } psd_precision_t;
 
@@ -175,6 +178,93 @@ psd_status_t psd_symm_product(int64_t n, const void *A, const void *B, int64_t l
                               int64_t ld_out, psd_precision_t precision, int32_t epi,
                               const double *params, const void *aux, int64_t ld_aux,
                               float *d_absmax, psd_stream_t stream);
+
+/* ---- Request server: continuous batching of projections ------------------
+ * Not in the paper: a serving layer that runs Algorithm 2 for many requests
+ * at once.  A server owns one device allocation of hbm_budget_bytes, carved at
+ * creation into
+ *   - an arena of 16-bit rows (row length ldm = max_order rounded up to 64):
+ *     a request of order n holds 4 n contiguous rows for X_0, two rotating
+ *     iterates and the stage polynomial, the four matrices of one stage;
+ *   - per-request records (argument block, device state, report), max_batch
+ *     of them;
+ *   - the Lanczos scratch of two preparation streams (norm bound of order up
+ *     to max_order each).
+ * A host thread admits queued requests in arrival order while their rows and
+ * a record fit, runs their norm bound and X_0 = X / lam~ on a preparation
+ * stream, and lets each join the running set at the next stage boundary.
+ * Every scheduler step then advances all running requests by one stage of
+ * Algorithm 2 with one grouped launch per product (X^2, the polynomial,
+ * X P / s_t) and per operand type, each request at its own stage with its own
+ * coefficients; requests that finish their last stage get the final product
+ * and their report in the same step.
+ *
+ * Results: each request's arithmetic (norm bound kernels, tile partition,
+ * summation order, coefficients and roundings) is that of psd_project with the
+ * same precision, so its output and report are bit-identical to a
+ * psd_project call on the same input, however many other requests share its
+ * launches.  Precisions: PSD_PREC_FP16 and PSD_PREC_BF16 (others return
+ * PSD_ERR_UNSUPPORTED at submit).
+ *
+ * Threads: every function may be called from any host thread; the server's
+ * own thread is the only one that issues GPU work for it. */
+typedef struct psd_server psd_server_t;
+/* Same type as cudaEvent_t. */
+typedef struct CUevent_st *psd_event_t;
+
+/* Creates a server on `device`.  max_order (1..131072)
+ * bounds n of every request; max_batch (1..1024) bounds the requests admitted
+ * at one time (prepared or running).  Returns PSD_ERR_NO_MEMORY if the budget
+ * cannot hold one request of order max_order or the allocation fails,
+ * PSD_ERR_UNSUPPORTED if the device is not sm_103. */
+psd_status_t psd_server_create(size_t hbm_budget_bytes, int32_t device, int64_t max_order, int32_t max_batch,
+                               psd_server_t **server);
+
+/* Queues one projection and returns at once with *ticket.  X (upper triangle,
+ * ld >= n) and out (ld_out >= n) are caller-owned device memory that must stay
+ * valid and untouched until the ticket completes; out == X with ld_out == ld is
+ * allowed.  If `ready` is not NULL the server's streams wait for that event
+ * before reading X (record it on the stream that produced X).  n == 0 gives a
+ * ticket that is complete at once.  Errors: PSD_ERR_INVALID_ARG (n > max_order,
+ * bad pointer, ld or overlap), PSD_ERR_UNSUPPORTED (precision). */
+psd_status_t psd_server_submit(psd_server_t *server, int64_t n, const float *X, int64_t ld, float *out,
+                               int64_t ld_out, psd_precision_t precision, psd_event_t ready,
+                               uint64_t *ticket);
+
+/* *done = 1 once the result is in `out` (the server's GPU work for it has
+ * finished).  A completed ticket is retired by the poll or wait that reports
+ * it: host_info (may be NULL) receives the report (status: the psd_status_t of
+ * the device-side work, or PSD_ERR_CANCELED) and latency_ms (may be NULL) the
+ * time from submit to completion.  Unknown or retired tickets:
+ * PSD_ERR_INVALID_ARG. */
+psd_status_t psd_server_poll(psd_server_t *server, uint64_t ticket, int32_t *done, psd_info_t *host_info,
+                             double *latency_ms);
+
+/* Blocks until the ticket completes, then behaves as psd_server_poll with
+ * done = 1.  timeout_ms > 0 bounds the wait (PSD_ERR_TIMEOUT, ticket kept). */
+psd_status_t psd_server_wait(psd_server_t *server, uint64_t ticket, int64_t timeout_ms, psd_info_t *host_info,
+                             double *latency_ms);
+
+/* Cancels a request that is still queued (not admitted): it completes with
+ * status PSD_ERR_CANCELED and `out` untouched.  An admitted request runs to
+ * the end: PSD_ERR_UNSUPPORTED. */
+psd_status_t psd_server_cancel(psd_server_t *server, uint64_t ticket);
+
+typedef struct {
+  uint64_t submitted, completed, canceled;
+  uint64_t steps;            /* scheduler steps (one stage of every running request) */
+  uint64_t kernel_launches;  /* kernels and graphs the server launched */
+  int32_t queued, admitted;  /* now */
+  int32_t max_running;       /* most requests advanced by one step */
+  int32_t pad;
+  double p50_ms, p99_ms, max_ms; /* submit -> completion, completed requests */
+  int64_t arena_rows, peak_rows; /* arena size and most rows held at once */
+} psd_server_stats_t;
+psd_status_t psd_server_stats(psd_server_t *server, psd_server_stats_t *stats);
+
+/* Cancels queued requests, lets admitted ones finish, stops the thread and
+ * frees the server's memory.  Tickets not yet retired are lost. */
+psd_status_t psd_server_destroy(psd_server_t *server);
 
 /* ---- Host-only queries (no GPU needed) ----------------------------------- */
 const char *psd_status_string(psd_status_t status);

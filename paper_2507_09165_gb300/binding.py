@@ -18,7 +18,8 @@ from . import _build
 
 PSD_OK = 0
 STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID_ARG", 2: "PSD_ERR_CUDA", 3: "PSD_ERR_NO_MEMORY",
-          4: "PSD_ERR_NONFINITE", 5: "PSD_ERR_BOUND", 6: "PSD_ERR_TIMEOUT", 7: "PSD_ERR_UNSUPPORTED"}
+          4: "PSD_ERR_NONFINITE", 5: "PSD_ERR_BOUND", 6: "PSD_ERR_TIMEOUT", 7: "PSD_ERR_UNSUPPORTED",
+          8: "PSD_ERR_CANCELED"}
 PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "mixed": 3, "fp8_early": 4}
 
 
@@ -43,6 +44,17 @@ class psd_block_desc_t(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("ld_out", ctypes.c_int64), ("info", ctypes.c_void_p)]
 
 
+class psd_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("canceled", ctypes.c_uint64),
+                ("steps", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("queued", ctypes.c_int32), ("admitted", ctypes.c_int32), ("max_running", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("arena_rows", ctypes.c_int64), ("peak_rows", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 _lib = None
 
 _VP, _I64, _I32, _SZ, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_double
@@ -62,6 +74,14 @@ _SIGS = {
     "psd_gemm_count": ([_I32], _I32),
     "psd_kernel_launches": ([_I64, _I32, _VP], _I32),
     "psd_version": ([], ctypes.c_char_p),
+    "psd_server_create": ([_SZ, _I32, _I64, _I32, ctypes.POINTER(_VP)], _I32),
+    "psd_server_submit": ([_VP, _I64, _VP, _I64, _VP, _I64, _I32, _VP, ctypes.POINTER(ctypes.c_uint64)], _I32),
+    "psd_server_poll": ([_VP, ctypes.c_uint64, ctypes.POINTER(_I32), ctypes.POINTER(psd_info_t),
+                         ctypes.POINTER(_D)], _I32),
+    "psd_server_wait": ([_VP, ctypes.c_uint64, _I64, ctypes.POINTER(psd_info_t), ctypes.POINTER(_D)], _I32),
+    "psd_server_cancel": ([_VP, ctypes.c_uint64], _I32),
+    "psd_server_stats": ([_VP, ctypes.POINTER(psd_server_stats_t)], _I32),
+    "psd_server_destroy": ([_VP], _I32),
 }
 
 
@@ -221,6 +241,60 @@ def block_descs(blocks, device="cuda"):
         arr[i] = psd_block_desc_t(n, _ptr(X), ld, _ptr(out), ld_out, _ptr(info))
     raw = bytes(arr)
     return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
+def psd_server_create(hbm_budget_bytes, device=0, max_order=8192, max_batch=64):
+    """Returns the server handle (an integer)."""
+    h = ctypes.c_void_p()
+    _check(lib().psd_server_create(hbm_budget_bytes, device, max_order, max_batch, ctypes.byref(h)),
+           "psd_server_create")
+    return h.value
+
+
+def _event(e):
+    if e is None:
+        return None
+    if hasattr(e, "cuda_event"):
+        return e.cuda_event
+    return int(e)
+
+
+def psd_server_submit(server, n, X, ld, out, ld_out, precision="bf16", ready=None):
+    """Queues one projection; `ready` is an event (torch.cuda.Event or handle) to wait for. Returns the ticket."""
+    t = ctypes.c_uint64()
+    _check(lib().psd_server_submit(server, n, _ptr(X), ld, _ptr(out), ld_out, _prec(precision), _event(ready),
+                                   ctypes.byref(t)), "psd_server_submit")
+    return t.value
+
+
+def psd_server_poll(server, ticket):
+    """(done, info dict or None, latency_ms or None); a completed ticket is retired."""
+    done, info, lat = _I32(), psd_info_t(), _D()
+    _check(lib().psd_server_poll(server, ticket, ctypes.byref(done), ctypes.byref(info), ctypes.byref(lat)),
+           "psd_server_poll")
+    return (True, info.as_dict(), lat.value) if done.value else (False, None, None)
+
+
+def psd_server_wait(server, ticket, timeout_ms=0):
+    """Blocks until the ticket completes; returns (info dict, latency_ms)."""
+    info, lat = psd_info_t(), _D()
+    _check(lib().psd_server_wait(server, ticket, timeout_ms, ctypes.byref(info), ctypes.byref(lat)),
+           "psd_server_wait")
+    return info.as_dict(), lat.value
+
+
+def psd_server_cancel(server, ticket):
+    _check(lib().psd_server_cancel(server, ticket), "psd_server_cancel")
+
+
+def psd_server_stats(server):
+    st = psd_server_stats_t()
+    _check(lib().psd_server_stats(server, ctypes.byref(st)), "psd_server_stats")
+    return st.as_dict()
+
+
+def psd_server_destroy(server):
+    _check(lib().psd_server_destroy(server), "psd_server_destroy")
 
 
 INFO_BYTES = ctypes.sizeof(psd_info_t)

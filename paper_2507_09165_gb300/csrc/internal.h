@@ -63,12 +63,17 @@ enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_BF16X3 = 3 };
 struct BlockRec {
   int64_t off;          // first row in the stacked iterate buffers
   int n;                // order
-  int pad;
+  int track;            // absmax_blocks == 2: track max |output| of this block
   const float* X;       // EPI_FINAL: caller input (upper triangle), column-major
   int64_t ld;
   float* out;           // EPI_FINAL: caller output
   int64_t ld_out;
   DevState* st;         // lam~, and the max |X_T| of the last stage
+  float ca, cb, cc, cs; // per-block stage coefficients (EpiParams::per_block_coef)
+  // Row offsets of the B operand, the output C and the EPI_POLY operand Y,
+  // relative to `off` (the A operand's first row).  Zero when every operand of
+  // the block sits at the same rows of its own buffer.
+  int64_t db, dc, dy;
 };
 
 struct EpiParams {
@@ -79,7 +84,9 @@ struct EpiParams {
   const void* Y_lo;
   int64_t ldy;
   float a, b, c, s;      // EPI_POLY coefficients, EPI_SCALE factor
-  int absmax_blocks;     // nonzero: atomic max of |output| into blocks[b].st->absmax_bits
+  int absmax_blocks;     // 1: atomic max of |output| into blocks[b].st->absmax_bits;
+                         // 2: the same for the blocks with a nonzero `track`
+  int per_block_coef;    // nonzero: a, b, c, s from each tile's block record
   unsigned* absmax;      // if set: atomic max of |output| into this word instead
   int* status;           // device status word for timeouts
 };
@@ -189,5 +196,29 @@ cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t str
 cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t stream);
 cudaError_t enqueue_state_reset(DevState* st, cudaStream_t stream);
 cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t stream);
+
+// Status and overshoot of the last stage: a non-finite or overshooting X_T
+// (max |X_T(i,j)| > kOvershootLimit) turns an OK status into an error; the
+// result goes to the state and, if given, the report.
+__device__ __forceinline__ void finalize_report(DevState* st, psd_info_t* info) {
+  const float amax = __uint_as_float(st->absmax_bits);
+  int status = st->status;
+  if (status == 0) {
+    if (!(amax == amax) || isinf(amax))
+      status = PSD_ERR_NONFINITE;
+    else if (amax > kOvershootLimit)
+      status = PSD_ERR_BOUND;
+    st->status = status;
+  }
+  if (info) {
+    info->overshoot_max = static_cast<double>(amax);
+    info->status = status;
+  }
+}
+
+// Kernel launches of one enqueue_norm_bound: start vector (2), the Lanczos
+// steps (7 each, plus the Frobenius norm in the first), the tridiagonal
+// solve, Ritz vector and residual (8).
+constexpr int kNormBoundLaunches = 2 + 7 * kMaxSteps + 1 + 8;
 
 }  // namespace psd

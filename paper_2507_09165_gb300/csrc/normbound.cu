@@ -813,22 +813,7 @@ __global__ void set_args_kernel(DevArgs* d, DevArgs h, BlockRec* blk) {
 __global__ void set_block_kernel(BlockRec* dst, BlockRec v) { *dst = v; }
 
 // Status word and overshoot of the last stage into the report.
-__global__ void finalize_kernel(const DevArgs* args, DevState* st) {
-  const float amax = __uint_as_float(st->absmax_bits);
-  int status = st->status;
-  if (status == 0) {
-    if (!(amax == amax) || isinf(amax))
-      status = PSD_ERR_NONFINITE;
-    else if (amax > kOvershootLimit)
-      status = PSD_ERR_BOUND;
-    st->status = status;
-  }
-  psd_info_t* info = args->info;
-  if (info) {
-    info->overshoot_max = static_cast<double>(amax);
-    info->status = status;
-  }
-}
+__global__ void finalize_kernel(const DevArgs* args, DevState* st) { finalize_report(st, args->info); }
 
 }  // namespace
 

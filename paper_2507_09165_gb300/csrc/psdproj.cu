@@ -626,6 +626,7 @@ const char* psd_status_string(psd_status_t status) {
     case PSD_ERR_BOUND: return "norm bound below ||X||_2: the filter diverged";
     case PSD_ERR_TIMEOUT: return "a bounded device wait timed out";
     case PSD_ERR_UNSUPPORTED: return "unsupported device or precision";
+    case PSD_ERR_CANCELED: return "request canceled before it ran";
     default: return "unknown status";
   }
 }

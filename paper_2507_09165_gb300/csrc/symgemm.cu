@@ -109,10 +109,13 @@ __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t* src, int f
 // from their upper part; off-diagonal chunks are written at both positions,
 // (r, c) and (c, r), with 16-byte stores from the staged copies.
 template <int EPI>
-__device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16, int n, uint16_t* C, int r0,
-                                                 int c0, const uint32_t (&v)[32], uint8_t* wbuf,
-                                                 const uint4 (&y)[4], int lane, bool track,
+__device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const BlockRec& br, bool bf16, int n,
+                                                 uint16_t* C, int r0, int c0, const uint32_t (&v)[32],
+                                                 uint8_t* wbuf, const uint4 (&y)[4], int lane, bool track,
                                                  unsigned& amax_bits) {
+  const bool pb = p.ep.per_block_coef != 0;
+  const float ca = pb ? br.ca : p.ep.a, cb = pb ? br.cb : p.ep.b, cc = pb ? br.cc : p.ep.c;
+  const float cs = pb ? br.cs : p.ep.s;
   uint16_t* S = reinterpret_cast<uint16_t*>(wbuf);  // [32][kH] row t = output row r0 + t
   uint16_t* ST = S + 32 * kH;                        // [32][kH] row j = output column c0 + j
   uint16_t* YB = ST + 32 * kH;                       // [32][kH] row j = Y column c0 + j
@@ -131,10 +134,10 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, bool bf16,
     float val;
     if (EPI == EPI_POLY) {
       const float yv = from16(YB[j * kH + lane], bf16);
-      val = fmaf(p.ep.c, acc, p.ep.b * yv);
-      if (diag && j == lane) val += p.ep.a;
+      val = fmaf(cc, acc, cb * yv);
+      if (diag && j == lane) val += ca;
     } else if (EPI == EPI_SCALE) {
-      val = acc * p.ep.s;
+      val = acc * cs;
     } else {
       val = acc;
     }
@@ -297,9 +300,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
         const int4 tc = p.tiles[t];
-        const int64_t off = p.blocks[tc.z].off;
-        const int kbn = (p.blocks[tc.z].n + kBK16 - 1) / kBK16;
-        const int ya = static_cast<int>(off + tc.x), yb = static_cast<int>(off + tc.y);
+        const BlockRec& bz = p.blocks[tc.z];
+        const int kbn = (bz.n + kBK16 - 1) / kBK16;
+        const int ya = static_cast<int>(bz.off + tc.x), yb = static_cast<int>(bz.off + bz.db + tc.y);
         for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t acc = 0, acc_ph = 0;
     unsigned amax_bits = 0;  // max |output| of the current block (absmax_blocks) or of the launch
     int amax_block = -1;
-    const bool track = p.ep.absmax_blocks != 0 || p.ep.absmax != nullptr;
+    const bool track_launch = p.ep.absmax_blocks != 0 || p.ep.absmax != nullptr;
     auto flush_amax = [&](int blk) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
@@ -397,9 +400,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const BlockRec& br = p.blocks[tc.z];
       const int n = br.n;
       const int64_t off = br.off;
-      uint16_t* C = static_cast<uint16_t*>(p.ep.C) + off * p.ep.ldc;
-      const uint16_t* Y = static_cast<const uint16_t*>(p.ep.Y) + off * p.ep.ldy;
-      if (track && amax_block != tc.z) {
+      uint16_t* C = static_cast<uint16_t*>(p.ep.C) + (off + br.dc) * p.ep.ldc;
+      const uint16_t* Y = static_cast<const uint16_t*>(p.ep.Y) + (off + br.dy) * p.ep.ldy;
+      const bool track = track_launch && (p.ep.absmax_blocks != 2 || br.track != 0);
+      if (track_launch && amax_block != tc.z) {
         if (amax_block >= 0) flush_amax(amax_block);
         amax_block = tc.z;
       }
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (EPI == EPI_FINAL)
           epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam);
         else
-          epilogue_chunk16<EPI>(p, bf16, n, C, r0, c0, v, wbuf, ycur, lane, track, amax_bits);
+          epilogue_chunk16<EPI>(p, br, bf16, n, C, r0, c0, v, wbuf, ycur, lane, track, amax_bits);
       }
       tc_fence_before();
       __syncwarp();
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       acc ^= 1u;
       if (acc == 0) acc_ph ^= 1u;
     }
-    if (EPI != EPI_FINAL && track && amax_block >= 0) flush_amax(amax_block);
+    if (EPI != EPI_FINAL && track_launch && amax_block >= 0) flush_amax(amax_block);
   }
 
   tc_fence_before();

@@ -119,12 +119,15 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
                                                   bool track, unsigned& amax_bits) {
   const int n = br.n;
   const int64_t off = br.off;
+  const bool pb = p.ep.per_block_coef != 0;
+  const float ca = pb ? br.ca : p.ep.a, cb = pb ? br.cb : p.ep.b, cc = pb ? br.cc : p.ep.c;
+  const float cs = pb ? br.cs : p.ep.s;
   const int64_t esz = OUT == 1 ? 2 : (TF32 ? 4 : 2);  // element size of the iterate output
-  void* C = static_cast<uint8_t*>(p.ep.C) + off * p.ep.ldc * esz;
-  void* C_lo = p.ep.C_lo ? static_cast<uint8_t*>(p.ep.C_lo) + off * p.ep.ldc * esz : nullptr;
+  void* C = static_cast<uint8_t*>(p.ep.C) + (off + br.dc) * p.ep.ldc * esz;
+  void* C_lo = p.ep.C_lo ? static_cast<uint8_t*>(p.ep.C_lo) + (off + br.dc) * p.ep.ldc * esz : nullptr;
   const int64_t ysz = TF32 ? 4 : 2;
-  const void* Yh = p.ep.Y ? static_cast<const uint8_t*>(p.ep.Y) + off * p.ep.ldy * ysz : nullptr;
-  const void* Yl = p.ep.Y_lo ? static_cast<const uint8_t*>(p.ep.Y_lo) + off * p.ep.ldy * ysz : nullptr;
+  const void* Yh = p.ep.Y ? static_cast<const uint8_t*>(p.ep.Y) + (off + br.dy) * p.ep.ldy * ysz : nullptr;
+  const void* Yl = p.ep.Y_lo ? static_cast<const uint8_t*>(p.ep.Y_lo) + (off + br.dy) * p.ep.ldy * ysz : nullptr;
   const int r = r0 + lane;
   const bool diag = (r0 == c0);
   const bool row_ok = r < n;
@@ -153,10 +156,10 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
     const float acc = __uint_as_float(v[j]);
     float val;
     if (EPI == EPI_POLY) {
-      val = fmaf(p.ep.c, acc, p.ep.b * YB[j * kSW + lane]);
-      if (diag && j == lane) val += p.ep.a;
+      val = fmaf(cc, acc, cb * YB[j * kSW + lane]);
+      if (diag && j == lane) val += ca;
     } else if (EPI == EPI_SCALE) {
-      val = acc * p.ep.s;
+      val = acc * cs;
     } else if (EPI == EPI_FINAL) {
       const int c = c0 + j;
       float x = 0.f;
@@ -283,9 +286,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
         const int4 tc = p.tiles[t];
-        const int64_t boff = p.blocks[tc.z].off;
-        const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
-        const int ya = static_cast<int>(boff + tc.x), yb = static_cast<int>(boff + tc.y);
+        const BlockRec& bz = p.blocks[tc.z];
+        const int kbn = (bz.n + kKElems - 1) / kKElems;
+        const int ya = static_cast<int>(bz.off + tc.x), yb = static_cast<int>(bz.off + bz.db + tc.y);
         for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t acc = 0, acc_ph = 0;
     unsigned amax_bits = 0;
     int amax_block = -1;
-    const bool track = p.ep.absmax_blocks != 0 || p.ep.absmax != nullptr;
+    const bool track_launch = p.ep.absmax_blocks != 0 || p.ep.absmax != nullptr;
     auto flush_amax = [&](int blk) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
@@ -392,7 +395,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int4 tc = p.tiles[t];
       const BlockRec& br = p.blocks[tc.z];
       const int n = br.n;
-      if (track && amax_block != tc.z) {
+      const bool track = track_launch && (p.ep.absmax_blocks != 2 || br.track != 0);
+      if (track_launch && amax_block != tc.z) {
         if (amax_block >= 0) flush_amax(amax_block);
         amax_block = tc.z;
       }
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       acc ^= 1u;
       if (acc == 0) acc_ph ^= 1u;
     }
-    if (track && amax_block >= 0) flush_amax(amax_block);
+    if (track_launch && amax_block >= 0) flush_amax(amax_block);
   }
 
   tc_fence_before();
