@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp32-path", action="store_true", help="skip timing the FP32 comparator path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-block batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the ADMM serving leg")
+    ap.add_argument("--serve-rate", type=float, default=8.0, help="ADMM solve arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=2.5, help="length of the arrival window")
+    ap.add_argument("--serve-iters", type=int, default=50, help="ADMM iterations per solve")
     return ap.parse_args()
 
 
@@ -162,6 +167,70 @@ def accuracy_check(n, prec, dev, seed=20):
             "rel_err_F": rel_f, "rel_err_Pi": rel_pi, "status": inf["status"],
             "lambda_bound": inf["lambda_bound"], "lambda_true": float(np.max(np.abs(lam))),
             "seconds": time.perf_counter() - t0}
+
+
+def batched_leg(dev, prec="bf16", reps=5):
+    """512 Wigner blocks, sizes log-uniform in [16, 1024] (seed 7), one psd_project_batched call."""
+    import numpy as np
+    import torch
+    from paper_2507_09165_gb300 import binding as b, synth
+    sizes = synth.block_sizes(512, 7)
+    X = [torch.from_numpy(synth.wigner(n, 7000 + i)).to(dev) for i, n in enumerate(sizes)]
+    O = [torch.empty_like(x) for x in X]
+    descs = b.block_descs([(n, x, n, o, n, None) for n, x, o in zip(sizes, X, O)], dev)
+    s = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        b.psd_project_batched(len(sizes), descs, prec, s)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ts = []
+    for _ in range(reps):
+        ev[0].record(s)
+        b.psd_project_batched(len(sizes), descs, prec, s)
+        ev[1].record(s)
+        torch.cuda.synchronize(dev)
+        ts.append(ev[0].elapsed_time(ev[1]))
+    ms = float(np.median(ts))
+    flops = 22.0 * sum(n ** 3 for n in sizes)
+    return {"workload": "512 Wigner blocks, orders log-uniform in [16, 1024] (seed 7; sum n = %d, max %d)"
+                        % (sum(sizes), max(sizes)),
+            "precision": prec, "ms": ms, "ms_all": ts, "blocks_per_s": len(sizes) / (ms * 1e-3),
+            "tflops_22n3": flops / (ms * 1e-3) / 1e12}
+
+
+def serving_leg(dev, args, prec="bf16"):
+    """Interleaved ADMM solves (min <C,X>, diag X = 1, X PSD; C = Laplacian of G(n, 0.01),
+    n in {500, 2000, 8000}, seeds 8-10) as Poisson-arriving requests to one psd_server."""
+    import numpy as np
+    import torch
+    from paper_2507_09165_gb300 import admm, binding as b, synth
+    graphs = {n: torch.from_numpy(synth.er_laplacian(n, seed).astype(np.float32)).to(dev)
+              for n, seed in ((500, 8), (2000, 9), (8000, 10))}
+    server = b.psd_server_create(48 << 30, dev.index or 0, 8000, 64)
+    try:
+        # warm-up: a graph of the norm bound per (order, preparation stream)
+        warm = []
+        for n, C in graphs.items():
+            for _ in range(2):
+                o = torch.empty_like(C)
+                warm.append((b.psd_server_submit(server, n, C, n, o, n, prec), o))
+        for t, _ in warm:
+            b.psd_server_wait(server, t)
+        base = b.psd_server_stats(server)
+        res = admm.run_serving(server, graphs, prec, solve_rate=args.serve_rate,
+                               arrival_seconds=args.serve_seconds, iters=args.serve_iters, seed=5)
+        st = b.psd_server_stats(server)
+    finally:
+        b.psd_server_destroy(server)
+    out = admm.summarize(res)
+    out.update(workload="ADMM solves of min <C,X>, diag(X) = 1, X PSD; C = Laplacian of G(n, 0.01), n in "
+                        "{500, 2000, 8000} (seeds 8-10); solves Poisson at %.1f/s for %.1f s, %d iterations each, "
+                        "Exp(0.5 ms) think time; sigma log-uniform in [0.5, 2]"
+                        % (args.serve_rate, args.serve_seconds, args.serve_iters),
+               precision=prec, latency="submit -> completion callback on the host, per request",
+               steps=st["steps"] - base["steps"], kernel_launches=st["kernel_launches"] - base["kernel_launches"],
+               max_running=st["max_running"], budget_gb=48)
+    return out
 
 
 def run_reference(args):
@@ -294,6 +363,12 @@ def run_ours(args):
         ev1.record(s)
         torch.cuda.synchronize(dev)
         fp32_ms = ev0.elapsed_time(ev1) / k32
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_leg(dev)
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = serving_leg(dev, args)
     acc = None
     if rank == 0 and not args.no_accuracy:
         acc = accuracy_check(n, prec, dev)
@@ -327,6 +402,8 @@ def run_ours(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "accuracy": acc,
+            "batched": batched,
+            "serving": serving,
             "info": {k: info[k] for k in ("lambda_bound", "lanczos_steps", "overshoot_max")},
         }
         print(json.dumps(line), flush=True)
