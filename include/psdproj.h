@@ -72,7 +72,13 @@ typedef enum {
   PSD_PREC_MIXED = 3, /* f~*_half; stages 1-3 on BF16 hi/lo split operands
                          (three BF16 products each), stages 4-7 and the final
                          product in FP16; FP32 accumulation throughout */
-  PSD_PREC_FP8_EARLY = 4 /* reserved: not built, returns PSD_ERR_UNSUPPORTED */
+  PSD_PREC_FP8_EARLY = 4, /* reserved, returns PSD_ERR_UNSUPPORTED: e4m3 iterates in
+                             the first stages diverge (the stage-1 coefficients
+                             amplify the rounding of X^2 beyond the filter's basin) */
+  PSD_PREC_FP8_LATE = 5   /* f~*_half; stages 1-5 as FP16, stages 6-7 on e4m3
+                             operands (kind::f8f6f4) with power-of-two per-matrix
+                             scales, X_T and the final product in FP16; relative
+                             error vs the FP64 filter output ~2-3e-2 */
 } psd_precision_t;
 
 /* Per-projection report, written by the device. */
@@ -172,7 +178,13 @@ psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
  *   epi 2: C = (A B) * s
  *   epi 3: C = (Xf + lam * A B) / 2       (FP32 out with leading dim ld_out,
  *                                          Xf = aux FP32 upper triangle, ld_aux)
- * params: {a, b, c} for epi 1, {s} for epi 2, {lam} for epi 3.
+ *   precision FP8_LATE: single e4m3 matrices (1 byte per element, ld a
+ *     multiple of 16); epi 0-2 only, output e4m3.  Every e4m3 matrix holds its
+ *     values times a power of two: after the epilogue's own params come
+ *     {in_scale, y_scale, out_scale}: the accumulator is multiplied by
+ *     in_scale, Y by y_scale, and C is rounded (saturating) from
+ *     value * out_scale.
+ * params: {a, b, c} for epi 1, {s} for epi 2, {lam} for epi 3 (then the FP8 scales).
  * d_absmax (may be NULL): device float receiving max |C(i,j)| (atomic max). */
 psd_status_t psd_symm_product(int64_t n, const void *A, const void *B, int64_t ld, void *C,
                               int64_t ld_out, psd_precision_t precision, int32_t epi,

@@ -20,7 +20,7 @@ PSD_OK = 0
 STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID_ARG", 2: "PSD_ERR_CUDA", 3: "PSD_ERR_NO_MEMORY",
           4: "PSD_ERR_NONFINITE", 5: "PSD_ERR_BOUND", 6: "PSD_ERR_TIMEOUT", 7: "PSD_ERR_UNSUPPORTED",
           8: "PSD_ERR_CANCELED"}
-PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "mixed": 3, "fp8_early": 4}
+PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2, "mixed": 3, "fp8_early": 4, "fp8_late": 5}
 
 
 class PsdError(RuntimeError):
@@ -172,7 +172,8 @@ def psd_project_batched(count, d_descs, precision="bf16", stream=None):
            "psd_project_batched")
 
 
-_PRODUCT_BYTES = {"fp16": (1, 2), "bf16": (1, 2), "mixed": (2, 2), "fp32": (2, 4)}
+_PRODUCT_BYTES = {"fp16": (1, 2), "bf16": (1, 2), "mixed": (2, 2), "fp32": (2, 4), "fp8_late": (1, 1)}
+_FP8_PARAMS = {0: 3, 1: 6, 2: 4}  # epilogue params followed by (in_scale, y_scale, out_scale)
 
 
 def _check_extent(t, need, what):
@@ -198,6 +199,8 @@ def psd_symm_product(n, A, B, ld, C, ld_out=0, precision="fp16", epi=0, params=(
             _check_extent(C, need, "C")
             if epi == 1:
                 _check_extent(aux, need, "aux (Y)")
+    if pname == "fp8_late" and len(params) < _FP8_PARAMS.get(epi, 0):
+        raise ValueError("fp8_late epilogue %d takes %d params" % (epi, _FP8_PARAMS[epi]))
     arr = (ctypes.c_double * max(1, len(params)))(*params) if params else None
     _check(lib().psd_symm_product(n, _ptr(A), _ptr(B), ld, _ptr(C), ld_out, _prec(precision), epi, arr,
                                   _ptr(aux), ld_aux, _ptr(d_absmax), _stream(stream)), "psd_symm_product")

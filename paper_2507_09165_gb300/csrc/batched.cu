@@ -347,7 +347,8 @@ extern "C" psd_status_t psd_project_batched(int32_t count, const psd_block_desc_
   if (count < 0 || (count > 0 && !d_descs)) return PSD_ERR_INVALID_ARG;
   if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16 && precision != PSD_PREC_FP32 &&
       precision != PSD_PREC_MIXED)
-    return precision == PSD_PREC_FP8_EARLY ? PSD_ERR_UNSUPPORTED : PSD_ERR_INVALID_ARG;
+    return (precision == PSD_PREC_FP8_EARLY || precision == PSD_PREC_FP8_LATE) ? PSD_ERR_UNSUPPORTED
+                                                                               : PSD_ERR_INVALID_ARG;
   if (count == 0) return PSD_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PSD_ERR_CUDA;

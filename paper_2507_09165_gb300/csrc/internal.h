@@ -55,7 +55,7 @@ enum Epi : int { EPI_COPY = 0, EPI_POLY = 1, EPI_SCALE = 2, EPI_FINAL = 3 };
 
 // Operand storage of the chain: single 16-bit matrices, TF32 hi/lo pairs
 // (FP32 containers), BF16 hi/lo pairs.
-enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_BF16X3 = 3 };
+enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_BF16X3 = 3, DT_E4M3 = 4 };
 
 // One symmetric matrix of a product launch.  A launch covers one matrix
 // (single projection) or many (block-diagonal cone, served requests); the
@@ -87,6 +87,11 @@ struct EpiParams {
   int absmax_blocks;     // 1: atomic max of |output| into blocks[b].st->absmax_bits;
                          // 2: the same for the blocks with a nonzero `track`
   int per_block_coef;    // nonzero: a, b, c, s from each tile's block record
+  // e4m3 operands / outputs (the 16-bit kernel's FP8 instances): every e4m3
+  // matrix holds its values times a power of two; the accumulator is
+  // multiplied by in_scale = 1 / (scale_A scale_B), the EPI_POLY operand Y by
+  // y_scale = 1 / scale_Y, and an e4m3 output is rounded from value * out_scale.
+  float in_scale, y_scale, out_scale;
   unsigned* absmax;      // if set: atomic max of |output| into this word instead
   int* status;           // device status word for timeouts
 };
@@ -115,8 +120,10 @@ bool get_schedule(psd_precision_t prec, Schedule& s);
 
 // --- host helpers (symgemm.cu) ---
 bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows);
+// dtype: operand type (DT_F16, DT_BF16 or DT_E4M3); out_dtype: type of the
+// EPI_COPY/POLY/SCALE output (DT_F16, DT_BF16 or DT_E4M3; -1: the operand type).
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                           const GemmParams& p, int grid, cudaStream_t stream);
+                           const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1);
 // split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
 // out: 0 = split pair, 1 = single FP16, (EPI_FINAL) FP32 to the caller's output.
 cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm, const GemmParams& p, int grid,

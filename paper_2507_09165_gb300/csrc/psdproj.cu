@@ -12,6 +12,7 @@
 // into a CUDA graph; the caller's pointers reach the graph through a small
 // device argument block written by a one-thread kernel in front of each replay.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -50,6 +51,7 @@ bool get_schedule(psd_precision_t prec, Schedule& s) {
     case PSD_PREC_FP16:
     case PSD_PREC_BF16:
     case PSD_PREC_MIXED:
+    case PSD_PREC_FP8_LATE:
       s.T = 7;
       for (int t = 0; t < 7; ++t) {
         for (int k = 0; k < 3; ++k) s.coef[t][k] = kHalfCoef[t][k];
@@ -74,11 +76,33 @@ namespace {
 // TF32 hi/lo pairs (FP32 path), or BF16 hi/lo pairs for the first kMixedSplit
 // stages followed by FP16 (mixed).
 constexpr int kMixedSplit = 3;
+// FP8_LATE: the last kFp8Stages stages on e4m3 operands.  The first stages
+// cannot be: their coefficients (a_1 = 8.29, b_1 = -22.6) amplify the e4m3
+// rounding of X^2 (u = 2^-4) beyond the composite's basin.
+constexpr int kFp8Stages = 2;
+// Power-of-two scales of the e4m3 matrices: |X_t(i,j)|, |Y(i,j)| <= their
+// spectral norms <= 1.25 (the filter keeps the spectrum near [-1, 1]), so
+// 256 x 1.25 = 320 stays below the e4m3 maximum 448; P's scale comes from
+// max |a + b y + c y^2| over y in [0, 1.25].
+constexpr float kFp8ScaleX = 256.f;
+constexpr float kFp8ScaleY = 256.f;
+
+float fp8_poly_scale(const double (&c)[3]) {
+  double m = 0.0;
+  const double ys[3] = {0.0, 1.25, c[2] != 0.0 ? -c[1] / (2.0 * c[2]) : 0.0};
+  for (double y : ys)
+    if (y >= 0.0 && y <= 1.25) m = std::max(m, std::fabs(c[0] + c[1] * y + c[2] * y * y));
+  double sc = 1.0;
+  while (sc * 2.0 * m < 400.0) sc *= 2.0;
+  while (sc > 1.0 / 1024 && sc * m >= 400.0) sc *= 0.5;
+  return static_cast<float>(sc);
+}
 
 int dtype16_of(psd_precision_t prec) { return prec == PSD_PREC_BF16 ? DT_BF16 : DT_F16; }
 
 bool prec_built(psd_precision_t prec) {
-  return prec == PSD_PREC_FP16 || prec == PSD_PREC_BF16 || prec == PSD_PREC_FP32 || prec == PSD_PREC_MIXED;
+  return prec == PSD_PREC_FP16 || prec == PSD_PREC_BF16 || prec == PSD_PREC_FP32 || prec == PSD_PREC_MIXED ||
+         prec == PSD_PREC_FP8_LATE;
 }
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
@@ -96,7 +120,7 @@ int slots_needed(psd_precision_t prec) {
   switch (prec) {
     case PSD_PREC_FP32: return 16;   // X_0, X_{t-1}, P, X_t as TF32 pairs (Y and X_t share)
     case PSD_PREC_MIXED: return 9;   // X_0 pair + X_0 FP16 + three BF16 pairs
-    default: return 4;               // X_0 + three rotating 16-bit matrices
+    default: return 4;               // X_0 + three rotating 16-bit (or e4m3) matrices
   }
 }
 
@@ -206,14 +230,15 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
 }
 
 // A matrix of the chain living in workspace slots.
-enum MatKind : int { MK_16 = 0, MK_BF16X3 = 1, MK_TF32X3 = 2 };
+enum MatKind : int { MK_16 = 0, MK_BF16X3 = 1, MK_TF32X3 = 2, MK_E4M3 = 3 };
 struct Mat {
   int kind = MK_16;
   int slot = -1;
   int dt16 = DT_F16;  // element type of an MK_16 matrix
+  float scale = 1.f;  // MK_E4M3: stored value = RN_e4m3(value * scale)
 };
 
-int kind_slots(int kind) { return kind == MK_16 ? 1 : kind == MK_BF16X3 ? 2 : 4; }
+int kind_slots(int kind) { return kind == MK_16 || kind == MK_E4M3 ? 1 : kind == MK_BF16X3 ? 2 : 4; }
 
 struct SlotPool {
   uint32_t used = 0;
@@ -236,7 +261,9 @@ void* part_ptr(const Plan* p, const Mat& m, int part) {
   return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * step)) * p->slot_size;
 }
 
-int part_dtype(const Mat& m) { return m.kind == MK_16 ? m.dt16 : m.kind == MK_BF16X3 ? DT_BF16X3 : DT_TF32X3; }
+int part_dtype(const Mat& m) {
+  return m.kind == MK_16 ? m.dt16 : m.kind == MK_E4M3 ? DT_E4M3 : m.kind == MK_BF16X3 ? DT_BF16X3 : DT_TF32X3;
+}
 
 GemmParams base_params(const Plan* p) {
   GemmParams g{};
@@ -260,23 +287,26 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
   g.ep.absmax = absmax;
   if (epi != EPI_FINAL) {
     g.ep.C = part_ptr(p, *out, 0);
-    g.ep.C_lo = out->kind == MK_16 ? nullptr : part_ptr(p, *out, 1);
+    g.ep.C_lo = (out->kind == MK_16 || out->kind == MK_E4M3) ? nullptr : part_ptr(p, *out, 1);
     g.ep.ldc = ldm;
   }
   if (epi == EPI_POLY) {
     g.ep.Y = part_ptr(p, *Y, 0);
-    g.ep.Y_lo = Y->kind == MK_16 ? nullptr : part_ptr(p, *Y, 1);
+    g.ep.Y_lo = (Y->kind == MK_16 || Y->kind == MK_E4M3) ? nullptr : part_ptr(p, *Y, 1);
     g.ep.ldy = ldm;
   }
+  g.ep.in_scale = 1.f / (A.scale * B.scale);
+  g.ep.y_scale = Y ? 1.f / Y->scale : 1.f;
+  g.ep.out_scale = out ? out->scale : 1.f;
   const int grid = num_sms();
-  if (A.kind == MK_16) {
+  if (A.kind == MK_16 || A.kind == MK_E4M3) {
+    const int dt = part_dtype(A);
     CUtensorMap ta, tb;
-    if (!encode_tmap(&ta, A.dt16, part_ptr(p, A, 0), n, ldm, 128) ||
-        !encode_tmap(&tb, B.dt16, part_ptr(p, B, 0), n, ldm, 256))
+    if (!encode_tmap(&ta, dt, part_ptr(p, A, 0), n, ldm, 128) || !encode_tmap(&tb, dt, part_ptr(p, B, 0), n, ldm, 256))
       return cudaErrorInvalidValue;
-    const uint32_t fmt = A.dt16 == DT_BF16 ? 1u : 0u;
+    const uint32_t fmt = dt == DT_BF16 ? 1u : 0u;  // F16 and E4M3 are both format 0 in their MMA kinds
     g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);  // M = 128; N per tile
-    return launch_symgemm(A.dt16, epi, ta, tb, g, grid, s);
+    return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? part_dtype(*out) : -1);
   }
   const int dt = part_dtype(A);
   CUtensorMap tm[4];
@@ -299,13 +329,15 @@ cudaError_t enqueue_projection(Plan* p, cudaStream_t s) {
   auto kind_of_stage = [&](int t) {
     if (p->prec == PSD_PREC_FP32) return static_cast<int>(MK_TF32X3);
     if (p->prec == PSD_PREC_MIXED && t < kMixedSplit) return static_cast<int>(MK_BF16X3);
+    if (p->prec == PSD_PREC_FP8_LATE && t >= T - kFp8Stages) return static_cast<int>(MK_E4M3);
     return static_cast<int>(MK_16);
   };
   const int dt16 = dtype16_of(p->prec);
-  auto make = [&](int kind) {
+  auto make = [&](int kind, float scale = 1.f) {
     Mat m;
     m.kind = kind;
     m.dt16 = dt16;
+    m.scale = kind == MK_E4M3 ? scale : 1.f;
     m.slot = pool.alloc(kind_slots(kind));
     return m;
   };
@@ -324,17 +356,17 @@ cudaError_t enqueue_projection(Plan* p, cudaStream_t s) {
     const int k = kind_of_stage(t);
     const int knext = t + 1 < T ? kind_of_stage(t + 1) : static_cast<int>(MK_16);
     const int kout = (p->prec == PSD_PREC_FP32) ? static_cast<int>(MK_TF32X3) : knext;
-    Mat Y = make(k);
+    Mat Y = make(k, kFp8ScaleY);
     if (Y.slot < 0) return cudaErrorMemoryAllocation;
     if ((e = gemm(p, EPI_COPY, cur, cur, &Y, nullptr, 0.f, 0.f, 0.f, 1.f, nullptr, s)) != cudaSuccess) return e;
-    Mat P = make(k);
+    Mat P = make(k, fp8_poly_scale(p->sched.coef[t]));
     if (P.slot < 0) return cudaErrorMemoryAllocation;
     if ((e = gemm(p, EPI_POLY, Y, Y, &P, &Y, static_cast<float>(p->sched.coef[t][0]),
                   static_cast<float>(p->sched.coef[t][1]), static_cast<float>(p->sched.coef[t][2]), 1.f, nullptr,
                   s)) != cudaSuccess)
       return e;
     pool.release(Y.slot, kind_slots(Y.kind));
-    Mat Xn = make(kout);
+    Mat Xn = make(kout, kFp8ScaleX);
     if (Xn.slot < 0) return cudaErrorMemoryAllocation;
     unsigned* amax = (t == T - 1) ? &p->d_state->absmax_bits : nullptr;
     if ((e = gemm(p, EPI_SCALE, cur, P, &Xn, nullptr, 0.f, 0.f, 0.f, static_cast<float>(1.0 / p->sched.post[t]),
@@ -409,7 +441,7 @@ psd_status_t project_impl(int64_t n, const float* X, int64_t ld, float* out, int
                           psd_precision_t prec, psd_info_t* d_info, void* ws, size_t ws_bytes,
                           cudaStream_t stream) {
   if (n < 0 || n > kMaxOrder) return PSD_ERR_INVALID_ARG;
-  if (prec < PSD_PREC_FP32 || prec > PSD_PREC_FP8_EARLY) return PSD_ERR_INVALID_ARG;
+  if (prec < PSD_PREC_FP32 || prec > PSD_PREC_FP8_LATE) return PSD_ERR_INVALID_ARG;
   if (n == 0) return PSD_OK;
   if (!X || !out || ld < n || ld_out < n) return PSD_ERR_INVALID_ARG;
   if (ranges_overlap(X, out, n, ld, ld_out) && !(static_cast<const void*>(X) == out && ld == ld_out))
@@ -468,7 +500,7 @@ psd_status_t psd_project_ex(int64_t n, const float* X, int64_t ld, float* out, i
 }
 
 size_t psd_workspace_size(int64_t n, psd_precision_t precision) {
-  if (n <= 0 || n > kMaxOrder || precision < PSD_PREC_FP32 || precision > PSD_PREC_FP8_EARLY) return 0;
+  if (n <= 0 || n > kMaxOrder || precision < PSD_PREC_FP32 || precision > PSD_PREC_FP8_LATE) return 0;
   return total_ws_bytes(n, precision);
 }
 
@@ -524,8 +556,10 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
                               int64_t ld_aux, float* d_absmax, psd_stream_t stream) {
   if (n <= 0 || n > kMaxOrder || !A || !B || !C || ld < n || (ld % 8) != 0) return PSD_ERR_INVALID_ARG;
   const bool split = precision == PSD_PREC_MIXED || precision == PSD_PREC_FP32;
-  if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16 && !split) return PSD_ERR_INVALID_ARG;
+  const bool f8 = precision == PSD_PREC_FP8_LATE;
+  if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16 && !split && !f8) return PSD_ERR_INVALID_ARG;
   if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;
+  if (f8 && (epi == 3 || (ld % 16) != 0 || !params)) return PSD_ERR_INVALID_ARG;
   if ((epi == 1 || epi == 2 || epi == 3) && !params) return PSD_ERR_INVALID_ARG;
   if ((epi == 1 || epi == 3) && !aux) return PSD_ERR_INVALID_ARG;
   if (epi == 3 && (ld_aux < n || ld_out < n)) return PSD_ERR_INVALID_ARG;
@@ -561,8 +595,9 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   const int dtype = precision == PSD_PREC_BF16    ? DT_BF16
                     : precision == PSD_PREC_MIXED ? DT_BF16X3
                     : precision == PSD_PREC_FP32  ? DT_TF32X3
+                    : f8                          ? DT_E4M3
                                                   : DT_F16;
-  const size_t esz = dtype == DT_TF32X3 ? 4 : 2;
+  const size_t esz = dtype == DT_TF32X3 ? 4 : (f8 ? 1 : 2);
   const size_t pair = static_cast<size_t>(n) * static_cast<size_t>(ld) * esz;  // byte offset of the lo part
   GemmParams g{};
   g.num_tiles = ps.ntiles[n];
@@ -584,6 +619,13 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     g.ep.s = static_cast<float>(params[0]);
   } else if (epi == 3) {
     set_lambda_kernel<<<1, 1, 0, s>>>(ps.d_state, params[0]);
+    g.ep.absmax = nullptr;
+  }
+  if (f8) {
+    const double* sc = params + (epi == 0 ? 0 : epi == 1 ? 3 : 1);
+    g.ep.in_scale = static_cast<float>(sc[0]);
+    g.ep.y_scale = static_cast<float>(sc[1]);
+    g.ep.out_scale = static_cast<float>(sc[2]);
     g.ep.absmax = nullptr;
   }
   BlockRec br{};

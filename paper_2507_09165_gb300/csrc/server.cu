@@ -723,7 +723,7 @@ extern "C" psd_status_t psd_server_submit(psd_server_t* s, int64_t n, const floa
                                           int64_t ld_out, psd_precision_t precision, psd_event_t ready,
                                           uint64_t* ticket) {
   if (!s || !ticket) return PSD_ERR_INVALID_ARG;
-  if (precision < PSD_PREC_FP32 || precision > PSD_PREC_FP8_EARLY) return PSD_ERR_INVALID_ARG;
+  if (precision < PSD_PREC_FP32 || precision > PSD_PREC_FP8_LATE) return PSD_ERR_INVALID_ARG;
   if (n < 0 || n > s->max_order) return PSD_ERR_INVALID_ARG;
   if (n > 0) {
     if (!X || !out || ld < n || ld_out < n) return PSD_ERR_INVALID_ARG;

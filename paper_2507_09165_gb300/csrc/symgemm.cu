@@ -21,6 +21,7 @@
 // tile overlap the main loop of the next.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -36,8 +37,10 @@ constexpr int kBM = 128;
 constexpr int kBN = 256;
 constexpr int kThreads = 192;
 
-// 16-bit operands: 64 K-elements per stage (one 128-byte swizzle row).
+// 16-bit operands: 64 K-elements per stage (one 128-byte swizzle row); e4m3
+// operands: 128.  The stage layout in bytes is the same for both.
 constexpr int kBK16 = 64;
+constexpr int kBK8 = 128;
 constexpr int kStages16 = 4;
 constexpr int kABytes16 = kBM * kBK16 * 2;          // 16 KB
 constexpr int kBBytes16 = kBN * kBK16 * 2;          // 32 KB
@@ -63,6 +66,10 @@ __device__ __forceinline__ uint16_t to16(float v, bool bf16) {
 }
 __device__ __forceinline__ float from16(uint16_t u, bool bf16) {
   return bf16 ? __bfloat162float(__ushort_as_bfloat16(u)) : __half2float(__ushort_as_half(u));
+}
+
+__device__ __forceinline__ uint16_t to8(float v) {
+  return static_cast<uint16_t>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
 }
 
 __device__ __forceinline__ void raise_status(int* status, int code) {
@@ -93,6 +100,64 @@ __device__ __forceinline__ void load_y_chunk(const uint16_t* __restrict__ Y, int
   }
 }
 
+// The same chunk of a symmetric e4m3 matrix (8 bytes per lane and row),
+// decoded to FP16 and multiplied by ysc (a power of two: exact).
+__device__ __forceinline__ void load_y_chunk8(const uint8_t* __restrict__ Y, int64_t ldy, int n, int r0, int c0,
+                                              int lane, __half2 ysc, uint4 (&y)[4]) {
+  const int r = r0 + 8 * (lane & 3);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = c0 + (lane >> 2) + 8 * k;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (c < n && r < n) {
+      const uint8_t* p = Y + static_cast<int64_t>(c) * ldy + r;
+      uint2 raw = make_uint2(0u, 0u);
+      if (r + 7 < n) {
+        raw = __ldg(reinterpret_cast<const uint2*>(p));
+      } else {
+        for (int e = 0; e < 8 && r + e < n; ++e) {
+          const uint32_t b = p[e];
+          if (e < 4)
+            raw.x |= b << (8 * e);
+          else
+            raw.y |= b << (8 * (e - 4));
+        }
+      }
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t word = q < 2 ? raw.x : raw.y;
+        const __nv_fp8x2_storage_t pair = static_cast<__nv_fp8x2_storage_t>((word >> (16 * (q & 1))) & 0xFFFFu);
+        __half2 h = __half2(__nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3));
+        h = __hmul2(h, ysc);
+        w[q] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      v = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    y[k] = v;
+  }
+}
+
+// 8 e4m3 codes (low bytes of 8 staged 16-bit words) to global memory at dst[0..7], clipped at n.
+__device__ __forceinline__ void store8_u8(uint8_t* dst, const uint16_t* src, int first, int n) {
+  const uint4 v = *reinterpret_cast<const uint4*>(src);
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const uint32_t b = (w[e >> 1] >> (16 * (e & 1))) & 0xFFu;
+    if (e < 4)
+      lo |= b << (8 * e);
+    else
+      hi |= b << (8 * (e - 4));
+  }
+  if (first + 7 < n) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);
+  } else {
+    for (int e = 0; e < 8 && first + e < n; ++e) dst[e] = static_cast<uint8_t>(e < 4 ? lo >> (8 * e) : hi >> (8 * (e - 4)));
+  }
+}
+
 // 16 bytes (8 halves) of one staged row to global memory at dst[0..7], clipped at `limit`.
 __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t* src, int first, int n) {
   const uint4 v = *reinterpret_cast<const uint4*>(src);
@@ -108,9 +173,9 @@ __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t* src, int f
 // accumulator at column c0 + j.  Diagonal chunks (r0 == c0) are symmetrised
 // from their upper part; off-diagonal chunks are written at both positions,
 // (r, c) and (c, r), with 16-byte stores from the staged copies.
-template <int EPI>
+template <int EPI, bool IN8, bool OUT8>
 __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const BlockRec& br, bool bf16, int n,
-                                                 uint16_t* C, int r0, int c0, const uint32_t (&v)[32],
+                                                 void* Cv, int r0, int c0, const uint32_t (&v)[32],
                                                  uint8_t* wbuf, const uint4 (&y)[4], int lane, bool track,
                                                  unsigned& amax_bits) {
   const bool pb = p.ep.per_block_coef != 0;
@@ -130,10 +195,11 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
   uint32_t h[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    const float acc = __uint_as_float(v[j]);
+    float acc = __uint_as_float(v[j]);
+    if (IN8) acc *= p.ep.in_scale;
     float val;
     if (EPI == EPI_POLY) {
-      const float yv = from16(YB[j * kH + lane], bf16);
+      const float yv = from16(YB[j * kH + lane], IN8 ? false : bf16);
       val = fmaf(cc, acc, cb * yv);
       if (diag && j == lane) val += ca;
     } else if (EPI == EPI_SCALE) {
@@ -141,7 +207,7 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
     } else {
       val = acc;
     }
-    h[j] = to16(val, bf16);
+    h[j] = OUT8 ? to8(val * p.ep.out_scale) : to16(val, bf16);
   }
   uint16_t* row = S + lane * kH;
 #pragma unroll
@@ -164,7 +230,7 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
 #pragma unroll
     for (int j = 0; j < 32; ++j) ST[j * kH + lane] = static_cast<uint16_t>(h[j]);
   }
-  if (track && r < n) {
+  if (!OUT8 && track && r < n) {
 #pragma unroll
     for (int j = 0; j < 32; ++j)
       if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(from16(static_cast<uint16_t>(h[j]), bf16))));
@@ -174,11 +240,18 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
   const int seg = 8 * (lane & 3);
   // memory rows c0 + j: output column c0 + j over rows r0..r0+31 (ST row j; S row j when symmetric)
   const uint16_t* SA = diag ? S : ST;
+  uint16_t* C = static_cast<uint16_t*>(Cv);
+  uint8_t* C8 = static_cast<uint8_t*>(Cv);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int jj = (lane >> 2) + 8 * k;
     const int c = c0 + jj;
-    if (c < n && r0 + seg < n) store8(C + static_cast<int64_t>(c) * ldc + r0 + seg, SA + jj * kH + seg, r0 + seg, n);
+    if (c < n && r0 + seg < n) {
+      if (OUT8)
+        store8_u8(C8 + static_cast<int64_t>(c) * ldc + r0 + seg, SA + jj * kH + seg, r0 + seg, n);
+      else
+        store8(C + static_cast<int64_t>(c) * ldc + r0 + seg, SA + jj * kH + seg, r0 + seg, n);
+    }
   }
   if (!diag) {
     // memory rows r0 + t: output row r0 + t over columns c0..c0+31 (S row t)
@@ -186,8 +259,12 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
     for (int k = 0; k < 4; ++k) {
       const int tt = (lane >> 2) + 8 * k;
       const int rr = r0 + tt;
-      if (rr < n && c0 + seg < n)
-        store8(C + static_cast<int64_t>(rr) * ldc + c0 + seg, S + tt * kH + seg, c0 + seg, n);
+      if (rr < n && c0 + seg < n) {
+        if (OUT8)
+          store8_u8(C8 + static_cast<int64_t>(rr) * ldc + c0 + seg, S + tt * kH + seg, c0 + seg, n);
+        else
+          store8(C + static_cast<int64_t>(rr) * ldc + c0 + seg, S + tt * kH + seg, c0 + seg, n);
+      }
     }
   }
   __syncwarp();
@@ -245,7 +322,7 @@ __device__ __forceinline__ void epilogue_chunk_final(const BlockRec& br, int r0,
   }
 }
 
-template <int EPI>
+template <int EPI, bool IN8, bool OUT8>
 __global__ void __launch_bounds__(kThreads, 1)
     symgemm16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const GemmParams p, const int bf16_flag) {
@@ -301,7 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
         const int4 tc = p.tiles[t];
         const BlockRec& bz = p.blocks[tc.z];
-        const int kbn = (bz.n + kBK16 - 1) / kBK16;
+        constexpr int kBK = IN8 ? kBK8 : kBK16;
+        const int kbn = (bz.n + kBK - 1) / kBK;
         const int ya = static_cast<int>(bz.off + tc.x), yb = static_cast<int>(bz.off + bz.db + tc.y);
         for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
@@ -310,8 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mbar_arrive_expect_tx(full_bar(s), kStageBytes16);
           const uint32_t a_dst = smem_u32(stages + s * kStageBytes16);
-          tma_load_2d(a_dst, &tmA, kb * kBK16, ya, full_bar(s));
-          tma_load_2d(a_dst + kABytes16, &tmB, kb * kBK16, yb, full_bar(s));
+          tma_load_2d(a_dst, &tmA, kb * kBK, ya, full_bar(s));
+          tma_load_2d(a_dst + kABytes16, &tmB, kb * kBK, yb, full_bar(s));
           last_parity[s] = static_cast<int>(ph);
           if (++s == kStages16) {
             s = 0;
@@ -335,7 +413,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
       const int4 tc = p.tiles[t];
-      const int kbn = (p.blocks[tc.z].n + kBK16 - 1) / kBK16;
+      constexpr int kBK = IN8 ? kBK8 : kBK16;
+      const int kbn = (p.blocks[tc.z].n + kBK - 1) / kBK;
       const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
       if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
         ok = false;
@@ -353,9 +432,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a_addr = smem_u32(stages + s * kStageBytes16);
           const uint32_t b_addr = a_addr + kABytes16;
 #pragma unroll
-          for (int k = 0; k < kBK16 / 16; ++k) {
-            mma_f16(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k),
-                    idesc, (kb | k) != 0 ? 1u : 0u);
+          for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction (16 halves or 32 e4m3)
+            if (IN8)
+              mma_f8(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k), idesc,
+                     (kb | k) != 0 ? 1u : 0u);
+            else
+              mma_f16(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k), idesc,
+                      (kb | k) != 0 ? 1u : 0u);
           }
           mma_commit(empty_bar(s));
         }
@@ -400,8 +483,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const BlockRec& br = p.blocks[tc.z];
       const int n = br.n;
       const int64_t off = br.off;
-      uint16_t* C = static_cast<uint16_t*>(p.ep.C) + (off + br.dc) * p.ep.ldc;
-      const uint16_t* Y = static_cast<const uint16_t*>(p.ep.Y) + (off + br.dy) * p.ep.ldy;
+      void* C = static_cast<uint8_t*>(p.ep.C) + (off + br.dc) * p.ep.ldc * (OUT8 ? 1 : 2);
+      const uint8_t* Yb = static_cast<const uint8_t*>(p.ep.Y) + (off + br.dy) * p.ep.ldy * (IN8 ? 1 : 2);
       const bool track = track_launch && (p.ep.absmax_blocks != 2 || br.track != 0);
       if (track_launch && amax_block != tc.z) {
         if (amax_block >= 0) flush_amax(amax_block);
@@ -412,7 +495,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int ch_begin = max(0, (r0 - tc.y) >> 5);
       const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
       uint4 ynext[4] = {};
-      if (EPI == EPI_POLY && ch_begin < ch_end) load_y_chunk(Y, p.ep.ldy, n, r0, tc.y + 32 * ch_begin, lane, ynext);
+      auto load_y = [&](int c0, uint4 (&dst)[4]) {
+        if (IN8)
+          load_y_chunk8(Yb, p.ep.ldy, n, r0, c0, lane, __float2half2_rn(p.ep.y_scale), dst);
+        else
+          load_y_chunk(reinterpret_cast<const uint16_t*>(Yb), p.ep.ldy, n, r0, c0, lane, dst);
+      };
+      if (EPI == EPI_POLY && ch_begin < ch_end) load_y(tc.y + 32 * ch_begin, ynext);
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
@@ -422,13 +511,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint4 ycur[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) ycur[k] = ynext[k];
-        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y_chunk(Y, p.ep.ldy, n, r0, c0 + 32, lane, ynext);
+        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y(c0 + 32, ynext);
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
         if (EPI == EPI_FINAL)
           epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam);
         else
-          epilogue_chunk16<EPI>(p, br, bf16, n, C, r0, c0, v, wbuf, ycur, lane, track, amax_bits);
+          epilogue_chunk16<EPI, IN8, OUT8>(p, br, bf16, n, C, r0, c0, v, wbuf, ycur, lane, track, amax_bits);
       }
       tc_fence_before();
       __syncwarp();
@@ -450,13 +539,29 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 using Kernel16 = void (*)(const CUtensorMap, const CUtensorMap, const GemmParams, const int);
 
-Kernel16 kernel16_for(int epi) {
-  switch (epi) {
-    case EPI_COPY: return symgemm16_kernel<EPI_COPY>;
-    case EPI_POLY: return symgemm16_kernel<EPI_POLY>;
-    case EPI_SCALE: return symgemm16_kernel<EPI_SCALE>;
-    default: return symgemm16_kernel<EPI_FINAL>;
+// Instances: 16-bit operands with 16-bit output (every epilogue); e4m3
+// operands with e4m3 output (the FP8 stages), e4m3 operands with 16-bit output
+// and 16-bit operands with e4m3 output (EPI_SCALE only: the last FP8 stage and
+// the stage before the first one).
+Kernel16 kernel16_for(int epi, bool in8, bool out8) {
+  if (!in8 && !out8) {
+    switch (epi) {
+      case EPI_COPY: return symgemm16_kernel<EPI_COPY, false, false>;
+      case EPI_POLY: return symgemm16_kernel<EPI_POLY, false, false>;
+      case EPI_SCALE: return symgemm16_kernel<EPI_SCALE, false, false>;
+      default: return symgemm16_kernel<EPI_FINAL, false, false>;
+    }
   }
+  if (in8 && out8) {
+    switch (epi) {
+      case EPI_COPY: return symgemm16_kernel<EPI_COPY, true, true>;
+      case EPI_POLY: return symgemm16_kernel<EPI_POLY, true, true>;
+      case EPI_SCALE: return symgemm16_kernel<EPI_SCALE, true, true>;
+      default: return nullptr;
+    }
+  }
+  if (epi != EPI_SCALE) return nullptr;
+  return in8 ? symgemm16_kernel<EPI_SCALE, true, false> : symgemm16_kernel<EPI_SCALE, false, true>;
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -498,9 +603,10 @@ int num_sms() {
 bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows) {
   EncodeFn fn = get_encode();
   if (!fn) return false;
-  const int esz = dtype == DT_TF32X3 ? 4 : 2;
+  const int esz = dtype == DT_TF32X3 ? 4 : (dtype == DT_E4M3 ? 1 : 2);
   const CUtensorMapDataType dt = dtype == DT_F16                          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                  : (dtype == DT_BF16 || dtype == DT_BF16X3) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : dtype == DT_E4M3                         ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
@@ -518,9 +624,10 @@ bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t col
                       int box_rows) {
   EncodeFn fn = get_encode();
   if (!fn) return false;
-  const int esz = dtype == DT_TF32X3 ? 4 : 2;
+  const int esz = dtype == DT_TF32X3 ? 4 : (dtype == DT_E4M3 ? 1 : 2);
   const CUtensorMapDataType dt = dtype == DT_F16                          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                  : (dtype == DT_BF16 || dtype == DT_BF16X3) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : dtype == DT_E4M3                         ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
@@ -561,19 +668,24 @@ std::vector<int4> make_tile_list(int64_t n, int block) {
 }
 
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                           const GemmParams& p, int grid, cudaStream_t stream) {
+                           const GemmParams& p, int grid, cudaStream_t stream, int out_dtype) {
   if (p.num_tiles == 0) return cudaSuccess;
-  if (dtype == DT_TF32X3) return cudaErrorNotSupported;
-  Kernel16 k = kernel16_for(epi);
-  static bool attr_set[4] = {false, false, false, false};
+  if (dtype != DT_F16 && dtype != DT_BF16 && dtype != DT_E4M3) return cudaErrorNotSupported;
+  if (out_dtype < 0) out_dtype = dtype;
+  if (epi < EPI_COPY || epi > EPI_FINAL) return cudaErrorInvalidValue;
+  const bool in8 = dtype == DT_E4M3, out8 = epi != EPI_FINAL && out_dtype == DT_E4M3;
+  Kernel16 k = kernel16_for(epi, in8, out8);
+  if (!k) return cudaErrorNotSupported;
+  static bool attr_set[16] = {};
+  const int idx = epi * 4 + (in8 ? 2 : 0) + (out8 ? 1 : 0);
   const int smem = smem_bytes16();
-  if (!attr_set[epi]) {
+  if (!attr_set[idx]) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    attr_set[epi] = true;
+    attr_set[idx] = true;
   }
   const int g = std::max(1, std::min(grid, p.num_tiles));
-  k<<<g, kThreads, smem, stream>>>(tmA, tmB, p, dtype == DT_BF16 ? 1 : 0);
+  k<<<g, kThreads, smem, stream>>>(tmA, tmB, p, out_dtype == DT_BF16 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,7 @@ def test_gemm_counts():
     assert b.psd_gemm_count("fp16") == 22  # Sec. 3.3 / abstract
     assert b.psd_gemm_count("bf16") == 22
     assert b.psd_gemm_count("fp32") == 31
+    assert b.psd_gemm_count("fp8_late") == 22  # the half schedule with e4m3 late stages
 
 
 def test_host_side_argument_checks():

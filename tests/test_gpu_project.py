@@ -152,3 +152,43 @@ def test_project_default_api_and_last_info(cases):
     b.psd_project(256, Xd, 256, out2, "fp16", s)
     torch.cuda.synchronize()
     assert torch.equal(out, out2)
+
+
+FP8_TOL = 5e-2  # the FP8 bar
+
+
+@pytest.fixture(scope="module")
+def fp8_cases():
+    out = {}
+    for kind, n, seed in (("wigner", 300, 5), ("uniform", 777, 4), ("clustered", 512, 4), ("powerlaw", 640, 4),
+                          ("lowrank", 700, 3)):
+        if kind == "wigner":
+            X = synth.wigner(n, seed)
+        elif kind == "lowrank":
+            X = synth.lowrank_plus_noise(n, seed)
+        else:
+            X = synth.spectral_matrix(kind, n, seed)[0]
+        out[kind] = (X, oracle.oracle_project(X.astype(np.float64), "half"))
+    return out
+
+
+@pytest.mark.parametrize("kind", ["wigner", "uniform", "clustered", "powerlaw", "lowrank"])
+def test_fp8_late_matches_oracle(fp8_cases, kind):
+    # stages 6-7 on e4m3 operands: a CPU emulation of the chain with e4m3
+    # roundings lands at 1.5-3.2e-2 on these spectrum families
+    X, ref = fp8_cases[kind]
+    got, info = run_project(X, "fp8_late")
+    assert info["status"] == 0
+    assert np.array_equal(got, got.T)
+    err = oracle.rel_err(got, ref["F"])
+    assert err <= FP8_TOL, err
+    # and it is measurably coarser than the FP16 path on the same input
+    got16, _ = run_project(X, "fp16")
+    assert oracle.rel_err(got16, ref["F"]) < err
+
+
+def test_fp8_early_is_refused():
+    X = torch.zeros((8, 8), device=DEV)
+    with pytest.raises(b.PsdError) as e:
+        b.psd_project(8, X, 8, X, "fp8_early")
+    assert e.value.status == 7

@@ -209,3 +209,58 @@ def test_split_product(n, prec):
     # (measured 1.8e-6 at n = 255, 3.7e-6 at n = 513).
     bound = 4e-5 if prec == "mixed" else max(1e-6, 1e-8 * n)
     assert np.linalg.norm(err) / np.linalg.norm(D[iu]) < bound
+
+
+F8 = getattr(torch, "float8_e4m3fn", None)
+
+
+def e4m3_sym(n, ld, seed, scale):
+    """(device bytes, decoded FP64 values) of a symmetric matrix stored as RN_e4m3(value * scale)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    A = 0.5 * (G + G.T)
+    q = torch.from_numpy(A * scale).to(F8)  # round to nearest, values far below 448
+    t = torch.zeros((n, ld), dtype=torch.uint8)
+    t[:, :n] = q.view(torch.uint8)
+    return t.cuda(), q.double().numpy() / scale
+
+
+@pytest.mark.skipif(F8 is None, reason="torch without float8_e4m3fn")
+@pytest.mark.parametrize("n", [16, 130, 255, 300, 700])
+def test_fp8_products(n):
+    # e4m3 operands (kind::f8f6f4), FP32 accumulation, e4m3 output with power-of-two scales
+    ld = (n + 15) // 16 * 16
+    sA, sB, sC, sY = 256.0, 128.0, 64.0, 256.0
+    Ad, A = e4m3_sym(n, ld, 40 + n, sA)
+    Bd, B = e4m3_sym(n, ld, 41 + n, sB)
+    Yd, Y = e4m3_sym(n, ld, 42 + n, sY)
+    absAB = np.abs(A) @ np.abs(B)
+    acc = 2 * n * 2.0 ** -23 * absAB
+
+    def run(epi, params):
+        C = torch.full((n, ld), 0x7F, dtype=torch.uint8, device="cuda")  # e4m3 NaN poison
+        b.psd_symm_product(n, Ad, Bd, ld, C, 0, "fp8_late", epi, params, Yd if epi == 1 else None, ld)
+        torch.cuda.synchronize()
+        Cb = C.cpu()
+        assert (Cb[:, n:] == 0x7F).all()  # padding never written
+        v = Cb[:, :n].contiguous().view(F8).double().numpy() / sC
+        return v
+
+    D = A @ B
+    iu = np.triu_indices(n)
+    # epi 0: C = A B
+    C0 = run(0, (1.0 / (sA * sB), 1.0, sC))
+    assert np.all(np.isfinite(C0)) and np.array_equal(C0, C0.T)
+    tol = 2.0 ** -4 * np.abs(D) + 2.0 ** -10 / sC + acc
+    assert np.all(np.abs(C0 - D)[iu] <= tol[iu])
+    # epi 1: C = a I + b Y + c A B  (Y read as e4m3 / sY)
+    a, bb, c = 0.75, -0.5, 0.25
+    C1 = run(1, (a, bb, c, 1.0 / (sA * sB), 1.0 / sY, sC))
+    D1 = a * np.eye(n) + bb * Y + c * D
+    tol1 = 2.0 ** -4 * np.abs(D1) + 2.0 ** -10 / sC + abs(c) * acc + 1e-6
+    assert np.all(np.abs(C1 - D1)[iu] <= tol1[iu])
+    # epi 2: C = (A B) s
+    C2 = run(2, (0.5, 1.0 / (sA * sB), 1.0, sC))
+    D2 = 0.5 * D
+    tol2 = 2.0 ** -4 * np.abs(D2) + 2.0 ** -10 / sC + acc
+    assert np.all(np.abs(C2 - D2)[iu] <= tol2[iu])
