@@ -12,6 +12,15 @@
 // Same symmetric tiling, warp roles and fused stage epilogues as the 16-bit
 // kernel (symgemm.cu); the output is again a pair, or a single FP16 matrix
 // (the last split stage hands over to FP16), or the FP32 final result.
+//
+// Promoted accumulation (TF32 pairs): the tensor cores add into an FP32
+// accumulator without rounding to nearest, so over the 3 n / 8 accumulation
+// steps of a product the error grows like n.  TF32 products therefore
+// accumulate K in chunks of kPromoteK elements in one tensor-memory buffer;
+// after each chunk the epilogue warps add it to a running FP32 sum in a
+// second buffer (round to nearest, chunks in order) and hand the chunk buffer
+// back, so the accumulation error stays that of a kPromoteK-long sum at any n
+// (the technique used for the low-precision accumulators of FP8 GEMMs).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -34,6 +43,7 @@ constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;  // 96 KB: A_hi | A_lo | 
 constexpr int kSW = 33;                                 // staging row stride (words)
 constexpr int kEpiWarpBytes = 2 * 32 * kSW * 4;         // values + Y chunk
 constexpr int kTmemCols = 512;
+constexpr int kPromoteK = 128;  // K elements per promoted chunk (TF32 pairs)
 
 __host__ __device__ constexpr int smem_bytes_x3() {
   return 1024 + kStages * kStageBytes + 4 * kEpiWarpBytes + 8 * (2 * kStages + 5) + 16;
@@ -277,6 +287,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_base = *tmem_holder;
   constexpr int kKElems = TF32 ? 32 : 64;  // K elements per 128-byte row
   constexpr int kKStep = TF32 ? 8 : 16;    // K per MMA instruction (32 bytes)
+  constexpr bool kPromote = TF32;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -317,6 +328,61 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
       }
     }
+  } else if (warp == 1 && kPromote) {
+    // chunk buffer at column 0 (tfull/tempty[0]); the running sum (column kBN)
+    // belongs to the epilogue warps
+    uint32_t s = 0, ph = 0, cph = 0;
+    bool ok = true;
+    constexpr int kChunkBlocks = kPromoteK / kKElems;
+    for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+      const int4 tc = p.tiles[t];
+      const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
+      const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
+      for (int kc = 0; ok && kc < kbn; kc += kChunkBlocks) {
+        if (!wait_bounded(tempty_bar(0), cph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int kend = min(kbn, kc + kChunkBlocks);
+        for (int kb = kc; kb < kend; ++kb) {
+          if (!wait_bounded(full_bar(s), ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t ah = smem_u32(stages + s * kStageBytes);
+            const uint32_t al = ah + kABytes, bh = ah + 2 * kABytes, bl = bh + kBBytes;
+#pragma unroll
+            for (int k = 0; k < kKElems / kKStep; ++k) {
+              const uint32_t off = 32 * k;
+              const uint32_t first = ((kb - kc) | k) == 0 ? 0u : 1u;
+              mma_tf32(tmem_base, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
+              mma_tf32(tmem_base, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
+              mma_tf32(tmem_base, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
+            }
+            mma_commit(empty_bar(s));
+          }
+          __syncwarp();
+          if (++s == kStages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit(tfull_bar(0));
+        __syncwarp();
+        cph ^= 1u;
+      }
+    }
+    if (!ok && lane == 0) {
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+    __syncwarp();
   } else if (warp == 1) {
     uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
     bool ok = true;
@@ -400,23 +466,67 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (amax_block >= 0) flush_amax(amax_block);
         amax_block = tc.z;
       }
-      if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
-      tc_fence_after();
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
       const int r0 = tc.x + 32 * ew;
       const int ch_begin = max(0, (r0 - tc.y) >> 5);
       const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
+      const uint32_t lanes = static_cast<uint32_t>(32 * ew) << 16;
+      if constexpr (kPromote) {
+        // fold every chunk into the running sum (column kBN), in K order
+        const int kbn = (n + kKElems - 1) / kKElems;
+        constexpr int kChunkBlocks = kPromoteK / kKElems;
+        bool ok = true;
+        for (int kc = 0; kc < kbn; kc += kChunkBlocks) {
+          if (!wait_bounded(tfull_bar(0), acc_ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          // one load round trip per 32 columns: chunk and sum loads issued
+          // together, stores left in flight until the end of the fold
 #pragma unroll 1
-      for (int ch = ch_begin; ch < ch_end; ++ch) {
-        uint32_t v[32];
-        tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
-        epilogue_chunk_x3<TF32, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
+          for (int ch = ch_begin; ch < ch_end; ++ch) {
+            uint32_t v[32], w[32];
+            tmem_ld32_async(tmem_base + lanes + 32 * ch, v);
+            if (kc > 0) {
+              tmem_ld32_async(tmem_base + lanes + kBN + 32 * ch, w);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) w[j] = 0u;  // +0.0f: the first chunk is stored as it is
+            }
+            tmem_wait_ld2(v, w);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(w[j]) + __uint_as_float(v[j]));
+            tmem_st32_async(tmem_base + lanes + kBN + 32 * ch, v);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty_bar(0));
+          acc_ph ^= 1u;
+        }
+        if (!ok) break;
+#pragma unroll 1
+        for (int ch = ch_begin; ch < ch_end; ++ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem_base + lanes + kBN + 32 * ch, v);
+          epilogue_chunk_x3<TF32, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
+        }
+      } else {
+        if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
+        tc_fence_after();
+#pragma unroll 1
+        for (int ch = ch_begin; ch < ch_end; ++ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem_base + lanes + acc * kBN + 32 * ch, v);
+          epilogue_chunk_x3<TF32, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        acc ^= 1u;
+        if (acc == 0) acc_ph ^= 1u;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(acc));
-      acc ^= 1u;
-      if (acc == 0) acc_ph ^= 1u;
     }
     if (track_launch && amax_block >= 0) flush_amax(amax_block);
   }
