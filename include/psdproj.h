@@ -204,12 +204,15 @@ psd_status_t psd_symm_product(int64_t n, const void *A, const void *B, int64_t l
  *     to max_order each).
  * A host thread admits queued requests in arrival order while their rows and
  * a record fit, runs their norm bound and X_0 = X / lam~ on a preparation
- * stream, and lets each join the running set at the next stage boundary.
- * Every scheduler step then advances all running requests by one stage of
- * Algorithm 2 with one grouped launch per product (X^2, the polynomial,
- * X P / s_t) and per operand type, each request at its own stage with its own
- * coefficients; requests that finish their last stage get the final product
- * and their report in the same step.
+ * stream, and lets each join the running set at the next step.  A scheduler
+ * step is one grouped launch per product (X^2, the polynomial, X P / s_t, the
+ * final product) and operand type over the running requests, each at its own
+ * stage with its own coefficients.  A step has a work budget (about 0.5 ms of
+ * the GPU): requests are served smallest first, each with the next tiles of
+ * its current product, and one that completes a product goes on to the next
+ * in the same step, so a small request runs a whole stage per step while a
+ * large one's products are spread over several steps (it always receives a
+ * minimum share).  Requests that finish get their report in the same step.
  *
  * Results: each request's arithmetic (norm bound kernels, tile partition,
  * summation order, coefficients and roundings) is that of psd_project with the

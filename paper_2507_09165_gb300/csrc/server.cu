@@ -16,7 +16,8 @@
 // and after the last stage out = (X + lam~ X_0 X_T) / 2.  The products are the
 // 16-bit symmetric tensor-core kernels of symgemm.cu over a block table with
 // per-block row offsets and coefficients, so one launch covers every running
-// request whatever its stage.  The norm bound runs on a preparation stream
+// request whatever its stage; a step spreads large products over several
+// launches under a work budget (enqueue_step).  The norm bound runs on a preparation stream
 // ("lane") with the single-projection kernels, replayed from a CUDA graph per
 // (lane, n); its result is copied into the request's record.
 #include <algorithm>
@@ -42,6 +43,13 @@ constexpr size_t kLaneHead = 1024;   // DevArgs (256) | DevState (768)
 constexpr int kMaxGraphsPerLane = 32;
 constexpr int kMaxBatchLimit = 1024;
 constexpr int64_t kMaxArenaRows = (int64_t{1} << 31) - 1024;  // TMA row coordinates are 32-bit
+// Work budget of one scheduler step in tile-K-blocks (one 128 x 256 output
+// tile over 64 K: 4.2 MFLOP; at ~1.3 PFLOP/s about 3 ns of the whole GPU), so a
+// step lasts about 0.5 ms however large the running requests are (measured on
+// the mixed ADMM stream: 1 ms steps gave n = 500 requests 14 / 24 ms p50 / p99,
+// 0.5 ms steps 10 / 14 ms, at 1.7% less throughput).
+constexpr int64_t kStepBudget = 150000;
+constexpr int64_t kQuantumDiv = 8;
 
 using Clock = std::chrono::steady_clock;
 
@@ -63,7 +71,10 @@ struct Request {
   int64_t row = -1;  // first arena row
   int lane = 0;
   int stage = 0;
-  int ntiles = 0;
+  int g = 0;         // product of the stage in progress: 0 Y, 1 P, 2 X_t, 3 final
+  int k = 0;         // tiles of that product done
+  int ntiles = 0;    // bound on the tile count (admission)
+  std::vector<int4> tl;  // tile list of order n
   Clock::time_point t_submit;
   double latency_ms = 0.0;
   psd_info_t info{};
@@ -198,7 +209,7 @@ __global__ void server_finalize_kernel(uint8_t* recs, const int* slots, int coun
 // Staging layout of one step (host and device copies are identical):
 //   BlockRec blocks[4][max_batch]   GEMM 1, 2, 3 and the final product
 //   int fin_slots[max_batch]        record slots of the requests that finish
-//   int4 tiles[...]                 tile lists of the step, then of the finals
+//   int4 tiles[4 tile_cap]          tile lists of the step's launches
 //   psd_info_t infos[max_batch]     reports of the finishing requests (device -> host)
 struct StageLayout {
   size_t blocks, fin, tiles, infos, total;
@@ -208,7 +219,7 @@ StageLayout stage_layout(int max_batch, int64_t tile_cap) {
   L.blocks = 0;
   L.fin = round_up(4 * sizeof(BlockRec) * max_batch, 256);
   L.tiles = L.fin + round_up(sizeof(int) * max_batch, 256);
-  L.infos = L.tiles + round_up(sizeof(int4) * 2 * tile_cap, 256);
+  L.infos = L.tiles + round_up(sizeof(int4) * 4 * tile_cap, 256);  // up to 4 product slots per request
   L.total = L.infos + round_up(sizeof(psd_info_t) * max_batch, 256);
   return L;
 }
@@ -335,10 +346,18 @@ cudaError_t step_gemm(psd_server* s, int dti, int epi, const BlockRec* d_blocks,
   return launch_symgemm(dti == 1 ? DT_BF16 : DT_F16, epi, s->tmA[dti], s->tmB[dti], g, grid, s->main);
 }
 
-// Builds and enqueues one scheduler step over `run` (sorted by n, largest
-// first).  Between building the step's tables and enqueueing its GPU work the
-// running set moves on (finishing requests leave it, the others advance one
-// stage), so that the completion callback never sees a request that is still
+// Builds and enqueues one scheduler step over `run`.  A step is one grouped
+// launch per product slot (Y = X^2, the polynomial, X P / s_t, the final
+// product) and operand type.  Each request keeps a cursor (stage, product,
+// tiles done) and takes the next tiles of its current product; a request that
+// completes a product continues with the next slot in the same step, so a
+// small request runs a whole stage per step.  Requests are visited smallest
+// first against a work budget of kStepBudget tile-K-blocks, which bounds the
+// step's duration; a request the budget does not reach still gets
+// kStepBudget / kQuantumDiv worth of tiles, so large requests always progress.
+// Every tile's arithmetic is the same whichever launch computes it.
+// Between building the step and enqueueing its GPU work the running set moves
+// on, so that the completion callback never sees a request that is still
 // listed as running.
 bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches) {
   const int slot = s->ring_next;
@@ -352,27 +371,9 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
   int4* ht = reinterpret_cast<int4*>(h + SL.tiles);
   const int T = s->sched.T;
   const int mb = s->max_batch;
-  std::vector<uint64_t> fin_ids;
-  int nf = 0;
-  // tile ranges per operand type: [type][0] step products, [type][1] finals
-  int cnt[2][2] = {{0, 0}, {0, 0}};
-  int64_t nt = 0;
-  std::vector<int4> tl;
-  for (int pass = 0; pass < 2; ++pass) {       // 0: step tiles, 1: final tiles
-    for (int dti = 0; dti < 2; ++dti) {        // FP16, BF16
-      const int64_t start = nt;
-      for (size_t i = 0; i < run.size(); ++i) {
-        const Request* r = run[i];
-        if ((r->dt == DT_BF16 ? 1 : 0) != dti) continue;
-        if (pass == 1 && r->stage != T - 1) continue;
-        tl = make_tile_list(r->n, static_cast<int>(i));
-        std::memcpy(ht + nt, tl.data(), tl.size() * sizeof(int4));
-        nt += static_cast<int64_t>(tl.size());
-      }
-      cnt[dti][pass] = static_cast<int>(nt - start);
-    }
-  }
-  for (size_t i = 0; i < run.size(); ++i) {
+  const int nrun = static_cast<int>(run.size());
+  // block records of every running request for every product slot
+  for (int i = 0; i < nrun; ++i) {
     Request* r = run[i];
     const int t = r->stage;
     const int64_t n = r->n;
@@ -383,30 +384,26 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
     BlockRec b{};
     b.n = static_cast<int>(n);
     b.st = st;
-    // GEMM 1: Y = cur cur
+    // Y = cur cur
     b.off = cur;
-    b.db = 0;
     b.dc = ry - cur;
     hb[0 * mb + i] = b;
-    // GEMM 2: P = a I + b Y + c Y Y
+    // P = a I + b Y + c Y Y
     b.off = ry;
-    b.db = 0;
     b.dc = rp - ry;
-    b.dy = 0;
     b.ca = static_cast<float>(s->sched.coef[t][0]);
     b.cb = static_cast<float>(s->sched.coef[t][1]);
     b.cc = static_cast<float>(s->sched.coef[t][2]);
     hb[1 * mb + i] = b;
-    // GEMM 3: X_t = cur P / s_t (into Y's rows), max |X_T| tracked at the last stage
+    // X_t = cur P / s_t into Y's rows; max |X_T| tracked at the last stage
     b.off = cur;
     b.db = rp - cur;
     b.dc = ry - cur;
-    b.dy = 0;
     b.ca = b.cb = b.cc = 0.f;
     b.cs = static_cast<float>(1.0 / s->sched.post[t]);
     b.track = t == T - 1 ? 1 : 0;
     hb[2 * mb + i] = b;
-    // final: out = (X + lam~ X_0 X_T) / 2
+    // out = (X + lam~ X_0 X_T) / 2
     BlockRec f{};
     f.n = static_cast<int>(n);
     f.st = st;
@@ -417,37 +414,109 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
     f.out = r->out;
     f.ld_out = r->ld_out;
     hb[3 * mb + i] = f;
-    if (t == T - 1) {
-      hfin[nf++] = r->slot;
-      fin_ids.push_back(r->id);
+  }
+  // tile allotment, smallest requests first
+  struct Part {
+    int req, begin, end;
+  };
+  std::vector<Part> parts[4];
+  struct Cursor {
+    int stage, g, k;
+    bool done;
+  };
+  std::vector<Cursor> next(nrun);
+  std::vector<int> order(nrun);
+  for (int i = 0; i < nrun; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return run[a]->n < run[b]->n; });
+  int64_t budget = kStepBudget;
+  for (int i : order) {
+    Request* r = run[i];
+    const int nt = static_cast<int>(r->tl.size());
+    const int64_t cost = (r->n + 63) / 64;  // K-blocks of 64 per tile
+    Cursor c{r->stage, r->g, r->k, false};
+    bool any = false;
+    for (;;) {
+      const int rem = nt - c.k;
+      int64_t m = std::min<int64_t>(rem, std::max<int64_t>(budget, 0) / cost);
+      if (m <= 0 && !any) m = std::min<int64_t>(rem, std::max<int64_t>(1, kStepBudget / kQuantumDiv / cost));
+      if (m <= 0) break;
+      parts[c.g].push_back({i, c.k, c.k + static_cast<int>(m)});
+      any = true;
+      budget -= m * cost;
+      c.k += static_cast<int>(m);
+      if (c.k < nt) break;  // the product continues in the next step
+      c.k = 0;
+      if (c.g == 3) {
+        c.done = true;
+        break;
+      }
+      if (c.g == 2) {
+        if (c.stage == T - 1) {
+          c.g = 3;  // the final product follows in this step
+        } else {
+          c.g = 0;  // the next stage starts with the next step
+          ++c.stage;
+          break;
+        }
+      } else {
+        ++c.g;
+      }
+    }
+    next[i] = c;
+  }
+  // tile lists per slot and operand type, largest orders first (long tiles lead)
+  int cnt[4][2] = {};
+  int64_t nt_all = 0;
+  for (int g = 0; g < 4; ++g) {
+    for (int dti = 0; dti < 2; ++dti) {
+      const int64_t start = nt_all;
+      for (auto it = parts[g].rbegin(); it != parts[g].rend(); ++it) {
+        const Request* r = run[it->req];
+        if ((r->dt == DT_BF16 ? 1 : 0) != dti) continue;
+        for (int q = it->begin; q < it->end; ++q) {
+          int4 tc = r->tl[q];
+          tc.z = it->req;
+          ht[nt_all++] = tc;
+        }
+      }
+      cnt[g][dti] = static_cast<int>(nt_all - start);
     }
   }
+  std::vector<uint64_t> fin_ids;
+  int nf = 0;
+  for (int i = 0; i < nrun; ++i)
+    if (next[i].done) {
+      hfin[nf++] = run[i]->slot;
+      fin_ids.push_back(run[i]->id);
+    }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     ++s->steps;
-    s->max_running = std::max(s->max_running, static_cast<int>(run.size()));
+    s->max_running = std::max(s->max_running, nrun);
     std::vector<Request*> keep;
-    for (Request* r : s->run) {
-      if (r->stage == T - 1) continue;  // completes in on_step_done
-      ++r->stage;
+    for (int i = 0; i < nrun; ++i) {
+      Request* r = run[i];
+      if (next[i].done) continue;  // completes in on_step_done
+      r->stage = next[i].stage;
+      r->g = next[i].g;
+      r->k = next[i].k;
       keep.push_back(r);
     }
-    s->run.swap(keep);
+    s->run.swap(keep);  // only this thread changes the running set: s->run == run here
   }
   cudaStream_t ms = s->main;
-  const size_t upload = SL.tiles + sizeof(int4) * static_cast<size_t>(nt);
+  const size_t upload = SL.tiles + sizeof(int4) * static_cast<size_t>(nt_all);
   if (cudaMemcpyAsync(d, h, upload, cudaMemcpyHostToDevice, ms) != cudaSuccess) return false;
   const BlockRec* db = reinterpret_cast<const BlockRec*>(d + SL.blocks);
   const int4* dt = reinterpret_cast<const int4*>(d + SL.tiles);
-  const int4* t_step[2] = {dt, dt + cnt[0][0]};
-  const int4* t_fin[2] = {dt + cnt[0][0] + cnt[1][0], dt + cnt[0][0] + cnt[1][0] + cnt[0][1]};
-  const int epis[3] = {EPI_COPY, EPI_POLY, EPI_SCALE};
-  for (int k = 0; k < 3; ++k)
-    for (int dti = 0; dti < 2; ++dti)
-      if (step_gemm(s, dti, epis[k], db + k * mb, t_step[dti], cnt[dti][0], launches) != cudaSuccess) return false;
+  const int epis[4] = {EPI_COPY, EPI_POLY, EPI_SCALE, EPI_FINAL};
+  int64_t off = 0;
+  for (int g = 0; g < 4; ++g)
+    for (int dti = 0; dti < 2; ++dti) {
+      if (step_gemm(s, dti, epis[g], db + g * mb, dt + off, cnt[g][dti], launches) != cudaSuccess) return false;
+      off += cnt[g][dti];
+    }
   if (nf > 0) {
-    for (int dti = 0; dti < 2; ++dti)
-      if (step_gemm(s, dti, EPI_FINAL, db + 3 * mb, t_fin[dti], cnt[dti][1], launches) != cudaSuccess) return false;
     server_finalize_kernel<<<(nf + 127) / 128, 128, 0, ms>>>(s->recs, reinterpret_cast<const int*>(d + SL.fin), nf,
                                                              s->d_launch_status,
                                                              reinterpret_cast<psd_info_t*>(d + SL.infos));
@@ -549,6 +618,8 @@ void scheduler(psd_server* s) {
           if (!ready) wait_first = true;
           r->state = RQ_RUN;
           r->stage = 0;
+          r->g = 0;
+          r->k = 0;
           s->run.push_back(r);
           if (!ready) run_now.push_back(r);
         } else {
@@ -556,7 +627,6 @@ void scheduler(psd_server* s) {
         }
       }
       s->prep.swap(still);
-      std::stable_sort(s->run.begin(), s->run.end(), [](const Request* a, const Request* b) { return a->n > b->n; });
     }
     if (wait_first) {
       for (Request* r : run_now) ok = ok && cudaStreamWaitEvent(s->main, s->prep_ev[r->slot], 0) == cudaSuccess;
@@ -740,6 +810,7 @@ extern "C" psd_status_t psd_server_submit(psd_server_t* s, int64_t n, const floa
   r->dt = precision == PSD_PREC_BF16 ? DT_BF16 : DT_F16;
   r->ready = reinterpret_cast<cudaEvent_t>(ready);
   r->ntiles = static_cast<int>(tiles_of(n));
+  if (n > 0) r->tl = make_tile_list(n, 0);
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
