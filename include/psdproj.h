@@ -69,9 +69,9 @@ typedef enum {
   PSD_PREC_FP16 = 1,  /* f~*_half (Table 2), T = 7, 22 products, FP16 operands,
                          FP32 accumulation in tensor memory */
   PSD_PREC_BF16 = 2,  /* as FP16 with BF16 operands */
-  PSD_PREC_MIXED = 3, /* f~*_half; stages 1-3 on BF16 hi/lo split operands
-                         (three BF16 products each), stages 4-7 and the final
-                         product in FP16; FP32 accumulation throughout */
+  PSD_PREC_MIXED = 3, /* f~*_half with FP16 iterates; in stages 1-4 Y = X^2 and
+                         the stage polynomial P are FP16 hi/lo pairs (Y^2 as
+                         three FP16 products, X P as two); FP32 accumulation */
   PSD_PREC_FP8_EARLY = 4, /* reserved, returns PSD_ERR_UNSUPPORTED: e4m3 iterates in
                              the first stages diverge (the stage-1 coefficients
                              amplify the rounding of X^2 beyond the filter's basin) */
@@ -169,10 +169,11 @@ psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
  * pointers 16-byte aligned).  Only the upper tiles of A * B are formed on the
  * tensor cores and mirrored, so C is exactly symmetric.
  *   precision FP16 / BF16: single 16-bit matrices;
- *   precision MIXED: BF16 pairs, precision FP32: TF32 pairs (FP32 containers):
- *     every operand (A, B, C, Y) is two matrices stored back to back, hi at
- *     M and lo at M + n*ld elements, value = hi + lo; the product is
- *     A_hi B_hi + A_hi B_lo + A_lo B_hi in one FP32 accumulator.
+ *   precision MIXED: FP16 pairs (epi 0-2), precision FP32: TF32 pairs (FP32
+ *     containers): every operand (A, B, C, Y) is two matrices stored back to
+ *     back, hi at M and lo at M + n*ld elements, value = hi + lo; the product
+ *     is A_hi B_hi + A_hi B_lo + A_lo B_hi in one FP32 accumulator (TF32:
+ *     folded every 128 K into a round-to-nearest running sum).
  *   epi 0: C = A B
  *   epi 1: C = a I + b Y + c A B          (Y = aux, same storage and ld)
  *   epi 2: C = (A B) * s

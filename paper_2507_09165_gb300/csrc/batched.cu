@@ -15,21 +15,11 @@
 #include <mutex>
 #include <vector>
 
+#include "chain.h"
 #include "internal.h"
 
 namespace psd {
 namespace {
-
-constexpr int kMixedSplitB = 3;  // mixed: BF16 pairs for stages 1..3, then FP16
-
-enum Kind : int { K16 = 0, KB3 = 1, KT3 = 2 };
-int kslots(int k) { return k == K16 ? 1 : k == KB3 ? 2 : 4; }
-
-struct BMat {
-  int kind = K16;
-  int slot = -1;
-  int dt16 = DT_F16;
-};
 
 struct BatchPlan {
   psd_precision_t prec = PSD_PREC_BF16;
@@ -63,7 +53,7 @@ std::map<std::tuple<int, cudaStream_t, int, std::vector<int>>, BatchPlan*> g_bpl
 
 int64_t rup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-int nslots_for(psd_precision_t prec) { return prec == PSD_PREC_FP32 ? 16 : prec == PSD_PREC_MIXED ? 9 : 4; }
+int nslots_for(psd_precision_t prec) { return chain_slots(prec); }
 
 int dt16_for(psd_precision_t prec) { return prec == PSD_PREC_BF16 ? DT_BF16 : DT_F16; }
 
@@ -197,29 +187,12 @@ psd_status_t build_bplan(BatchPlan* p) {
   return PSD_OK;
 }
 
-struct Pool {
-  uint32_t used = 0;
-  int n = 0;
-  int alloc(int k) {
-    for (int s = 0; s + k <= n; ++s) {
-      const uint32_t m = ((1u << k) - 1u) << s;
-      if (!(used & m)) {
-        used |= m;
-        return s;
-      }
-    }
-    return -1;
-  }
-  void release(const BMat& m) { used &= ~(((1u << kslots(m.kind)) - 1u) << m.slot); }
-};
-
-void* bpart(const BatchPlan* p, const BMat& m, int part) {
-  const int step = m.kind == KT3 ? 2 : 1;
-  return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * step)) * p->slot_size;
+void* bpart(const BatchPlan* p, const Mat& m, int part) {
+  return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * kind_lo_step(m.kind))) * p->slot_size;
 }
-int bdtype(const BMat& m) { return m.kind == K16 ? m.dt16 : m.kind == KB3 ? DT_BF16X3 : DT_TF32X3; }
 
-cudaError_t bgemm(BatchPlan* p, int epi, const BMat& A, const BMat& B, const BMat* out, const BMat* Y, float a,
+// One grouped product over every block's tiles (routes: chain.h gemm_route).
+cudaError_t bgemm(BatchPlan* p, int epi, const Mat& A, const Mat& B, const Mat* out, const Mat* Y, float a,
                   float b, float c, float sc, bool track, cudaStream_t s) {
   GemmParams g{};
   g.num_tiles = p->ntiles;
@@ -233,87 +206,60 @@ cudaError_t bgemm(BatchPlan* p, int epi, const BMat& A, const BMat& B, const BMa
   g.ep.absmax_blocks = track ? 1 : 0;
   if (epi != EPI_FINAL) {
     g.ep.C = bpart(p, *out, 0);
-    g.ep.C_lo = out->kind == K16 ? nullptr : bpart(p, *out, 1);
+    g.ep.C_lo = kind_is_pair(out->kind) ? bpart(p, *out, 1) : nullptr;
     g.ep.ldc = p->ldm;
   }
   if (epi == EPI_POLY) {
     g.ep.Y = bpart(p, *Y, 0);
-    g.ep.Y_lo = Y->kind == K16 ? nullptr : bpart(p, *Y, 1);
+    g.ep.Y_lo = kind_is_pair(Y->kind) ? bpart(p, *Y, 1) : nullptr;
     g.ep.ldy = p->ldm;
   }
+  g.ep.in_scale = g.ep.y_scale = g.ep.out_scale = 1.f;
   const int grid = num_sms();
   const int64_t cols = p->ldm, rows = p->R;
-  if (A.kind == K16) {
+  const GemmRoute route = gemm_route(A, B);
+  if (route == ROUTE_16) {
+    const int dt = kind_dtype(A);
     CUtensorMap ta, tb;
-    if (!encode_tmap_rows(&ta, A.dt16, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
-        !encode_tmap_rows(&tb, B.dt16, bpart(p, B, 0), cols, rows, p->ldm, 256))
+    if (!encode_tmap_rows(&ta, dt, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
+        !encode_tmap_rows(&tb, dt, bpart(p, B, 0), cols, rows, p->ldm, 256))
       return cudaErrorInvalidValue;
-    const uint32_t fmt = A.dt16 == DT_BF16 ? 1u : 0u;
+    const uint32_t fmt = dt == DT_BF16 ? 1u : 0u;
     g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);
-    return launch_symgemm(A.dt16, epi, ta, tb, g, grid, s);
+    return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? kind_dtype(*out) : -1);
   }
-  const int dt = bdtype(A);
+  if (route == ROUTE_NONE) return cudaErrorNotSupported;
+  const bool a1 = route == ROUTE_X2;
+  const int dt = kind_dtype(B);
   CUtensorMap tm[4];
   if (!encode_tmap_rows(&tm[0], dt, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
-      !encode_tmap_rows(&tm[1], dt, bpart(p, A, 1), cols, rows, p->ldm, 128) ||
+      !encode_tmap_rows(&tm[1], dt, bpart(p, A, a1 ? 0 : 1), cols, rows, p->ldm, 128) ||
       !encode_tmap_rows(&tm[2], dt, bpart(p, B, 0), cols, rows, p->ldm, 256) ||
       !encode_tmap_rows(&tm[3], dt, bpart(p, B, 1), cols, rows, p->ldm, 256))
     return cudaErrorInvalidValue;
-  const int out_mode = epi == EPI_FINAL ? 2 : (out->kind == K16 ? 1 : 0);
-  return launch_symgemm_x3(A.kind == KT3, epi, out_mode, tm, g, grid, s);
+  const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
+  return launch_symgemm_x3(dt, a1, epi, out_mode, tm, g, grid, s);
 }
+
+struct BatchOps {
+  BatchPlan* p;
+  cudaStream_t s;
+  cudaError_t cast(const Mat& X0) {
+    BatchCast bc{bpart(p, X0, 0), kind_is_pair(X0.kind) ? bpart(p, X0, 1) : nullptr, p->ldm};
+    return enqueue_batch_cast(kind_dtype(X0), bc, p->d_bb, p->d_st, p->d_cast, p->ncast, s);
+  }
+  cudaError_t gemm(int epi, const Mat& A, const Mat& B, const Mat* out, const Mat* Y, float a, float b, float c,
+                   float sc, bool track) {
+    return bgemm(p, epi, A, B, out, Y, a, b, c, sc, track, s);
+  }
+  cudaError_t finish() { return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, s); }
+};
 
 cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
   cudaError_t e;
   if ((e = enqueue_batch_norm_bound(p->L, p->count, p->d_symv, p->nsymv, s)) != cudaSuccess) return e;
-  Pool pool;
-  pool.n = p->nslots;
-  const int T = p->sched.T;
-  const int dt16 = dt16_for(p->prec);
-  auto kind_of = [&](int t) {
-    if (p->prec == PSD_PREC_FP32) return static_cast<int>(KT3);
-    if (p->prec == PSD_PREC_MIXED && t < kMixedSplitB) return static_cast<int>(KB3);
-    return static_cast<int>(K16);
-  };
-  auto make = [&](int k) {
-    BMat m;
-    m.kind = k;
-    m.dt16 = dt16;
-    m.slot = pool.alloc(kslots(k));
-    return m;
-  };
-  BMat X0 = make(kind_of(0)), X0f16;
-  if (p->prec == PSD_PREC_MIXED) X0f16 = make(K16);
-  if (X0.slot < 0 || (p->prec == PSD_PREC_MIXED && X0f16.slot < 0)) return cudaErrorMemoryAllocation;
-  BatchCast bc{bpart(p, X0, 0), X0.kind == K16 ? nullptr : bpart(p, X0, 1),
-               p->prec == PSD_PREC_MIXED ? bpart(p, X0f16, 0) : nullptr, p->ldm};
-  if ((e = enqueue_batch_cast(bdtype(X0), bc, p->d_bb, p->d_st, p->d_cast, p->ncast, s)) != cudaSuccess) return e;
-  BMat cur = X0;
-  for (int t = 0; t < T; ++t) {
-    const int k = kind_of(t);
-    const int kout = p->prec == PSD_PREC_FP32 ? static_cast<int>(KT3) : (t + 1 < T ? kind_of(t + 1) : static_cast<int>(K16));
-    BMat Y = make(k);
-    if (Y.slot < 0) return cudaErrorMemoryAllocation;
-    if ((e = bgemm(p, EPI_COPY, cur, cur, &Y, nullptr, 0.f, 0.f, 0.f, 1.f, false, s)) != cudaSuccess) return e;
-    BMat P = make(k);
-    if (P.slot < 0) return cudaErrorMemoryAllocation;
-    if ((e = bgemm(p, EPI_POLY, Y, Y, &P, &Y, static_cast<float>(p->sched.coef[t][0]),
-                   static_cast<float>(p->sched.coef[t][1]), static_cast<float>(p->sched.coef[t][2]), 1.f, false,
-                   s)) != cudaSuccess)
-      return e;
-    pool.release(Y);
-    BMat Xn = make(kout);
-    if (Xn.slot < 0) return cudaErrorMemoryAllocation;
-    if ((e = bgemm(p, EPI_SCALE, cur, P, &Xn, nullptr, 0.f, 0.f, 0.f, static_cast<float>(1.0 / p->sched.post[t]),
-                   t == T - 1, s)) != cudaSuccess)
-      return e;
-    pool.release(P);
-    if (cur.slot != X0.slot) pool.release(cur);
-    cur = Xn;
-  }
-  const BMat& A0 = p->prec == PSD_PREC_MIXED ? X0f16 : X0;
-  if ((e = bgemm(p, EPI_FINAL, A0, cur, nullptr, nullptr, 0.f, 0.f, 0.f, 1.f, false, s)) != cudaSuccess) return e;
-  return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, s);
+  BatchOps ops{p, s};
+  return run_chain(p->prec, p->sched, p->nslots, dt16_for(p->prec), ops);
 }
 
 void ensure_bgraph(BatchPlan* p) {

@@ -619,18 +619,6 @@ __device__ __forceinline__ void bstore4(const BatchCast& c, int64_t pos, const f
       Mh[k] = h;
       Ml[k] = tf32_round(v[k] - h);
     }
-  } else if (DT == DT_BF16X3) {
-    uint16_t h[4], l[4], f[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const __nv_bfloat16 hb = __float2bfloat16_rn(v[k]);
-      h[k] = __bfloat16_as_ushort(hb);
-      l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k] - __bfloat162float(hb)));
-      f[k] = __half_as_ushort(__float2half_rn(v[k]));
-    }
-    put4_16(static_cast<uint16_t*>(c.M) + pos, h, valid);
-    put4_16(static_cast<uint16_t*>(c.M_lo) + pos, l, valid);
-    if (c.M_f16) put4_16(static_cast<uint16_t*>(c.M_f16) + pos, f, valid);
   } else {
     uint16_t u[4];
 #pragma unroll
@@ -758,7 +746,7 @@ cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* 
     case DT_F16: bcast_kernel<DT_F16><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
     case DT_BF16: bcast_kernel<DT_BF16><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
     case DT_TF32X3: bcast_kernel<DT_TF32X3><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
-    default: bcast_kernel<DT_BF16X3><<<nitems, 256, 0, s>>>(c, blk, st, items); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

@@ -55,7 +55,8 @@ enum Epi : int { EPI_COPY = 0, EPI_POLY = 1, EPI_SCALE = 2, EPI_FINAL = 3 };
 
 // Operand storage of the chain: single 16-bit matrices, TF32 hi/lo pairs
 // (FP32 containers), BF16 hi/lo pairs.
-enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_BF16X3 = 3, DT_E4M3 = 4 };
+// Element types; the X2/X3 names are hi/lo pairs (DT_F16X2: FP16 hi + FP16 lo).
+enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_E4M3 = 4, DT_F16X2 = 5 };
 
 // One symmetric matrix of a product launch.  A launch covers one matrix
 // (single projection) or many (block-diagonal cone, served requests); the
@@ -121,13 +122,16 @@ bool get_schedule(psd_precision_t prec, Schedule& s);
 // --- host helpers (symgemm.cu) ---
 bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows);
 // dtype: operand type (DT_F16, DT_BF16 or DT_E4M3); out_dtype: type of the
-// EPI_COPY/POLY/SCALE output (DT_F16, DT_BF16 or DT_E4M3; -1: the operand type).
+// EPI_COPY/POLY/SCALE output (DT_F16, DT_BF16, DT_E4M3, or DT_F16X2 for an FP16
+// pair written to ep.C / ep.C_lo; -1: the operand type).
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1);
 // split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
 // out: 0 = split pair, 1 = single FP16, (EPI_FINAL) FP32 to the caller's output.
-cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm, const GemmParams& p, int grid,
-                              cudaStream_t stream);
+// Split-operand products: et = DT_TF32X3 (TF32 pairs) or DT_F16X2 (FP16
+// pairs); a_single: A is one FP16 matrix and B an FP16 pair.
+cudaError_t launch_symgemm_x3(int et, bool a_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
+                              int grid, cudaStream_t stream);
 int num_sms();
 
 // --- batched projection of a block-diagonal cone (batched_kernels.cu) ---
@@ -158,7 +162,6 @@ struct BatchLanczos {
 struct BatchCast {
   void* M;                // X_0: stacked iterate buffer (hi part of a pair)
   void* M_lo;
-  void* M_f16;            // mixed: the FP16 copy
   int64_t ldm;
 };
 
@@ -194,10 +197,9 @@ size_t lanczos_bytes(int64_t n);
 void lanczos_carve(LanczosBufs& b, int64_t n, uint8_t* base);
 cudaError_t enqueue_norm_bound(const LanczosBufs& b, const DevArgs* args, DevState* st,
                                cudaStream_t stream);
-// X_0 = X / lam~ as `dtype` (pairs: M = hi, M_lo = lo); M_f16 (may be null): an
-// additional FP16 copy (DT_BF16X3 only).
+// X_0 = X / lam~ as `dtype` (DT_F16, DT_BF16, or DT_TF32X3 with M = hi, M_lo = lo).
 cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n,
-                               void* M, void* M_lo, void* M_f16, int64_t ldm, cudaStream_t stream);
+                               void* M, void* M_lo, int64_t ldm, cudaStream_t stream);
 // Argument block of one replay (and the caller fields of a one-block record, if given).
 cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t stream, BlockRec* blk = nullptr);
 cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t stream);

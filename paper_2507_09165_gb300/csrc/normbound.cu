@@ -671,8 +671,7 @@ __device__ __forceinline__ float tf32_round(float v) {
 }
 
 // Four consecutive elements (positions pos .. pos+3 of a row) of the output
-// matrix in the chain's storage: 16-bit, TF32 hi/lo pairs, or BF16 hi/lo pairs
-// plus an FP16 copy (M_f16, may be null).
+// matrix in the chain's storage: 16-bit, or TF32 hi/lo pairs.
 __device__ __forceinline__ void put16(uint16_t* H, const uint16_t (&u)[4], int valid) {
   if (valid == 4) {
     *reinterpret_cast<uint2*>(H) =
@@ -683,7 +682,7 @@ __device__ __forceinline__ void put16(uint16_t* H, const uint16_t (&u)[4], int v
 }
 
 template <int DT>
-__device__ __forceinline__ void store4(void* M, void* M_lo, void* M_f16, int64_t pos, const float (&v)[4],
+__device__ __forceinline__ void store4(void* M, void* M_lo, int64_t pos, const float (&v)[4],
                                        int valid) {
   if (DT == DT_TF32X3) {
     float h[4], l[4];
@@ -703,18 +702,6 @@ __device__ __forceinline__ void store4(void* M, void* M_lo, void* M_f16, int64_t
         Ml[k] = l[k];
       }
     }
-  } else if (DT == DT_BF16X3) {
-    uint16_t h[4], l[4], f[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const __nv_bfloat16 hb = __float2bfloat16_rn(v[k]);
-      h[k] = __bfloat16_as_ushort(hb);
-      l[k] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k] - __bfloat162float(hb)));
-      f[k] = __half_as_ushort(__float2half_rn(v[k]));
-    }
-    put16(static_cast<uint16_t*>(M) + pos, h, valid);
-    put16(static_cast<uint16_t*>(M_lo) + pos, l, valid);
-    if (M_f16) put16(static_cast<uint16_t*>(M_f16) + pos, f, valid);
   } else {
     uint16_t u[4];
 #pragma unroll
@@ -732,7 +719,7 @@ __device__ __forceinline__ void store4(void* M, void* M_lo, void* M_f16, int64_t
 template <int DT>
 __global__ void __launch_bounds__(256) scale_cast_kernel(const DevArgs* __restrict__ args, int n,
                                                          const DevState* __restrict__ st, void* __restrict__ M,
-                                                         void* __restrict__ M_lo, void* __restrict__ M_f16,
+                                                         void* __restrict__ M_lo,
                                                          int64_t ldm) {
   __shared__ float s[64][65];
   int bi, bj;
@@ -786,14 +773,14 @@ __global__ void __launch_bounds__(256) scale_cast_kernel(const DevArgs* __restri
     // position (i + j ldm): memory row j, elements i0 + 4 tx .. +3
     if (j < n && valid_i > 0) {
       const float v[4] = {s[4 * tx][jj], s[4 * tx + 1][jj], s[4 * tx + 2][jj], s[4 * tx + 3][jj]};
-      store4<DT>(M, M_lo, M_f16, static_cast<int64_t>(j) * ldm + ib, v, valid_i);
+      store4<DT>(M, M_lo, static_cast<int64_t>(j) * ldm + ib, v, valid_i);
     }
     // mirrored position (j + i ldm): memory row i = i0 + jj, elements j0 + 4 tx .. +3
     const int i = i0 + jj, jc = j0 + 4 * tx;
     const int valid_j = min(4, n - jc);
     if (!diag && i < n && valid_j > 0) {
       const float v[4] = {s[jj][4 * tx], s[jj][4 * tx + 1], s[jj][4 * tx + 2], s[jj][4 * tx + 3]};
-      store4<DT>(M, M_lo, M_f16, static_cast<int64_t>(i) * ldm + jc, v, valid_j);
+      store4<DT>(M, M_lo, static_cast<int64_t>(i) * ldm + jc, v, valid_j);
     }
   }
 }
@@ -898,16 +885,16 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
 }
 
 cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n, void* M,
-                               void* M_lo, void* M_f16, int64_t ldm, cudaStream_t s) {
+                               void* M_lo, int64_t ldm, cudaStream_t s) {
   const int nb = static_cast<int>((n + 63) / 64);
   const int tiles = nb * (nb + 1) / 2;
   const int blk = 256;
   const int ni = static_cast<int>(n);
   switch (dtype) {
-    case DT_F16: scale_cast_kernel<DT_F16><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
-    case DT_BF16: scale_cast_kernel<DT_BF16><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
-    case DT_TF32X3: scale_cast_kernel<DT_TF32X3><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
-    default: scale_cast_kernel<DT_BF16X3><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, M_f16, ldm); break;
+    case DT_F16: scale_cast_kernel<DT_F16><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, ldm); break;
+    case DT_BF16: scale_cast_kernel<DT_BF16><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, ldm); break;
+    case DT_TF32X3: scale_cast_kernel<DT_TF32X3><<<tiles, blk, 0, s>>>(args, ni, st, M, M_lo, ldm); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

@@ -20,6 +20,7 @@
 #include <tuple>
 #include <vector>
 
+#include "chain.h"
 #include "internal.h"
 
 namespace psd {
@@ -72,32 +73,6 @@ bool get_schedule(psd_precision_t prec, Schedule& s) {
 
 namespace {
 
-// Storage of the iterates per precision: 16-bit single matrices (FP16, BF16),
-// TF32 hi/lo pairs (FP32 path), or BF16 hi/lo pairs for the first kMixedSplit
-// stages followed by FP16 (mixed).
-constexpr int kMixedSplit = 3;
-// FP8_LATE: the last kFp8Stages stages on e4m3 operands.  The first stages
-// cannot be: their coefficients (a_1 = 8.29, b_1 = -22.6) amplify the e4m3
-// rounding of X^2 (u = 2^-4) beyond the composite's basin.
-constexpr int kFp8Stages = 2;
-// Power-of-two scales of the e4m3 matrices: |X_t(i,j)|, |Y(i,j)| <= their
-// spectral norms <= 1.25 (the filter keeps the spectrum near [-1, 1]), so
-// 256 x 1.25 = 320 stays below the e4m3 maximum 448; P's scale comes from
-// max |a + b y + c y^2| over y in [0, 1.25].
-constexpr float kFp8ScaleX = 256.f;
-constexpr float kFp8ScaleY = 256.f;
-
-float fp8_poly_scale(const double (&c)[3]) {
-  double m = 0.0;
-  const double ys[3] = {0.0, 1.25, c[2] != 0.0 ? -c[1] / (2.0 * c[2]) : 0.0};
-  for (double y : ys)
-    if (y >= 0.0 && y <= 1.25) m = std::max(m, std::fabs(c[0] + c[1] * y + c[2] * y * y));
-  double sc = 1.0;
-  while (sc * 2.0 * m < 400.0) sc *= 2.0;
-  while (sc > 1.0 / 1024 && sc * m >= 400.0) sc *= 0.5;
-  return static_cast<float>(sc);
-}
-
 int dtype16_of(psd_precision_t prec) { return prec == PSD_PREC_BF16 ? DT_BF16 : DT_F16; }
 
 bool prec_built(psd_precision_t prec) {
@@ -111,18 +86,12 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 int64_t internal_ld(int64_t n) { return round_up(std::max<int64_t>(n, 1), 64); }
 
 // Workspace is carved into slots of one n x ldm 16-bit matrix: a 16-bit
-// matrix takes 1 slot, a BF16 pair 2, a TF32 pair 4.
+// matrix takes 1 slot, an FP16 pair 2, a TF32 pair 4.
 size_t slot_bytes(int64_t n) {
   return static_cast<size_t>(round_up(static_cast<int64_t>(internal_ld(n)) * n * 2, 1024));
 }
 
-int slots_needed(psd_precision_t prec) {
-  switch (prec) {
-    case PSD_PREC_FP32: return 16;   // X_0, X_{t-1}, P, X_t as TF32 pairs (Y and X_t share)
-    case PSD_PREC_MIXED: return 9;   // X_0 pair + X_0 FP16 + three BF16 pairs
-    default: return 4;               // X_0 + three rotating 16-bit (or e4m3) matrices
-  }
-}
+int slots_needed(psd_precision_t prec) { return chain_slots(prec); }
 
 size_t total_ws_bytes(int64_t n, psd_precision_t prec) {
   return slots_needed(prec) * slot_bytes(n) + lanczos_bytes(n) + 1024;
@@ -229,40 +198,8 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   return PSD_OK;
 }
 
-// A matrix of the chain living in workspace slots.
-enum MatKind : int { MK_16 = 0, MK_BF16X3 = 1, MK_TF32X3 = 2, MK_E4M3 = 3 };
-struct Mat {
-  int kind = MK_16;
-  int slot = -1;
-  int dt16 = DT_F16;  // element type of an MK_16 matrix
-  float scale = 1.f;  // MK_E4M3: stored value = RN_e4m3(value * scale)
-};
-
-int kind_slots(int kind) { return kind == MK_16 || kind == MK_E4M3 ? 1 : kind == MK_BF16X3 ? 2 : 4; }
-
-struct SlotPool {
-  uint32_t used = 0;
-  int nslots = 0;
-  int alloc(int k) {
-    for (int s = 0; s + k <= nslots; ++s) {
-      const uint32_t mask = ((1u << k) - 1u) << s;
-      if ((used & mask) == 0) {
-        used |= mask;
-        return s;
-      }
-    }
-    return -1;
-  }
-  void release(int s, int k) { used &= ~(((1u << k) - 1u) << s); }
-};
-
 void* part_ptr(const Plan* p, const Mat& m, int part) {
-  const int step = m.kind == MK_TF32X3 ? 2 : 1;
-  return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * step)) * p->slot_size;
-}
-
-int part_dtype(const Mat& m) {
-  return m.kind == MK_16 ? m.dt16 : m.kind == MK_E4M3 ? DT_E4M3 : m.kind == MK_BF16X3 ? DT_BF16X3 : DT_TF32X3;
+  return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * kind_lo_step(m.kind))) * p->slot_size;
 }
 
 GemmParams base_params(const Plan* p) {
@@ -274,7 +211,7 @@ GemmParams base_params(const Plan* p) {
   return g;
 }
 
-// One product C = epi(A * B).  A and B have the same kind; `out` is the
+// One product C = epi(A * B) (routes: chain.h gemm_route); `out` is the
 // output matrix (ignored for EPI_FINAL), `Y` the EPI_POLY operand.
 cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, const Mat* Y, float a, float b,
                  float c, float sc, unsigned* absmax, cudaStream_t s) {
@@ -287,99 +224,61 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
   g.ep.absmax = absmax;
   if (epi != EPI_FINAL) {
     g.ep.C = part_ptr(p, *out, 0);
-    g.ep.C_lo = (out->kind == MK_16 || out->kind == MK_E4M3) ? nullptr : part_ptr(p, *out, 1);
+    g.ep.C_lo = kind_is_pair(out->kind) ? part_ptr(p, *out, 1) : nullptr;
     g.ep.ldc = ldm;
   }
   if (epi == EPI_POLY) {
     g.ep.Y = part_ptr(p, *Y, 0);
-    g.ep.Y_lo = (Y->kind == MK_16 || Y->kind == MK_E4M3) ? nullptr : part_ptr(p, *Y, 1);
+    g.ep.Y_lo = kind_is_pair(Y->kind) ? part_ptr(p, *Y, 1) : nullptr;
     g.ep.ldy = ldm;
   }
   g.ep.in_scale = 1.f / (A.scale * B.scale);
   g.ep.y_scale = Y ? 1.f / Y->scale : 1.f;
   g.ep.out_scale = out ? out->scale : 1.f;
   const int grid = num_sms();
-  if (A.kind == MK_16 || A.kind == MK_E4M3) {
-    const int dt = part_dtype(A);
+  const GemmRoute route = gemm_route(A, B);
+  if (route == ROUTE_16) {
+    const int dt = kind_dtype(A);
     CUtensorMap ta, tb;
     if (!encode_tmap(&ta, dt, part_ptr(p, A, 0), n, ldm, 128) || !encode_tmap(&tb, dt, part_ptr(p, B, 0), n, ldm, 256))
       return cudaErrorInvalidValue;
     const uint32_t fmt = dt == DT_BF16 ? 1u : 0u;  // F16 and E4M3 are both format 0 in their MMA kinds
     g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);  // M = 128; N per tile
-    return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? part_dtype(*out) : -1);
+    return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? kind_dtype(*out) : -1);
   }
-  const int dt = part_dtype(A);
+  if (route == ROUTE_NONE) return cudaErrorNotSupported;
+  const bool a1 = route == ROUTE_X2;
+  const int dt = kind_dtype(B);
   CUtensorMap tm[4];
   if (!encode_tmap(&tm[0], dt, part_ptr(p, A, 0), n, ldm, 128) ||
-      !encode_tmap(&tm[1], dt, part_ptr(p, A, 1), n, ldm, 128) ||
+      !encode_tmap(&tm[1], dt, part_ptr(p, A, a1 ? 0 : 1), n, ldm, 128) ||
       !encode_tmap(&tm[2], dt, part_ptr(p, B, 0), n, ldm, 256) ||
       !encode_tmap(&tm[3], dt, part_ptr(p, B, 1), n, ldm, 256))
     return cudaErrorInvalidValue;
-  const int out_mode = epi == EPI_FINAL ? 2 : (out->kind == MK_16 ? 1 : 0);
-  return launch_symgemm_x3(A.kind == MK_TF32X3, epi, out_mode, tm, g, grid, s);
+  const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
+  return launch_symgemm_x3(dt, a1, epi, out_mode, tm, g, grid, s);
 }
+
+struct PlanOps {
+  Plan* p;
+  cudaStream_t s;
+  cudaError_t cast(const Mat& X0) {
+    return enqueue_scale_cast(kind_dtype(X0), p->d_args, p->d_state, p->n, part_ptr(p, X0, 0),
+                              kind_is_pair(X0.kind) ? part_ptr(p, X0, 1) : nullptr, p->ldm, s);
+  }
+  cudaError_t gemm(int epi, const Mat& A, const Mat& B, const Mat* out, const Mat* Y, float a, float b, float c,
+                   float sc, bool track) {
+    return psd::gemm(p, epi, A, B, out, Y, a, b, c, sc, track ? &p->d_state->absmax_bits : nullptr, s);
+  }
+  cudaError_t finish() { return enqueue_finalize(p->d_args, p->d_state, s); }
+};
 
 // Enqueue the whole projection (used for graph capture and for direct launch).
 cudaError_t enqueue_projection(Plan* p, cudaStream_t s) {
   cudaError_t e;
   if ((e = enqueue_norm_bound(p->L, p->d_args, p->d_state, s)) != cudaSuccess) return e;
-  SlotPool pool;
-  pool.nslots = p->nslots;
-  const int T = p->sched.T;
-  auto kind_of_stage = [&](int t) {
-    if (p->prec == PSD_PREC_FP32) return static_cast<int>(MK_TF32X3);
-    if (p->prec == PSD_PREC_MIXED && t < kMixedSplit) return static_cast<int>(MK_BF16X3);
-    if (p->prec == PSD_PREC_FP8_LATE && t >= T - kFp8Stages) return static_cast<int>(MK_E4M3);
-    return static_cast<int>(MK_16);
-  };
-  const int dt16 = dtype16_of(p->prec);
-  auto make = [&](int kind, float scale = 1.f) {
-    Mat m;
-    m.kind = kind;
-    m.dt16 = dt16;
-    m.scale = kind == MK_E4M3 ? scale : 1.f;
-    m.slot = pool.alloc(kind_slots(kind));
-    return m;
-  };
-  // X_0 in the first stage's storage (and an FP16 copy for the mixed final product)
-  Mat X0 = make(kind_of_stage(0));
-  Mat X0f16;
-  if (p->prec == PSD_PREC_MIXED) X0f16 = make(MK_16);
-  if (X0.slot < 0 || (p->prec == PSD_PREC_MIXED && X0f16.slot < 0)) return cudaErrorMemoryAllocation;
-  if ((e = enqueue_scale_cast(part_dtype(X0), p->d_args, p->d_state, p->n, part_ptr(p, X0, 0),
-                              X0.kind == MK_16 ? nullptr : part_ptr(p, X0, 1),
-                              p->prec == PSD_PREC_MIXED ? part_ptr(p, X0f16, 0) : nullptr, p->ldm, s)) !=
-      cudaSuccess)
-    return e;
-  Mat cur = X0;
-  for (int t = 0; t < T; ++t) {
-    const int k = kind_of_stage(t);
-    const int knext = t + 1 < T ? kind_of_stage(t + 1) : static_cast<int>(MK_16);
-    const int kout = (p->prec == PSD_PREC_FP32) ? static_cast<int>(MK_TF32X3) : knext;
-    Mat Y = make(k, kFp8ScaleY);
-    if (Y.slot < 0) return cudaErrorMemoryAllocation;
-    if ((e = gemm(p, EPI_COPY, cur, cur, &Y, nullptr, 0.f, 0.f, 0.f, 1.f, nullptr, s)) != cudaSuccess) return e;
-    Mat P = make(k, fp8_poly_scale(p->sched.coef[t]));
-    if (P.slot < 0) return cudaErrorMemoryAllocation;
-    if ((e = gemm(p, EPI_POLY, Y, Y, &P, &Y, static_cast<float>(p->sched.coef[t][0]),
-                  static_cast<float>(p->sched.coef[t][1]), static_cast<float>(p->sched.coef[t][2]), 1.f, nullptr,
-                  s)) != cudaSuccess)
-      return e;
-    pool.release(Y.slot, kind_slots(Y.kind));
-    Mat Xn = make(kout, kFp8ScaleX);
-    if (Xn.slot < 0) return cudaErrorMemoryAllocation;
-    unsigned* amax = (t == T - 1) ? &p->d_state->absmax_bits : nullptr;
-    if ((e = gemm(p, EPI_SCALE, cur, P, &Xn, nullptr, 0.f, 0.f, 0.f, static_cast<float>(1.0 / p->sched.post[t]),
-                  amax, s)) != cudaSuccess)
-      return e;
-    pool.release(P.slot, kind_slots(P.kind));
-    if (cur.slot != X0.slot) pool.release(cur.slot, kind_slots(cur.kind));
-    cur = Xn;
-  }
-  // out = (X + lam~ X_0 X_T) / 2
-  const Mat& A0 = (p->prec == PSD_PREC_MIXED) ? X0f16 : X0;
-  if ((e = gemm(p, EPI_FINAL, A0, cur, nullptr, nullptr, 0.f, 0.f, 0.f, 1.f, nullptr, s)) != cudaSuccess) return e;
-  return enqueue_finalize(p->d_args, p->d_state, s);
+  PlanOps ops{p, s};
+  return run_chain(p->prec, p->sched, p->nslots, dtype16_of(p->prec), ops);
 }
 
 Plan* get_plan(int dev, cudaStream_t stream, int64_t n, psd_precision_t prec, void* user_ws, size_t user_bytes,
@@ -560,6 +459,7 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16 && !split && !f8) return PSD_ERR_INVALID_ARG;
   if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;
   if (f8 && (epi == 3 || (ld % 16) != 0 || !params)) return PSD_ERR_INVALID_ARG;
+  if (precision == PSD_PREC_MIXED && epi == 3) return PSD_ERR_INVALID_ARG;  // FP16 pairs: epi 0-2
   if ((epi == 1 || epi == 2 || epi == 3) && !params) return PSD_ERR_INVALID_ARG;
   if ((epi == 1 || epi == 3) && !aux) return PSD_ERR_INVALID_ARG;
   if (epi == 3 && (ld_aux < n || ld_out < n)) return PSD_ERR_INVALID_ARG;
@@ -593,7 +493,7 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     ps.ntiles[n] = static_cast<int>(tl.size());
   }
   const int dtype = precision == PSD_PREC_BF16    ? DT_BF16
-                    : precision == PSD_PREC_MIXED ? DT_BF16X3
+                    : precision == PSD_PREC_MIXED ? DT_F16X2
                     : precision == PSD_PREC_FP32  ? DT_TF32X3
                     : f8                          ? DT_E4M3
                                                   : DT_F16;
@@ -653,7 +553,7 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     if (!encode_tmap(&tm[0], dtype, a8, n, ld, 128) || !encode_tmap(&tm[1], dtype, a8 + pair, n, ld, 128) ||
         !encode_tmap(&tm[2], dtype, b8, n, ld, 256) || !encode_tmap(&tm[3], dtype, b8 + pair, n, ld, 256))
       return PSD_ERR_CUDA;
-    e = launch_symgemm_x3(dtype == DT_TF32X3, epi, epi == 3 ? 2 : 0, tm, g, num_sms(), s);
+    e = launch_symgemm_x3(dtype, false, epi, epi == 3 ? 2 : 0, tm, g, num_sms(), s);
   }
   return e == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
 }

@@ -316,7 +316,7 @@ bool enqueue_prep(psd_server* s, Request* r, int& launches) {
   if (enqueue_set_args(largs, h, ls) != cudaSuccess) return false;
   if (cudaGraphLaunch(g, ls) != cudaSuccess) return false;
   adopt_kernel<<<1, 1, 0, ls>>>(rec_args(s, r->slot), rec_state(s, r->slot), largs, lst);
-  if (enqueue_scale_cast(r->dt, rec_args(s, r->slot), rec_state(s, r->slot), n, base, nullptr, nullptr, s->ldm,
+  if (enqueue_scale_cast(r->dt, rec_args(s, r->slot), rec_state(s, r->slot), n, base, nullptr, s->ldm,
                          ls) != cudaSuccess)
     return false;
   if (cudaEventRecord(s->prep_ev[r->slot], ls) != cudaSuccess) return false;

@@ -173,42 +173,13 @@ __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t* src, int f
 // accumulator at column c0 + j.  Diagonal chunks (r0 == c0) are symmetrised
 // from their upper part; off-diagonal chunks are written at both positions,
 // (r, c) and (c, r), with 16-byte stores from the staged copies.
-template <int EPI, bool IN8, bool OUT8>
-__device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const BlockRec& br, bool bf16, int n,
-                                                 void* Cv, int r0, int c0, const uint32_t (&v)[32],
-                                                 uint8_t* wbuf, const uint4 (&y)[4], int lane, bool track,
-                                                 unsigned& amax_bits) {
-  const bool pb = p.ep.per_block_coef != 0;
-  const float ca = pb ? br.ca : p.ep.a, cb = pb ? br.cb : p.ep.b, cc = pb ? br.cc : p.ep.c;
-  const float cs = pb ? br.cs : p.ep.s;
-  uint16_t* S = reinterpret_cast<uint16_t*>(wbuf);  // [32][kH] row t = output row r0 + t
-  uint16_t* ST = S + 32 * kH;                        // [32][kH] row j = output column c0 + j
-  uint16_t* YB = ST + 32 * kH;                       // [32][kH] row j = Y column c0 + j
-  const int r = r0 + lane;
-  const bool diag = (r0 == c0);
-  if (EPI == EPI_POLY) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      *reinterpret_cast<uint4*>(YB + ((lane >> 2) + 8 * k) * kH + 8 * (lane & 3)) = y[k];
-    __syncwarp();
-  }
-  uint32_t h[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    float acc = __uint_as_float(v[j]);
-    if (IN8) acc *= p.ep.in_scale;
-    float val;
-    if (EPI == EPI_POLY) {
-      const float yv = from16(YB[j * kH + lane], IN8 ? false : bf16);
-      val = fmaf(cc, acc, cb * yv);
-      if (diag && j == lane) val += ca;
-    } else if (EPI == EPI_SCALE) {
-      val = acc * cs;
-    } else {
-      val = acc;
-    }
-    h[j] = OUT8 ? to8(val * p.ep.out_scale) : to16(val, bf16);
-  }
+// Stages a 32 x 32 chunk of 16-bit codes (h[j] = code at (r0 + lane, c0 + j))
+// and writes it at (r, c) and, unless diagonal, mirrored at (c, r); diagonal
+// chunks are symmetrised from their upper part first (h is updated to the
+// symmetric codes).  OUTK 1 writes the low bytes (e4m3 codes).
+template <int OUTK>
+__device__ __forceinline__ void stage_store16(uint32_t (&h)[32], uint16_t* S, uint16_t* ST, bool diag, void* Cv,
+                                              int64_t ldc, int n, int r0, int c0, int lane) {
   uint16_t* row = S + lane * kH;
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -230,13 +201,7 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
 #pragma unroll
     for (int j = 0; j < 32; ++j) ST[j * kH + lane] = static_cast<uint16_t>(h[j]);
   }
-  if (!OUT8 && track && r < n) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(from16(static_cast<uint16_t>(h[j]), bf16))));
-  }
   __syncwarp();
-  const int64_t ldc = p.ep.ldc;
   const int seg = 8 * (lane & 3);
   // memory rows c0 + j: output column c0 + j over rows r0..r0+31 (ST row j; S row j when symmetric)
   const uint16_t* SA = diag ? S : ST;
@@ -247,7 +212,7 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
     const int jj = (lane >> 2) + 8 * k;
     const int c = c0 + jj;
     if (c < n && r0 + seg < n) {
-      if (OUT8)
+      if (OUTK == 1)
         store8_u8(C8 + static_cast<int64_t>(c) * ldc + r0 + seg, SA + jj * kH + seg, r0 + seg, n);
       else
         store8(C + static_cast<int64_t>(c) * ldc + r0 + seg, SA + jj * kH + seg, r0 + seg, n);
@@ -260,7 +225,7 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
       const int tt = (lane >> 2) + 8 * k;
       const int rr = r0 + tt;
       if (rr < n && c0 + seg < n) {
-        if (OUT8)
+        if (OUTK == 1)
           store8_u8(C8 + static_cast<int64_t>(rr) * ldc + c0 + seg, S + tt * kH + seg, c0 + seg, n);
         else
           store8(C + static_cast<int64_t>(rr) * ldc + c0 + seg, S + tt * kH + seg, c0 + seg, n);
@@ -268,6 +233,61 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
     }
   }
   __syncwarp();
+}
+
+// One 32 x 32 chunk with 16-bit (or e4m3, or FP16 hi/lo pair) output.  Lane l
+// holds row r0 + l, v[j] is the accumulator at column c0 + j.
+//   OUTK 0: 16-bit (FP16 or BF16 by `bf16`), 1: e4m3 (value * out_scale),
+//   2: FP16 pair, hi = RN(value) at C, lo = RN(value - hi) at C_lo.
+template <int EPI, bool IN8, int OUTK>
+__device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const BlockRec& br, bool bf16, int n,
+                                                 void* Cv, void* Cv_lo, int r0, int c0, const uint32_t (&v)[32],
+                                                 uint8_t* wbuf, const uint4 (&y)[4], int lane, bool track,
+                                                 unsigned& amax_bits) {
+  const bool pb = p.ep.per_block_coef != 0;
+  const float ca = pb ? br.ca : p.ep.a, cb = pb ? br.cb : p.ep.b, cc = pb ? br.cc : p.ep.c;
+  const float cs = pb ? br.cs : p.ep.s;
+  uint16_t* S = reinterpret_cast<uint16_t*>(wbuf);  // [32][kH] row t = output row r0 + t
+  uint16_t* ST = S + 32 * kH;                        // [32][kH] row j = output column c0 + j
+  uint16_t* YB = ST + 32 * kH;                       // [32][kH] row j = Y column c0 + j
+  const int r = r0 + lane;
+  const bool diag = (r0 == c0);
+  if (EPI == EPI_POLY) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      *reinterpret_cast<uint4*>(YB + ((lane >> 2) + 8 * k) * kH + 8 * (lane & 3)) = y[k];
+    __syncwarp();
+  }
+  uint32_t h[32], l[OUTK == 2 ? 32 : 1];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    float acc = __uint_as_float(v[j]);
+    if (IN8) acc *= p.ep.in_scale;
+    float val;
+    if (EPI == EPI_POLY) {
+      const float yv = from16(YB[j * kH + lane], IN8 ? false : bf16);
+      val = fmaf(cc, acc, cb * yv);
+      if (diag && j == lane) val += ca;
+    } else if (EPI == EPI_SCALE) {
+      val = acc * cs;
+    } else {
+      val = acc;
+    }
+    if constexpr (OUTK == 2) {
+      h[j] = to16(val, false);
+      l[j] = to16(val - from16(static_cast<uint16_t>(h[j]), false), false);
+    } else {
+      h[j] = OUTK == 1 ? to8(val * p.ep.out_scale) : to16(val, bf16);
+    }
+  }
+  const int64_t ldc = p.ep.ldc;
+  stage_store16<OUTK>(h, S, ST, diag, Cv, ldc, n, r0, c0, lane);
+  if constexpr (OUTK == 2) stage_store16<0>(l, S, ST, diag, Cv_lo, ldc, n, r0, c0, lane);
+  if (OUTK == 0 && track && r < n) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < n) amax_bits = max(amax_bits, __float_as_uint(fabsf(from16(static_cast<uint16_t>(h[j]), bf16))));
+  }
 }
 
 // One 32 x 32 chunk of the final output out = (X + lam~ acc) / 2 in FP32,
@@ -322,7 +342,7 @@ __device__ __forceinline__ void epilogue_chunk_final(const BlockRec& br, int r0,
   }
 }
 
-template <int EPI, bool IN8, bool OUT8>
+template <int EPI, bool IN8, int OUTK>
 __global__ void __launch_bounds__(kThreads, 1)
     symgemm16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const GemmParams p, const int bf16_flag) {
@@ -483,7 +503,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const BlockRec& br = p.blocks[tc.z];
       const int n = br.n;
       const int64_t off = br.off;
-      void* C = static_cast<uint8_t*>(p.ep.C) + (off + br.dc) * p.ep.ldc * (OUT8 ? 1 : 2);
+      void* C = static_cast<uint8_t*>(p.ep.C) + (off + br.dc) * p.ep.ldc * (OUTK == 1 ? 1 : 2);
+      void* C_lo = OUTK == 2 ? static_cast<uint8_t*>(p.ep.C_lo) + (off + br.dc) * p.ep.ldc * 2 : nullptr;
       const uint8_t* Yb = static_cast<const uint8_t*>(p.ep.Y) + (off + br.dy) * p.ep.ldy * (IN8 ? 1 : 2);
       const bool track = track_launch && (p.ep.absmax_blocks != 2 || br.track != 0);
       if (track_launch && amax_block != tc.z) {
@@ -517,7 +538,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (EPI == EPI_FINAL)
           epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam);
         else
-          epilogue_chunk16<EPI, IN8, OUT8>(p, br, bf16, n, C, r0, c0, v, wbuf, ycur, lane, track, amax_bits);
+          epilogue_chunk16<EPI, IN8, OUTK>(p, br, bf16, n, C, C_lo, r0, c0, v, wbuf, ycur, lane, track,
+                                           amax_bits);
       }
       tc_fence_before();
       __syncwarp();
@@ -540,28 +562,30 @@ __global__ void __launch_bounds__(kThreads, 1)
 using Kernel16 = void (*)(const CUtensorMap, const CUtensorMap, const GemmParams, const int);
 
 // Instances: 16-bit operands with 16-bit output (every epilogue); e4m3
-// operands with e4m3 output (the FP8 stages), e4m3 operands with 16-bit output
+// operands with e4m3 output (the FP8 stages); e4m3 operands with 16-bit output
 // and 16-bit operands with e4m3 output (EPI_SCALE only: the last FP8 stage and
-// the stage before the first one).
-Kernel16 kernel16_for(int epi, bool in8, bool out8) {
-  if (!in8 && !out8) {
+// the stage before the first one); FP16 operands with an FP16 pair output
+// (EPI_COPY: Y = X^2 of the mixed precision's pair stages).
+Kernel16 kernel16_for(int epi, bool in8, int outk) {
+  if (!in8 && outk == 0) {
     switch (epi) {
-      case EPI_COPY: return symgemm16_kernel<EPI_COPY, false, false>;
-      case EPI_POLY: return symgemm16_kernel<EPI_POLY, false, false>;
-      case EPI_SCALE: return symgemm16_kernel<EPI_SCALE, false, false>;
-      default: return symgemm16_kernel<EPI_FINAL, false, false>;
+      case EPI_COPY: return symgemm16_kernel<EPI_COPY, false, 0>;
+      case EPI_POLY: return symgemm16_kernel<EPI_POLY, false, 0>;
+      case EPI_SCALE: return symgemm16_kernel<EPI_SCALE, false, 0>;
+      default: return symgemm16_kernel<EPI_FINAL, false, 0>;
     }
   }
-  if (in8 && out8) {
+  if (in8 && outk == 1) {
     switch (epi) {
-      case EPI_COPY: return symgemm16_kernel<EPI_COPY, true, true>;
-      case EPI_POLY: return symgemm16_kernel<EPI_POLY, true, true>;
-      case EPI_SCALE: return symgemm16_kernel<EPI_SCALE, true, true>;
+      case EPI_COPY: return symgemm16_kernel<EPI_COPY, true, 1>;
+      case EPI_POLY: return symgemm16_kernel<EPI_POLY, true, 1>;
+      case EPI_SCALE: return symgemm16_kernel<EPI_SCALE, true, 1>;
       default: return nullptr;
     }
   }
+  if (!in8 && outk == 2) return epi == EPI_COPY ? symgemm16_kernel<EPI_COPY, false, 2> : nullptr;
   if (epi != EPI_SCALE) return nullptr;
-  return in8 ? symgemm16_kernel<EPI_SCALE, true, false> : symgemm16_kernel<EPI_SCALE, false, true>;
+  return in8 ? symgemm16_kernel<EPI_SCALE, true, 0> : symgemm16_kernel<EPI_SCALE, false, 1>;
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -604,10 +628,10 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
   EncodeFn fn = get_encode();
   if (!fn) return false;
   const int esz = dtype == DT_TF32X3 ? 4 : (dtype == DT_E4M3 ? 1 : 2);
-  const CUtensorMapDataType dt = dtype == DT_F16                          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                 : (dtype == DT_BF16 || dtype == DT_BF16X3) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                 : dtype == DT_E4M3                         ? CU_TENSOR_MAP_DATA_TYPE_UINT8
-                                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = (dtype == DT_F16 || dtype == DT_F16X2) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : dtype == DT_BF16                     ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : dtype == DT_E4M3                     ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};
@@ -625,10 +649,10 @@ bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t col
   EncodeFn fn = get_encode();
   if (!fn) return false;
   const int esz = dtype == DT_TF32X3 ? 4 : (dtype == DT_E4M3 ? 1 : 2);
-  const CUtensorMapDataType dt = dtype == DT_F16                          ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                 : (dtype == DT_BF16 || dtype == DT_BF16X3) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                 : dtype == DT_E4M3                         ? CU_TENSOR_MAP_DATA_TYPE_UINT8
-                                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = (dtype == DT_F16 || dtype == DT_F16X2) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : dtype == DT_BF16                     ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : dtype == DT_E4M3                     ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};
@@ -673,11 +697,13 @@ cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUt
   if (dtype != DT_F16 && dtype != DT_BF16 && dtype != DT_E4M3) return cudaErrorNotSupported;
   if (out_dtype < 0) out_dtype = dtype;
   if (epi < EPI_COPY || epi > EPI_FINAL) return cudaErrorInvalidValue;
-  const bool in8 = dtype == DT_E4M3, out8 = epi != EPI_FINAL && out_dtype == DT_E4M3;
-  Kernel16 k = kernel16_for(epi, in8, out8);
+  const bool in8 = dtype == DT_E4M3;
+  const int outk = epi == EPI_FINAL ? 0 : out_dtype == DT_E4M3 ? 1 : out_dtype == DT_F16X2 ? 2 : 0;
+  if (outk == 2 && dtype != DT_F16) return cudaErrorNotSupported;
+  Kernel16 k = kernel16_for(epi, in8, outk);
   if (!k) return cudaErrorNotSupported;
-  static bool attr_set[16] = {};
-  const int idx = epi * 4 + (in8 ? 2 : 0) + (out8 ? 1 : 0);
+  static bool attr_set[24] = {};
+  const int idx = epi * 6 + (in8 ? 3 : 0) + outk;
   const int smem = smem_bytes16();
   if (!attr_set[idx]) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -5,13 +5,14 @@
 //   TF32 pairs (kind::tf32): the FP32 path; three-term TF32 splitting as in
 //     Ootomo & Yokota, "Recovering single precision accuracy from Tensor Cores
 //     while surpassing the FP32 theoretical peak performance" (IJHPCA 2022).
-//   BF16 pairs (kind::f16): about 16 significant bits at three BF16 products,
-//     the early stages of the mixed-precision chain (a split in the manner of
-//     Henry, Tang & Heinecke, "Leveraging the bfloat16 artificial intelligence
-//     datatype for higher-precision computations", ARITH 2019).
+//   FP16 pairs (kind::f16): about 22 significant bits (fewer where the lo part
+//     is subnormal) at three FP16 products; the Y^2 product of the
+//     mixed-precision chain's pair stages.
+// A variant with a single A operand (A1) forms A B_hi + A B_lo: the X P
+// product of those stages, where only P is a pair.
 // Same symmetric tiling, warp roles and fused stage epilogues as the 16-bit
-// kernel (symgemm.cu); the output is again a pair, or a single FP16 matrix
-// (the last split stage hands over to FP16), or the FP32 final result.
+// kernel (symgemm.cu); the output is again a pair, or a single FP16 matrix,
+// or the FP32 final result.
 //
 // Promoted accumulation (TF32 pairs): the tensor cores add into an FP32
 // accumulator without rounding to nearest, so over the 3 n / 8 accumulation
@@ -49,17 +50,17 @@ __host__ __device__ constexpr int smem_bytes_x3() {
   return 1024 + kStages * kStageBytes + 4 * kEpiWarpBytes + 8 * (2 * kStages + 5) + 16;
 }
 
-template <bool TF32>
+template <int ET>
 __device__ __forceinline__ float ld_elem(const void* p, int64_t idx) {
-  if (TF32) return static_cast<const float*>(p)[idx];
-  return __bfloat162float(__ushort_as_bfloat16(static_cast<const uint16_t*>(p)[idx]));
+  if (ET == DT_TF32X3) return static_cast<const float*>(p)[idx];
+  return __half2float(__ushort_as_half(static_cast<const uint16_t*>(p)[idx]));
 }
 
 __device__ __forceinline__ float tf32_rn(float v) {
   if (!isfinite(v)) return v;
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
-__device__ __forceinline__ float bf16_rn(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float f16_rn(float v) { return __half2float(__float2half_rn(v)); }
 
 // 4 consecutive elements of a staged column (col = true: S[t..t+3][j]) or row
 // (S[t][j..j+3]) to global memory as FP32, BF16 or FP16, clipped at `valid`.
@@ -123,10 +124,11 @@ __device__ __forceinline__ void store_chunk(void* C, int64_t ldc, int n, int r0,
 }
 
 // OUT: 0 = split pair of the operand kind, 1 = single FP16, 2 = FP32 final output.
-template <bool TF32, int EPI, int OUT>
+template <int ET, int EPI, int OUT>
 __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const BlockRec& br, int r0, int c0,
                                                   const uint32_t (&v)[32], float* S, float* YB, int lane, float lam,
                                                   bool track, unsigned& amax_bits) {
+  constexpr bool TF32 = ET == DT_TF32X3;
   const int n = br.n;
   const int64_t off = br.off;
   const bool pb = p.ep.per_block_coef != 0;
@@ -150,7 +152,7 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
       float y = 0.f;
       if (row_ok && c < n) {
         const int64_t idx = static_cast<int64_t>(c) * p.ep.ldy + r;
-        y = ld_elem<TF32>(Yh, idx) + ld_elem<TF32>(Yl, idx);
+        y = ld_elem<ET>(Yh, idx) + ld_elem<ET>(Yl, idx);
       }
       YB[j * kSW + lane] = y;
     }
@@ -216,8 +218,8 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
   float lo[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    const float hi = TF32 ? tf32_rn(o[j]) : bf16_rn(o[j]);
-    lo[j] = TF32 ? tf32_rn(o[j] - hi) : bf16_rn(o[j] - hi);
+    const float hi = TF32 ? tf32_rn(o[j]) : f16_rn(o[j]);
+    lo[j] = TF32 ? tf32_rn(o[j] - hi) : f16_rn(o[j] - hi);
     o[j] = hi;
   }
   if (track && row_ok) {
@@ -228,17 +230,17 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
 #pragma unroll
   for (int j = 0; j < 32; ++j) S[lane * kSW + j] = o[j];
   __syncwarp();
-  store_chunk<TF32 ? 0 : 1>(C, p.ep.ldc, n, r0, c0, diag, S, lane);
+  store_chunk<TF32 ? 0 : 2>(C, p.ep.ldc, n, r0, c0, diag, S, lane);
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < 32; ++j) S[lane * kSW + j] = lo[j];
   __syncwarp();
-  store_chunk<TF32 ? 0 : 1>(C_lo, p.ep.ldc, n, r0, c0, diag, S, lane);
+  store_chunk<TF32 ? 0 : 2>(C_lo, p.ep.ldc, n, r0, c0, diag, S, lane);
   __syncwarp();
   }
 }
 
-template <bool TF32, int EPI, int OUT>
+template <int ET, int EPI, int OUT, bool A1>
 __global__ void __launch_bounds__(kThreads, 1)
     symgemm_x3_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                       const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_desc(&tmAh);
-    tma_prefetch_desc(&tmAl);
+    if (!A1) tma_prefetch_desc(&tmAl);
     tma_prefetch_desc(&tmBh);
     tma_prefetch_desc(&tmBl);
   }
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  constexpr bool TF32 = ET == DT_TF32X3;
   constexpr int kKElems = TF32 ? 32 : 64;  // K elements per 128-byte row
   constexpr int kKStep = TF32 ? 8 : 16;    // K per MMA instruction (32 bytes)
   constexpr bool kPromote = TF32;
@@ -305,10 +308,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(full_bar(s), kStageBytes);
+          mbar_arrive_expect_tx(full_bar(s), A1 ? kStageBytes - kABytes : kStageBytes);
           const uint32_t base = smem_u32(stages + s * kStageBytes);
           tma_load_2d(base, &tmAh, kb * kKElems, ya, full_bar(s));
-          tma_load_2d(base + kABytes, &tmAl, kb * kKElems, ya, full_bar(s));
+          if (!A1) tma_load_2d(base + kABytes, &tmAl, kb * kKElems, ya, full_bar(s));
           tma_load_2d(base + 2 * kABytes, &tmBh, kb * kKElems, yb, full_bar(s));
           tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, yb, full_bar(s));
           last_parity[s] = static_cast<int>(ph);
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
               mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
-              mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
+              if (!A1) mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
             }
           }
           mma_commit(empty_bar(s));
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ch = ch_begin; ch < ch_end; ++ch) {
           uint32_t v[32];
           tmem_ld32(tmem_base + lanes + kBN + 32 * ch, v);
-          epilogue_chunk_x3<TF32, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
+          epilogue_chunk_x3<ET, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
         }
       } else {
         if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ch = ch_begin; ch < ch_end; ++ch) {
           uint32_t v[32];
           tmem_ld32(tmem_base + lanes + acc * kBN + 32 * ch, v);
-          epilogue_chunk_x3<TF32, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
+          epilogue_chunk_x3<ET, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
         }
         tc_fence_before();
         __syncwarp();
@@ -543,26 +546,39 @@ __global__ void __launch_bounds__(kThreads, 1)
 using KernelX3 = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
                           const GemmParams);
 
-template <bool TF32>
-KernelX3 pick(int epi, int out) {
-  if (epi == EPI_FINAL) return symgemm_x3_kernel<TF32, EPI_FINAL, 2>;
-  if (out == 1) {
-    if (epi == EPI_COPY) return symgemm_x3_kernel<TF32, EPI_COPY, 1>;
-    if (epi == EPI_POLY) return symgemm_x3_kernel<TF32, EPI_POLY, 1>;
-    return symgemm_x3_kernel<TF32, EPI_SCALE, 1>;
+// Instances: TF32 pairs (the FP32 path: pair outputs, the FP32 final output);
+// FP16 pairs (pair or FP16 outputs); FP16 single A with FP16 pair B (X P of
+// the mixed precision's pair stages, FP16 output).
+KernelX3 pick(int et, bool a1, int epi, int out) {
+  if (et == DT_TF32X3) {
+    if (a1) return nullptr;
+    if (epi == EPI_FINAL) return out == 2 ? symgemm_x3_kernel<DT_TF32X3, EPI_FINAL, 2, false> : nullptr;
+    if (out != 0) return nullptr;
+    if (epi == EPI_COPY) return symgemm_x3_kernel<DT_TF32X3, EPI_COPY, 0, false>;
+    if (epi == EPI_POLY) return symgemm_x3_kernel<DT_TF32X3, EPI_POLY, 0, false>;
+    return symgemm_x3_kernel<DT_TF32X3, EPI_SCALE, 0, false>;
   }
-  if (epi == EPI_COPY) return symgemm_x3_kernel<TF32, EPI_COPY, 0>;
-  if (epi == EPI_POLY) return symgemm_x3_kernel<TF32, EPI_POLY, 0>;
-  return symgemm_x3_kernel<TF32, EPI_SCALE, 0>;
+  if (et != DT_F16X2 || epi == EPI_FINAL) return nullptr;
+  if (a1) return (epi == EPI_SCALE && out == 1) ? symgemm_x3_kernel<DT_F16X2, EPI_SCALE, 1, true> : nullptr;
+  if (out == 1) {
+    if (epi == EPI_COPY) return symgemm_x3_kernel<DT_F16X2, EPI_COPY, 1, false>;
+    if (epi == EPI_POLY) return symgemm_x3_kernel<DT_F16X2, EPI_POLY, 1, false>;
+    return symgemm_x3_kernel<DT_F16X2, EPI_SCALE, 1, false>;
+  }
+  if (epi == EPI_COPY) return symgemm_x3_kernel<DT_F16X2, EPI_COPY, 0, false>;
+  if (epi == EPI_POLY) return symgemm_x3_kernel<DT_F16X2, EPI_POLY, 0, false>;
+  return symgemm_x3_kernel<DT_F16X2, EPI_SCALE, 0, false>;
 }
 
 }  // namespace
 
-// tm: A_hi, A_lo, B_hi, B_lo.  out: 0 = split pair, 1 = FP16 (EPI_FINAL: FP32 to args->out).
-cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm, const GemmParams& p, int grid,
-                              cudaStream_t stream) {
+// et: DT_TF32X3 or DT_F16X2; a_single: A is one FP16 matrix (tm[1] unused).
+// tm: A_hi, A_lo, B_hi, B_lo.  out: 0 = split pair, 1 = FP16 (EPI_FINAL: 2, FP32 to the block's out).
+cudaError_t launch_symgemm_x3(int et, bool a_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
+                              int grid, cudaStream_t stream) {
   if (p.num_tiles == 0) return cudaSuccess;
-  KernelX3 k = tf32 ? pick<true>(epi, out) : pick<false>(epi, out);
+  KernelX3 k = pick(et, a_single, epi, out);
+  if (!k) return cudaErrorNotSupported;
   const int smem = smem_bytes_x3();
   static KernelX3 done[32];
   static int ndone = 0;
@@ -574,7 +590,7 @@ cudaError_t launch_symgemm_x3(bool tf32, int epi, int out, const CUtensorMap* tm
     if (ndone < 32) done[ndone++] = k;
   }
   GemmParams q = p;
-  const uint32_t fmt = tf32 ? 2u : 1u;
+  const uint32_t fmt = et == DT_TF32X3 ? 2u : 0u;  // kind::tf32, or kind::f16 with FP16 operands
   q.idesc = make_idesc(fmt, kBM, 0);  // N comes from each tile
   const int g = std::max(1, std::min(grid, p.num_tiles));
   k<<<g, kThreads, smem, stream>>>(tm[0], tm[1], tm[2], tm[3], q);
