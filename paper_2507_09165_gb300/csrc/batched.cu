@@ -229,16 +229,18 @@ cudaError_t bgemm(BatchPlan* p, int epi, const Mat& A, const Mat& B, const Mat* 
     return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? kind_dtype(*out) : -1);
   }
   if (route == ROUTE_NONE) return cudaErrorNotSupported;
-  const bool a1 = route == ROUTE_X2;
-  const int dt = kind_dtype(B);
+  const bool b1 = route == ROUTE_X2;
+  const Mat& PA = b1 ? B : A;  // the pair operand goes first
+  const Mat& PB = b1 ? A : B;
+  const int dt = kind_dtype(PA);
   CUtensorMap tm[4];
-  if (!encode_tmap_rows(&tm[0], dt, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
-      !encode_tmap_rows(&tm[1], dt, bpart(p, A, a1 ? 0 : 1), cols, rows, p->ldm, 128) ||
-      !encode_tmap_rows(&tm[2], dt, bpart(p, B, 0), cols, rows, p->ldm, 256) ||
-      !encode_tmap_rows(&tm[3], dt, bpart(p, B, 1), cols, rows, p->ldm, 256))
+  if (!encode_tmap_rows(&tm[0], dt, bpart(p, PA, 0), cols, rows, p->ldm, 128) ||
+      !encode_tmap_rows(&tm[1], dt, bpart(p, PA, 1), cols, rows, p->ldm, 128) ||
+      !encode_tmap_rows(&tm[2], dt, bpart(p, PB, 0), cols, rows, p->ldm, 256) ||
+      !encode_tmap_rows(&tm[3], dt, bpart(p, PB, b1 ? 0 : 1), cols, rows, p->ldm, 256))
     return cudaErrorInvalidValue;
   const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
-  return launch_symgemm_x3(dt, a1, epi, out_mode, tm, g, grid, s);
+  return launch_symgemm_x3(dt, b1, epi, out_mode, tm, g, grid, s);
 }
 
 struct BatchOps {

@@ -166,7 +166,9 @@ cudaError_t run_chain(psd_precision_t prec, const Schedule& sched, int nslots, i
 // Which kernel forms a product of the given operand kinds:
 //   both MK_16 or both MK_E4M3: the 16-bit/e4m3 kernel (symgemm.cu);
 //   both pairs of one type:      the split kernel (symgemm_x3.cu), three products;
-//   MK_16 A with an MK_F16X2 B:  the split kernel's single-A instance, two products.
+//   MK_16 A with an MK_F16X2 B:  the split kernel's single-B instance with the
+//                                operands exchanged (B A = A B: they commute),
+//                                two products.
 enum GemmRoute : int { ROUTE_16 = 0, ROUTE_X3 = 1, ROUTE_X2 = 2, ROUTE_NONE = 3 };
 inline GemmRoute gemm_route(const Mat& A, const Mat& B) {
   if ((A.kind == MK_16 || A.kind == MK_E4M3) && A.kind == B.kind) return ROUTE_16;

@@ -129,8 +129,8 @@ cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUt
 // split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
 // out: 0 = split pair, 1 = single FP16, (EPI_FINAL) FP32 to the caller's output.
 // Split-operand products: et = DT_TF32X3 (TF32 pairs) or DT_F16X2 (FP16
-// pairs); a_single: A is one FP16 matrix and B an FP16 pair.
-cudaError_t launch_symgemm_x3(int et, bool a_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
+// pairs); b_single: A is an FP16 pair and B one FP16 matrix.
+cudaError_t launch_symgemm_x3(int et, bool b_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
                               int grid, cudaStream_t stream);
 int num_sms();
 

@@ -247,16 +247,18 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
     return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? kind_dtype(*out) : -1);
   }
   if (route == ROUTE_NONE) return cudaErrorNotSupported;
-  const bool a1 = route == ROUTE_X2;
-  const int dt = kind_dtype(B);
+  const bool b1 = route == ROUTE_X2;
+  const Mat& PA = b1 ? B : A;  // the pair operand goes first
+  const Mat& PB = b1 ? A : B;
+  const int dt = kind_dtype(PA);
   CUtensorMap tm[4];
-  if (!encode_tmap(&tm[0], dt, part_ptr(p, A, 0), n, ldm, 128) ||
-      !encode_tmap(&tm[1], dt, part_ptr(p, A, a1 ? 0 : 1), n, ldm, 128) ||
-      !encode_tmap(&tm[2], dt, part_ptr(p, B, 0), n, ldm, 256) ||
-      !encode_tmap(&tm[3], dt, part_ptr(p, B, 1), n, ldm, 256))
+  if (!encode_tmap(&tm[0], dt, part_ptr(p, PA, 0), n, ldm, 128) ||
+      !encode_tmap(&tm[1], dt, part_ptr(p, PA, 1), n, ldm, 128) ||
+      !encode_tmap(&tm[2], dt, part_ptr(p, PB, 0), n, ldm, 256) ||
+      !encode_tmap(&tm[3], dt, part_ptr(p, PB, b1 ? 0 : 1), n, ldm, 256))
     return cudaErrorInvalidValue;
   const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
-  return launch_symgemm_x3(dt, a1, epi, out_mode, tm, g, grid, s);
+  return launch_symgemm_x3(dt, b1, epi, out_mode, tm, g, grid, s);
 }
 
 struct PlanOps {

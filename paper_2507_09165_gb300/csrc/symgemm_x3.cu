@@ -8,8 +8,9 @@
 //   FP16 pairs (kind::f16): about 22 significant bits (fewer where the lo part
 //     is subnormal) at three FP16 products; the Y^2 product of the
 //     mixed-precision chain's pair stages.
-// A variant with a single A operand (A1) forms A B_hi + A B_lo: the X P
-// product of those stages, where only P is a pair.
+// A variant with a single B operand (B1) forms A_hi B + A_lo B: the P X (= X P,
+// the two commute) product of those stages, where only P is a pair; its
+// 64 KB stages (no B_lo) leave room for a third stage.
 // Same symmetric tiling, warp roles and fused stage epilogues as the 16-bit
 // kernel (symgemm.cu); the output is again a pair, or a single FP16 matrix,
 // or the FP32 final result.
@@ -37,18 +38,24 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBN = 256;
 constexpr int kThreads = 192;
-constexpr int kStages = 2;
 constexpr int kABytes = kBM * 128;  // one 128-byte swizzle row of K per operand row
 constexpr int kBBytes = kBN * 128;
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;  // 96 KB: A_hi | A_lo | B_hi | B_lo
 constexpr int kSW = 33;                                 // staging row stride (words)
 constexpr int kEpiWarpBytes = 2 * 32 * kSW * 4;         // values + Y chunk
 constexpr int kTmemCols = 512;
 constexpr int kPromoteK = 128;  // K elements per promoted chunk (TF32 pairs)
 
-__host__ __device__ constexpr int smem_bytes_x3() {
-  return 1024 + kStages * kStageBytes + 4 * kEpiWarpBytes + 8 * (2 * kStages + 5) + 16;
-}
+// Pipeline: 2 stages of 96 KB (A_hi | A_lo | B_hi | B_lo), or with a single B
+// 3 stages of 64 KB (A_hi | A_lo | B).
+template <bool B1>
+struct X3Cfg {
+  static constexpr int kStages = B1 ? 3 : 2;
+  static constexpr int kStageBytes = B1 ? 2 * kABytes + kBBytes : 2 * kABytes + 2 * kBBytes;
+  static constexpr int smem() {
+    return 1024 + kStages * kStageBytes + 4 * kEpiWarpBytes + 8 * (2 * kStages + 5) + 16;
+  }
+};
+static_assert(X3Cfg<false>::smem() <= 232448 && X3Cfg<true>::smem() <= 232448, "shared memory per CTA");
 
 template <int ET>
 __device__ __forceinline__ float ld_elem(const void* p, int64_t idx) {
@@ -240,11 +247,13 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
   }
 }
 
-template <int ET, int EPI, int OUT, bool A1>
+template <int ET, int EPI, int OUT, bool B1>
 __global__ void __launch_bounds__(kThreads, 1)
     symgemm_x3_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                       const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                       const GemmParams p) {
+  constexpr int kStages = X3Cfg<B1>::kStages;
+  constexpr int kStageBytes = X3Cfg<B1>::kStageBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -275,9 +284,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_desc(&tmAh);
-    if (!A1) tma_prefetch_desc(&tmAl);
+    tma_prefetch_desc(&tmAl);
     tma_prefetch_desc(&tmBh);
-    tma_prefetch_desc(&tmBl);
+    if (!B1) tma_prefetch_desc(&tmBl);
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_holder), kTmemCols);
@@ -308,12 +317,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(full_bar(s), A1 ? kStageBytes - kABytes : kStageBytes);
+          mbar_arrive_expect_tx(full_bar(s), kStageBytes);
           const uint32_t base = smem_u32(stages + s * kStageBytes);
           tma_load_2d(base, &tmAh, kb * kKElems, ya, full_bar(s));
-          if (!A1) tma_load_2d(base + kABytes, &tmAl, kb * kKElems, ya, full_bar(s));
+          tma_load_2d(base + kABytes, &tmAl, kb * kKElems, ya, full_bar(s));
           tma_load_2d(base + 2 * kABytes, &tmBh, kb * kKElems, yb, full_bar(s));
-          tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, yb, full_bar(s));
+          if (!B1) tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, yb, full_bar(s));
           last_parity[s] = static_cast<int>(ph);
           if (++s == kStages) {
             s = 0;
@@ -418,8 +427,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_tf32(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
             } else {
               mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
-              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
-              if (!A1) mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
+              if (!B1) mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
+              mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
             }
           }
           mma_commit(empty_bar(s));
@@ -547,11 +556,11 @@ using KernelX3 = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMa
                           const GemmParams);
 
 // Instances: TF32 pairs (the FP32 path: pair outputs, the FP32 final output);
-// FP16 pairs (pair or FP16 outputs); FP16 single A with FP16 pair B (X P of
+// FP16 pairs (pair or FP16 outputs); FP16 pair A with a single FP16 B (P X of
 // the mixed precision's pair stages, FP16 output).
-KernelX3 pick(int et, bool a1, int epi, int out) {
+KernelX3 pick(int et, bool b1, int epi, int out) {
   if (et == DT_TF32X3) {
-    if (a1) return nullptr;
+    if (b1) return nullptr;
     if (epi == EPI_FINAL) return out == 2 ? symgemm_x3_kernel<DT_TF32X3, EPI_FINAL, 2, false> : nullptr;
     if (out != 0) return nullptr;
     if (epi == EPI_COPY) return symgemm_x3_kernel<DT_TF32X3, EPI_COPY, 0, false>;
@@ -559,7 +568,7 @@ KernelX3 pick(int et, bool a1, int epi, int out) {
     return symgemm_x3_kernel<DT_TF32X3, EPI_SCALE, 0, false>;
   }
   if (et != DT_F16X2 || epi == EPI_FINAL) return nullptr;
-  if (a1) return (epi == EPI_SCALE && out == 1) ? symgemm_x3_kernel<DT_F16X2, EPI_SCALE, 1, true> : nullptr;
+  if (b1) return (epi == EPI_SCALE && out == 1) ? symgemm_x3_kernel<DT_F16X2, EPI_SCALE, 1, true> : nullptr;
   if (out == 1) {
     if (epi == EPI_COPY) return symgemm_x3_kernel<DT_F16X2, EPI_COPY, 1, false>;
     if (epi == EPI_POLY) return symgemm_x3_kernel<DT_F16X2, EPI_POLY, 1, false>;
@@ -572,14 +581,14 @@ KernelX3 pick(int et, bool a1, int epi, int out) {
 
 }  // namespace
 
-// et: DT_TF32X3 or DT_F16X2; a_single: A is one FP16 matrix (tm[1] unused).
+// et: DT_TF32X3 or DT_F16X2; b_single: B is one FP16 matrix (tm[3] unused).
 // tm: A_hi, A_lo, B_hi, B_lo.  out: 0 = split pair, 1 = FP16 (EPI_FINAL: 2, FP32 to the block's out).
-cudaError_t launch_symgemm_x3(int et, bool a_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
+cudaError_t launch_symgemm_x3(int et, bool b_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
                               int grid, cudaStream_t stream) {
   if (p.num_tiles == 0) return cudaSuccess;
-  KernelX3 k = pick(et, a_single, epi, out);
+  KernelX3 k = pick(et, b_single, epi, out);
   if (!k) return cudaErrorNotSupported;
-  const int smem = smem_bytes_x3();
+  const int smem = b_single ? X3Cfg<true>::smem() : X3Cfg<false>::smem();
   static KernelX3 done[32];
   static int ndone = 0;
   bool set = false;
