@@ -66,8 +66,11 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
+// The FP32 estimate (FP64 runs at a small fraction of the FP32 rate on this GPU,
+// and every thread of a tile's CTA evaluates this) is corrected exactly by the
+// integer loops.
 __device__ __forceinline__ void tile_of(int t, int& bi, int& bj) {
-  int j = static_cast<int>((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  int j = static_cast<int>((sqrtf(8.f * static_cast<float>(t) + 1.f) - 1.f) * 0.5f);
   while ((j + 1) * (j + 2) / 2 <= t) ++j;
   while (j * (j + 1) / 2 > t) --j;
   bj = j;
