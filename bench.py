@@ -356,14 +356,18 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize(dev)
+    # one event per step boundary (recording an event between projections costs nothing
+    # measurable and gives the per-step distribution)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with Clocks(dev.index) as clk:
-        ev0.record(s)
-        for _ in range(args.steps):
+        evs[0].record(s)
+        for k in range(args.steps):
             b.psd_project(n, Xd, n, out, prec, s)
-        ev1.record(s)
+            evs[k + 1].record(s)
         torch.cuda.synchronize(dev)
     barrier()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    ms_step = evs[0].elapsed_time(evs[-1]) / args.steps
     if world > 1:
         t = torch.tensor([ms_step], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -466,6 +470,8 @@ def run_ours(args):
             "e2e": None if e2e_ms is None else {"value": e2e_ms / world, "unit": "ms",
                                                 "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": n * n * 4},
             "gpu_launches": launches * args.steps,
+            "step_stats_ms": {"median": statistics.median(per_step), "mean": statistics.fmean(per_step),
+                              "std": statistics.pstdev(per_step), "min": min(per_step), "max": max(per_step)},
             "fp32_path": None if fp32_ms is None else {
                 "ms": fp32_ms, "speedup": fp32_ms / ms_step,
                 "what": "same library, precision fp32 (TF32x3 products, f~*_single, 31 products), same matrix"},
