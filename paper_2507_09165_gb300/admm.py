@@ -13,7 +13,10 @@ projection).  Progress is measured with the surrogate KKT residual of Sec. 5
 
 `Solve` holds one solve's iterates; `run_serving` interleaves many solves
 whose arrivals are Poisson and whose iterations are closed-loop (the next
-request is issued a random think time after the previous one completes).
+request is issued a random think time after the previous one completes);
+`solve` runs one solve to a tolerance with the warm-start schedule of Sec. 5
+(low-precision projections until the surrogate first drops below 1e-2, then
+high-precision ones).
 """
 import math
 import time
@@ -176,3 +179,33 @@ def summarize(result):
         out["eta_median_by_n"] = {str(n): float(np.median([s["eta"] for s in result["solves"] if s["n"] == n]))
                                   for n in sorted({s["n"] for s in result["solves"]})}
     return out
+
+
+def solve(C, project, sigma=1.0, max_iters=5000, eta_switch=1e-2, eta_tol=1e-4, check_every=10,
+          low="mixed", high="fp32"):
+    """The ADMM solver of Sec. 5 with its warm-start schedule: iterate with the
+    `low` precision projection until the surrogate KKT residual (primal and
+    dual infeasibility, relative gap) first drops below eta_switch, then with
+    `high` until it drops below eta_tol or max_iters is reached.
+
+    project(V, S, precision) writes Pi(V) into S (both (n, n) tensors on C's
+    device; on a GPU, e.g. a psd_project call).  The surrogate is evaluated
+    every `check_every` iterations.  Returns dict(X, S, y, iters, switch_iter,
+    history=[(iteration, precision, eta)]).
+    """
+    sv = Solve(C, sigma, max_iters)
+    prec = low
+    switch_iter = None
+    history = []
+    for k in range(1, max_iters + 1):
+        V = sv.make_input()
+        project(V, sv.S, prec)
+        sv.finish_iteration()
+        if k % check_every == 0 or k == max_iters:
+            eta, _ = sv.surrogate()
+            history.append((k, prec, eta))
+            if prec == low and eta < eta_switch:
+                prec, switch_iter = high, k
+            elif prec == high and eta < eta_tol:
+                break
+    return dict(X=sv.X, S=sv.S, y=sv.y, iters=k, switch_iter=switch_iter, history=history)

@@ -59,3 +59,26 @@ def test_first_projection_input():
     V = sv.make_input().numpy()
     np.testing.assert_allclose(sv.y.numpy(), 0.5 + np.diag(C))
     np.testing.assert_allclose(V, C - np.diag(0.5 + np.diag(C)))
+
+
+def test_solver_switches_precision_and_converges():
+    # a deliberately coarse "low" projection (the exact one rounded to 3
+    # significant digits) stalls above the switch threshold's neighbourhood; the
+    # solver must switch to the exact "high" projection once the surrogate drops
+    # below 1e-2 and then converge to 1e-6
+    from paper_2507_09165_gb300.admm import solve
+
+    def project(V, S, prec):
+        P = exact_projection(V)
+        if prec == "low":
+            P = torch.from_numpy(np.round(P.numpy(), 3))
+        S.copy_(P)
+
+    C = torch.from_numpy(-cycle_laplacian(5) / 4.0)
+    r = solve(C, project, sigma=1.0, max_iters=4000, eta_switch=1e-2, eta_tol=1e-6, check_every=5,
+              low="low", high="high")
+    assert r["switch_iter"] is not None
+    assert all(p == "low" for k, p, _ in r["history"] if k <= r["switch_iter"])
+    assert r["history"][-1][2] < 1e-6
+    pobj = float((C * r["X"]).sum())
+    assert abs(pobj + (25 + 5 * math.sqrt(5)) / 8) < 1e-5

@@ -39,3 +39,30 @@ def test_served_admm_matches_direct_calls():
         assert eta == sd["eta"], (sd, eta)
     summary = admm.summarize(res)
     assert summary["bad_status"] == 0 and summary["requests"] == len(res["records"])
+
+
+def test_solver_warm_start_matches_exact_admm():
+    # max-cut SDP of a small random graph: the GPU solver (mixed projections,
+    # then FP32 ones once the surrogate is below 1e-2) reaches the optimum the
+    # same ADMM finds with exact (eigendecomposition) projections on the CPU
+    n = 120
+    L = synth.er_laplacian(n, 21, p=0.1)
+    C64 = -L / 4.0
+    C = torch.from_numpy(C64.astype(np.float32)).cuda()
+
+    def project_gpu(V, S, prec):
+        b.psd_project(n, V, n, S, prec)
+
+    r = admm.solve(C, project_gpu, sigma=1.0, max_iters=3000, eta_switch=1e-2, eta_tol=1e-4, check_every=10)
+    assert r["switch_iter"] is not None and r["history"][-1][1] == "fp32"
+    assert r["history"][-1][2] < 1e-4, r["history"][-5:]
+    pobj = float((C.double() * r["X"].double()).sum())
+
+    def project_cpu(V, S, prec):
+        w, Q = np.linalg.eigh(V.double().numpy())
+        S.copy_(torch.from_numpy((Q * np.maximum(w, 0.0)) @ Q.T))
+
+    ref = admm.solve(torch.from_numpy(C64), project_cpu, sigma=1.0, max_iters=6000, eta_switch=1e-2,
+                     eta_tol=1e-7, check_every=50)
+    pref = float((torch.from_numpy(C64) * ref["X"]).sum())
+    assert abs(pobj - pref) <= 1e-3 * abs(pref), (pobj, pref)
