@@ -11,7 +11,10 @@ Projection onto the PSD Cone with Composite Polynomial Filtering):
 * ``lanczos_bound``    the norm bound of Sec. 3.4 / Theorem 2 (FP64 Lanczos);
 * ``chain_fp64``       Algorithm 2 stage by stage in FP64;
 * ``composite``, ``efloat``, ``stage_image``  scalar checks (Sec. 3.1-3.3);
-* ``rel_err``, ``band_errors``  the FP64 error metrics (Sec. 4.1).
+* ``rel_err``, ``band_errors``  the FP64 error metrics (Sec. 4.1);
+* ``deflate_project``  deflation of the dominant Ritz pairs, then the filter
+                       (the remedy of Sec. 6, in this library's reading);
+* ``remez.sequential_remez``  Stage I of the coefficient design (Algorithm 1).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
 ``cpu_baseline`` / ``--impl reference`` leg may import, call, link or run
@@ -20,6 +23,7 @@ imports it.  Every function here is pinned, against closed forms, invariants
 and the values the paper prints, by ``tests/test_oracle_*.py``.
 """
 from . import schedules
+from .deflate import DEFLATE_TOL, deflate_project, ritz_pairs
 from ._clib import build as build_clib
 from .core import (BANDS, LANCZOS_SEED, band_errors, chain_fp64, composite, efloat,
                    eigh_jacobi, filter_from_eig, lanczos_bound, lanczos_start, phi,

@@ -146,7 +146,7 @@ def lanczos_bound(X, steps=LANCZOS_STEPS, seed=LANCZOS_SEED, breakdown=1e-12):
         an upper bound.
     Returns a dict with lam_tilde, sigma, resid, m, alpha, beta, beta_m (the
     norm of the m-th residual vector), y (Ritz vector in the Lanczos basis),
-    fro, maxdiag.
+    fro, maxdiag, Q (the n x m Lanczos basis).
     """
     X = np.asarray(X, dtype=np.float64)
     n = X.shape[0]
@@ -154,7 +154,7 @@ def lanczos_bound(X, steps=LANCZOS_STEPS, seed=LANCZOS_SEED, breakdown=1e-12):
     maxdiag = float(np.max(np.abs(np.diag(X)))) if n else 0.0
     if n == 0:
         return dict(lam_tilde=0.0, sigma=0.0, resid=0.0, m=0, alpha=[], beta=[], beta_m=0.0,
-                    y=np.zeros(0), fro=0.0, maxdiag=0.0)
+                    y=np.zeros(0), fro=0.0, maxdiag=0.0, Q=np.zeros((0, 0)))
     Qv = np.zeros((n, steps))
     alpha = []
     beta = []
@@ -189,7 +189,7 @@ def lanczos_bound(X, steps=LANCZOS_STEPS, seed=LANCZOS_SEED, breakdown=1e-12):
     lam = math.sqrt(max(sigma + resid, 0.0))
     lam = max(lam, fro / math.sqrt(n), maxdiag)
     return dict(lam_tilde=lam, sigma=sigma, resid=resid, m=m, alpha=alpha, beta=beta[: m - 1],
-                beta_m=beta_m, y=y, fro=fro, maxdiag=maxdiag)
+                beta_m=beta_m, y=y, fro=fro, maxdiag=maxdiag, Q=Qv[:, :m].copy())
 
 
 # ---------------------------------------------------------------------------
