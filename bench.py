@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-block batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the ADMM serving leg")
     ap.add_argument("--no-bands", action="store_true", help="skip the per-band accuracy leg (n = 4096)")
+    ap.add_argument("--no-deflate", action="store_true", help="skip the deflation leg (power law at the bench order)")
     ap.add_argument("--serve-rate", type=float, default=8.0, help="ADMM solve arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=2.5, help="length of the arrival window")
     ap.add_argument("--serve-iters", type=int, default=50, help="ADMM iterations per solve")
@@ -190,7 +191,9 @@ BANDS = ((0.0, 1e-4), (1e-4, 1e-3), (1e-3, 1e-2), (1e-2, 1e-1), (1e-1, 1.0 + 1e-
 def bands_leg(dev, n=4096, precisions=("fp16", "bf16", "mixed", "fp8_late", "fp32")):
     """Spectrum-controlled X = Q diag(l) Q^T, n = 4096, Haar Q; l uniform on [-1, 1], clustered
     around 0, power law (seeds 4-6).  Per precision: relative error against Pi overall and per
-    band of |l| / ||X||_2 split by sign, ||(out - Pi) Q_B||_F / ||l_B||_2."""
+    band of |l| / ||X||_2 split by sign, ||(out - Pi) Q_B||_F / ||l_B||_2.  For the clustered and
+    power-law spectra also psd_project_deflate (up to 16 dominant Ritz pairs deflated) with mixed
+    and fp32: pairs deflated, errors, and ms against the plain call (median of 3 after one warm-up)."""
     import numpy as np
     import torch
     from paper_2507_09165_gb300 import binding as b
@@ -223,11 +226,84 @@ def bands_leg(dev, n=4096, precisions=("fp16", "bf16", "mixed", "fp8_late", "fp3
             entry[prec] = {"status": inf["status"], "rel_err_Pi": rel_fro(o, P), "rel_err_F": rel_fro(o, F),
                            "bands_vs_Pi": {k: float(np.sqrt(col[m].sum()) / np.linalg.norm(lam[m]))
                                            for k, m in sel.items()}}
+        if kind != "uniform":  # deflation of the dominant Ritz pairs (Sec. 6 remedy)
+            kused = torch.zeros(1, dtype=torch.int32, device=dev)
+            for prec in ("mixed", "fp32"):
+                info = torch.zeros(b.INFO_BYTES, dtype=torch.uint8, device=dev)
+                b.psd_project_deflate(n, Xd, n, out, n, prec, 16, info, kused)
+                torch.cuda.synchronize(dev)
+                inf = b.info_from_bytes(info.cpu().numpy())
+                o = out.cpu().numpy().astype(np.float64)
+                P = (Q * np.maximum(lam, 0.0)[None, :]) @ Q.T
+                DQ = (o - P) @ Q
+                col = np.sum(DQ * DQ, axis=0)
+                ms = {}
+                for name, fn in (("plain", lambda: b.psd_project_ex(n, Xd, n, out, n, prec)),
+                                 ("deflate", lambda: b.psd_project_deflate(n, Xd, n, out, n, prec, 16))):
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                    ts = []
+                    for _ in range(4):
+                        ev[0].record()
+                        fn()
+                        ev[1].record()
+                        torch.cuda.synchronize(dev)
+                        ts.append(ev[0].elapsed_time(ev[1]))
+                    ms[name] = float(np.median(ts[1:]))
+                entry[prec + "+deflate"] = {
+                    "status": inf["status"], "k_deflated": int(kused.item()),
+                    "lambda_bound_deflated": inf["lambda_bound"], "rel_err_Pi": rel_fro(o, P),
+                    "ms": ms["deflate"], "ms_plain": ms["plain"],
+                    "bands_vs_Pi": {k: float(np.sqrt(col[m].sum()) / np.linalg.norm(lam[m])) for k, m in sel.items()}}
         res[kind] = entry
         del Xd, out
     res["seconds"] = time.perf_counter() - t0
     res["workload"] = ("Q diag(l) Q^T, n = %d, Haar Q (QR of a Gaussian, diag R > 0); l: uniform [-1, 1] (seed 4), "
                        "clustered +-1e-3 around 0 with +-1 anchors (seed 5), |l_i| ~ i^-1.5 random signs (seed 6)" % n)
+    return res
+
+
+def deflate_leg(dev, n, precisions=("mixed", "fp16", "fp32"), kmax=16):
+    """The Sec. 6 failure mode at the headline order: X = Q diag(l) Q^T with
+    |l_i| = i^-1.5, random signs (power law), built on the device (seed 12).
+    Per precision: ms of psd_project_ex and of psd_project_deflate (median of 5
+    after 2 warm-ups, 3 for fp32), pairs deflated, and each result's relative
+    Frobenius error against Pi(X) = Q max(l, 0) Q^T (FP64 on the device)."""
+    import numpy as np
+    import torch
+    from paper_2507_09165_gb300 import binding as b, synth
+    t0 = time.perf_counter()
+    X, Q, lam = synth.spectral_matrix_device("powerlaw", n, 12, dev)
+    P = (Q * lam.clamp(min=0.0)[None, :]) @ Q.T
+    del Q
+    Pn = float(torch.linalg.norm(P))
+    out = torch.empty_like(X)
+    kused = torch.zeros(1, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    res = {}
+    for prec in precisions:
+        entry = {}
+        for name, fn in (("plain", lambda: b.psd_project_ex(n, X, n, out, n, prec, None, None, 0, s)),
+                         ("deflate", lambda: b.psd_project_deflate(n, X, n, out, n, prec, kmax, None, kused, s))):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize(dev)
+            ts = []
+            for _ in range(3 if prec == "fp32" else 5):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record(s)
+                fn()
+                ev[1].record(s)
+                torch.cuda.synchronize(dev)
+                ts.append(ev[0].elapsed_time(ev[1]))
+            err = float(torch.linalg.norm(out.double() - P)) / Pn
+            entry[name] = {"ms": float(np.median(ts)), "rel_err_Pi": err}
+        entry["k_deflated"] = int(kused.item())
+        res[prec] = entry
+    del X, P, out
+    torch.cuda.empty_cache()
+    res["workload"] = ("Q diag(l) Q^T, n = %d, Haar Q from a device QR (torch generator seed 12), "
+                       "|l_i| = i^-1.5 random signs; kmax = %d" % (n, kmax))
+    res["seconds"] = time.perf_counter() - t0
     return res
 
 
@@ -443,6 +519,9 @@ def run_ours(args):
     bands = None
     if rank == 0 and not args.no_bands:
         bands = bands_leg(dev)
+    deflate = None
+    if rank == 0 and not args.no_deflate:
+        deflate = deflate_leg(dev, n)
     acc = None
     if rank == 0 and not args.no_accuracy:
         acc = accuracy_check(n, prec, dev)
@@ -481,6 +560,7 @@ def run_ours(args):
             "batched": batched,
             "serving": serving,
             "bands": bands,
+            "deflate": deflate,
             "info": {k: info[k] for k in ("lambda_bound", "lanczos_steps", "overshoot_max")},
         }
         print(json.dumps(line), flush=True)

@@ -282,6 +282,41 @@ psd_status_t psd_server_stats(psd_server_t *server, psd_server_stats_t *stats);
  * frees the server's memory.  Tickets not yet retired are lost. */
 psd_status_t psd_server_destroy(psd_server_t *server);
 
+/* ---- Deflation of dominant eigenpairs ------------------------------------ */
+/* Projection with the dominant eigenpairs taken out first: the remedy Sec. 6
+ * (Limitations) names for spectra where a few eigenvalues of large modulus
+ * push the rest into the band around 0 that the composite filter resolves
+ * poorly (power-law and low-rank-plus-noise spectra).  Not part of
+ * Algorithm 2.  Steps, on `stream`:
+ *   1. the norm bound of X (Algorithm 2 steps 1-2, Theorem 2), keeping its
+ *      Lanczos basis Q_m of K_m(X^2, q_0) and the products X Q_m;
+ *   2. Rayleigh-Ritz with X on span(Q_m): eigenpairs (mu_j, w_j) of
+ *      Q_m^T X Q_m, Ritz vectors v_j = Q_m w_j;
+ *   3. of the kmax pairs of largest |mu_j|, those with
+ *      ||X v_j - mu_j v_j||_2 <= 1e-6 lam~ are deflated:
+ *      out = X - V diag(mu) V^T;
+ *   4. out <- psd_project_ex(out) in place with `precision` (its own norm
+ *      bound of the deflated matrix; *d_info is that call's report);
+ *   5. out += V diag(max(mu, 0)) V^T.
+ * For an invariant span(V) the result is Pi(X) up to the filter's error on
+ * the deflated matrix; the residual bound keeps the dropped coupling near
+ * 2 sqrt(k) 1e-6 lam~ in the Frobenius norm.  Eigenvalues +-lam of (nearly)
+ * equal modulus share one eigenvalue of X^2, so K_m(X^2, q_0) may not
+ * separate them; such pairs are deflated only if their residuals pass.
+ * X: n x n column-major device matrix, upper triangle read, ld >= n.
+ * out: n x n written (both triangles), ld_out >= n; out == X (same ld) is
+ * allowed, other overlaps are PSD_ERR_INVALID_ARG.  0 <= kmax <= 16
+ * (kmax == 0: plain psd_project_ex).  d_info (may be NULL): device report of
+ * step 4.  d_kused (may be NULL): device int32, the number of pairs deflated.
+ * Workspace: a library cache keyed by (device, stream, n), kept until
+ * psd_release_workspaces(), plus the psd_project_ex cache.
+ * Errors: PSD_ERR_INVALID_ARG for bad sizes/pointers, PSD_ERR_UNSUPPORTED off
+ * sm_103, PSD_ERR_NO_MEMORY, PSD_ERR_CUDA; device-side statuses as for
+ * psd_project_ex (a non-finite X deflates nothing and is reported by step 4). */
+psd_status_t psd_project_deflate(int64_t n, const float *X, int64_t ld, float *out, int64_t ld_out,
+                                 psd_precision_t precision, int32_t kmax, psd_info_t *d_info,
+                                 int32_t *d_kused, psd_stream_t stream);
+
 /* ---- Host-only queries (no GPU needed) ----------------------------------- */
 const char *psd_status_string(psd_status_t status);
 /* Copies the library's schedule for `precision`: *T stages, coef[3*t + {0,1,2}]

@@ -82,6 +82,7 @@ _SIGS = {
     "psd_server_cancel": ([_VP, ctypes.c_uint64], _I32),
     "psd_server_stats": ([_VP, ctypes.POINTER(psd_server_stats_t)], _I32),
     "psd_server_destroy": ([_VP], _I32),
+    "psd_project_deflate": ([_I64, _VP, _I64, _VP, _I64, _I32, _I32, _VP, _VP, _VP], _I32),
 }
 
 
@@ -142,6 +143,12 @@ def psd_project_ex(n, X, ld, out, ld_out, precision="fp16", d_info=None, workspa
                    stream=None):
     _check(lib().psd_project_ex(n, _ptr(X), ld, _ptr(out), ld_out, _prec(precision), _ptr(d_info),
                                 _ptr(workspace), ws_bytes, _stream(stream)), "psd_project_ex")
+
+
+def psd_project_deflate(n, X, ld, out, ld_out, precision="fp16", kmax=8, d_info=None, d_kused=None,
+                        stream=None):
+    _check(lib().psd_project_deflate(n, _ptr(X), ld, _ptr(out), ld_out, _prec(precision), kmax, _ptr(d_info),
+                                     _ptr(d_kused), _stream(stream)), "psd_project_deflate")
 
 
 def psd_workspace_size(n, precision="fp16"):

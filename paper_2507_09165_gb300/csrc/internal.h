@@ -192,11 +192,14 @@ struct LanczosBufs {
   double* dots2;         // nvec_ctas x 32
   double* norms;         // npart (>= nvec_ctas)
   double* tile_fro;      // ntiles
+  double* zsave = nullptr;  // if set: X q_j of Lanczos step j kept at zsave + j npad (kMaxSteps x npad)
 };
 size_t lanczos_bytes(int64_t n);
 void lanczos_carve(LanczosBufs& b, int64_t n, uint8_t* base);
 cudaError_t enqueue_norm_bound(const LanczosBufs& b, const DevArgs* args, DevState* st,
                                cudaStream_t stream);
+// Frees the cached plans of psd_project_deflate (device synchronised by the caller).
+void release_deflate_plans();
 // X_0 = X / lam~ as `dtype` (DT_F16, DT_BF16, or DT_TF32X3 with M = hi, M_lo = lo).
 cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n,
                                void* M, void* M_lo, int64_t ldm, cudaStream_t stream);

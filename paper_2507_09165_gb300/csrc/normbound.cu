@@ -827,6 +827,7 @@ size_t lanczos_bytes(int64_t n) {
 }
 
 void lanczos_carve(LanczosBufs& L, int64_t n, uint8_t* base) {
+  L.zsave = nullptr;
   L.n = n;
   L.npad = (n + 255) / 256 * 256;
   L.nb = static_cast<int>((n + kSymvTile - 1) / kSymvTile);
@@ -869,7 +870,8 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
     } else {
       symv_upper_kernel<false><<<L.ntiles, 256, 0, s>>>(args, n, L.vh, L.vl, L.P1, L.P2, ps, L.tile_fro, st, 1);
     }
-    reduce_split_kernel<<<rb, rt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.u, L.vh, L.vl, st, 1);
+    double* u = L.zsave ? L.zsave + j * L.npad : L.u;
+    reduce_split_kernel<<<rb, rt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, u, L.vh, L.vl, st, 1);
     symv_upper_kernel<false><<<L.ntiles, 256, 0, s>>>(args, n, L.vh, L.vl, L.P1, L.P2, ps, L.tile_fro, st, 1);
     reduce_dots_kernel<<<rb, rt, 0, s>>>(n, L.nb, L.P1, L.P2, ps, L.w, L.Qv, L.npad, j, L.dots, st);
     orth_kernel<1><<<vb, vt, 0, s>>>(n, L.w, L.Qv, L.npad, j, L.dots, rb, L.dots2, st);
@@ -886,6 +888,7 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
   bound_final_kernel<<<1, 32, 0, s>>>(n, L.norms, rb, st, args);
   return cudaGetLastError();
 }
+
 
 cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* st, int64_t n, void* M,
                                void* M_lo, int64_t ldm, cudaStream_t s) {

@@ -433,6 +433,7 @@ psd_status_t psd_release_workspaces(void) {
     for (auto& t : kv.second.tiles) cudaFree(t.second);
   }
   g_prod.clear();
+  release_deflate_plans();
   return PSD_OK;
 }
 

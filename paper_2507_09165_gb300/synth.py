@@ -119,6 +119,29 @@ def spectral_matrix(kind, n, seed):
     return to_f32(X), Q, lam
 
 
+def spectral_matrix_device(kind, n, seed, device):
+    """X = Q diag(l) Q^T built on a CUDA device (for orders where the CPU QR is
+    slow): Q Haar from the QR of a Gaussian drawn by torch's generator seeded
+    with `seed` on `device` (diag R > 0), l = spectrum(kind, n, seed + 1).
+
+    Returns (X32, Q, lam) as device tensors: the FP32 input (exactly
+    symmetric) and the FP64 factors.  The bits differ from spectral_matrix's
+    (another random stream); the spectrum is the same.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    G = torch.randn(n, n, generator=g, dtype=torch.float64, device=device)
+    Q, R = torch.linalg.qr(G)
+    del G
+    Q *= torch.sign(torch.diagonal(R))[None, :]
+    del R
+    lam = torch.from_numpy(spectrum(kind, n, seed + 1)).to(device)
+    X = (Q * lam[None, :]) @ Q.T
+    X = 0.5 * (X + X.T)
+    return X.float().contiguous(), Q, lam
+
+
 def block_sizes(count=512, seed=7, lo=16, hi=1024):
     """Block orders n_i = round(exp(U[ln lo, ln hi])) for a block-diagonal cone."""
     u = _rng(seed).uniform(math.log(lo), math.log(hi), size=count)
