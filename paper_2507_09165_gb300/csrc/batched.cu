@@ -135,7 +135,8 @@ psd_status_t build_bplan(BatchPlan* p) {
   const size_t b_vec32 = rup(sizeof(float) * 2 * voff, 256);
   const size_t b_part = rup(sizeof(float2) * poff, 256);
   const size_t b_fro = rup(sizeof(double) * std::max<int64_t>(toff, 1), 256);
-  const size_t total = 1024 + b_slots + b_vec64 + b_vec32 + b_part + b_fro;
+  const size_t b_xt = sizeof(float) * kSymvTile * kSymvTile * symv.size();
+  const size_t total = 1024 + b_slots + b_vec64 + b_vec32 + b_part + b_fro + b_xt;
   if (cudaMalloc(&p->ws, total) != cudaSuccess) {
     cudaGetLastError();
     p->ws = nullptr;
@@ -152,6 +153,8 @@ psd_status_t build_bplan(BatchPlan* p) {
   p->L.part = reinterpret_cast<float2*>(q);
   q += b_part;
   p->L.tile_fro = reinterpret_cast<double*>(q);
+  q += b_fro;
+  p->L.xt = reinterpret_cast<float*>(q);
   // small records: BlockRec | BatchBlock | DevState | status | tiles | symv items | cast items
   const size_t o_bb = rup(sizeof(BlockRec) * count, 256);
   const size_t o_st = o_bb + rup(sizeof(BatchBlock) * count, 256);

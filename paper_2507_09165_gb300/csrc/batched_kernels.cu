@@ -78,8 +78,7 @@ struct BView {
   float2* P1;  // nb x n
   float2* P2;  // nb x n
 };
-__device__ __forceinline__ BView view(const BatchLanczos& L, int b) {
-  const BatchBlock& bb = L.blk[b];
+__device__ __forceinline__ BView view_of(const BatchLanczos& L, const BatchBlock& bb) {
   BView v;
   v.n = bb.n;
   v.nb = (bb.n + kSymvTile - 1) / kSymvTile;
@@ -94,12 +93,13 @@ __device__ __forceinline__ BView view(const BatchLanczos& L, int b) {
   v.P2 = v.P1 + static_cast<int64_t>(v.nb) * bb.n;
   return v;
 }
+__device__ __forceinline__ BView view(const BatchLanczos& L, int b) { return view_of(L, L.blk[b]); }
 
 // ------------------------------------------------------------ grouped mat-vec
 // One 128 x 128 upper tile of block `blk`: same arithmetic as the single-matrix
 // kernel (see normbound.cu), partial sums into the block's P1 / P2.
 template <bool STATS, bool DIAG>
-__device__ __forceinline__ void bsymv_tile(const float* __restrict__ X, int64_t ld, int n, int bi, int bj,
+__device__ __forceinline__ void bsymv_tile(const float* __restrict__ T, int n, int bi, int bj,
                                            const float* __restrict__ vh, float2* __restrict__ P1,
                                            float2* __restrict__ P2, double* __restrict__ tile_fro,
                                            int tile_slot, unsigned* maxdiag, float2 (*red)[kSymvTile],
@@ -109,26 +109,20 @@ __device__ __forceinline__ void bsymv_tile(const float* __restrict__ X, int64_t 
   const int tr = lane & 15, tcol = 2 * warp + (lane >> 4);
   const int ib = i0 + 8 * tr;
   const int jb = j0 + 8 * tcol;
-  const bool full = (ib + 7 < n) && (jb + 7 < n);
-  const bool vec = full && ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   float vi[8], vj[8], x[8][8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     vi[k] = (ib + k < n) ? __ldg(vh + ib + k) : 0.f;
     vj[k] = (jb + k < n) ? __ldg(vh + jb + k) : 0.f;
   }
+  // the packed tile: column c of the tile at T + 128 c, zeros outside n x n
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const float* col = X + static_cast<int64_t>(jb + c) * ld + ib;
-    if (vec) {
-      const float4 a4 = __ldg(reinterpret_cast<const float4*>(col));
-      const float4 b4 = __ldg(reinterpret_cast<const float4*>(col + 4));
-      x[c][0] = a4.x; x[c][1] = a4.y; x[c][2] = a4.z; x[c][3] = a4.w;
-      x[c][4] = b4.x; x[c][5] = b4.y; x[c][6] = b4.z; x[c][7] = b4.w;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) x[c][k] = (jb + c < n && ib + k < n) ? __ldg(col + k) : 0.f;
-    }
+    const float* col = T + (8 * tcol + c) * kSymvTile + 8 * tr;
+    const float4 a4 = __ldg(reinterpret_cast<const float4*>(col));
+    const float4 b4 = __ldg(reinterpret_cast<const float4*>(col + 4));
+    x[c][0] = a4.x; x[c][1] = a4.y; x[c][2] = a4.z; x[c][3] = a4.w;
+    x[c][4] = b4.x; x[c][5] = b4.y; x[c][6] = b4.z; x[c][7] = b4.w;
   }
   float rsum[8], csum[8];
   float fro = 0.f;
@@ -202,6 +196,28 @@ __device__ __forceinline__ void bsymv_tile(const float* __restrict__ X, int64_t 
   }
 }
 
+// Copies the 128 x 128 upper tiles of every block out of the caller's
+// matrices into L.xt, one contiguous 64 KB tile per mat-vec work item (column
+// c of the tile at 128 c; zeros outside the block and below the diagonal of a
+// diagonal tile, which the mat-vec masks anyway).  The caller's leading
+// dimensions are arbitrary, so this pass reads them with coalesced scalar
+// loads once per projection, and the 41 mat-vecs that follow read aligned,
+// contiguous tiles with 16-byte loads.
+__global__ void __launch_bounds__(256) bpack_kernel(BatchLanczos L, const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const BatchBlock bb = L.blk[it.x];
+  const int i0 = it.y * kSymvTile, j0 = it.z * kSymvTile;
+  const bool diag = it.y == it.z;
+  float* T = L.xt + static_cast<int64_t>(blockIdx.x) * kSymvTile * kSymvTile;
+  const int r = threadIdx.x & (kSymvTile - 1);
+  for (int c = threadIdx.x >> 7; c < kSymvTile; c += 2) {
+    const int i = i0 + r, j = j0 + c;
+    float x = 0.f;
+    if (i < bb.n && j < bb.n && (!diag || r <= c)) x = __ldg(bb.X + static_cast<int64_t>(j) * bb.ld + i);
+    T[c * kSymvTile + r] = x;
+  }
+}
+
 // work item: (block, bi, bj, tile slot of the block's tile_fro entries)
 template <bool STATS>
 __global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int4* __restrict__ items) {
@@ -209,14 +225,18 @@ __global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int
   __shared__ double fro_sh[8];
   const int4 it = items[blockIdx.x];
   const int b = it.x;
-  if (L.st[b].done && !STATS && L.skip_done) return;
-  const BatchBlock& bb = L.blk[b];
-  const BView v = view(L, b);
+  // the block record and the done flag are independent loads: issue both
+  // before the branch
+  const BatchBlock bb = L.blk[b];
+  const int done = L.st[b].done;
+  const BView v = view_of(L, bb);
+  const float* T = L.xt + static_cast<int64_t>(blockIdx.x) * kSymvTile * kSymvTile;
+  if (done && !STATS && L.skip_done) return;
   if (it.y == it.z)
-    bsymv_tile<STATS, true>(bb.X, bb.ld, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
+    bsymv_tile<STATS, true>(T, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
                             &L.st[b].maxdiag_bits, red, fro_sh);
   else
-    bsymv_tile<STATS, false>(bb.X, bb.ld, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
+    bsymv_tile<STATS, false>(T, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
                              &L.st[b].maxdiag_bits, red, fro_sh);
 }
 
@@ -299,39 +319,56 @@ __global__ void __launch_bounds__(kBT) breduce_kernel(BatchLanczos L, int mode) 
   }
 }
 
-// Sum over the CTA of up to 32 values per thread (v[k] for k <= j), fixed
-// order: recursive halving inside each warp (lane l ends with value l), then
-// the 8 warp sums of value k added by thread k.  Result in h[0..j].
-__device__ __forceinline__ void cta_multi_sum(double (&v)[kMaxSteps + 1], int j, double (*sh)[32], double* h) {
+// Lanczos step j after w = X u: alpha_j, two classical Gram-Schmidt passes
+// (all j + 1 projections of a pass reduced together), beta_j, breakdown test,
+// q_{j+1} = w / beta_j and its split.  GB300's FP64 pipe is narrow (a warp's
+// FP64 instruction occupies it for 16 cycles), so the step spends FP64 work
+// only where it is needed: warps that own no element add zeros without
+// arithmetic, and the cross-lane sum of the j + 1 partial dots halves only
+// over V = 2^ceil(log2(j + 1)) values (then a plain butterfly), not all 32.
+// Every reduction has a fixed order that depends on j alone, so a block's
+// result does not depend on the rest of the batch.
+
+// Sum over the CTA (kBT threads) of v[k], k <= j, into out[k]: recursive
+// halving over V values inside each warp (lane l ends with value l mod V,
+// summed over its V-lane group), a butterfly over the 32 / V groups, then the
+// warp sums of value k added in order by thread k.
+__device__ __forceinline__ void cta_multi_sum(const double (&v)[kMaxSteps + 1], int j, bool warp_active,
+                                              double (*sh)[32], double* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double t[32];
+  if (warp_active) {
+    int V = 1;
+    while (V < j + 1) V <<= 1;  // uniform across the CTA
+    double t[32];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) t[k] = (k <= j && k <= kMaxSteps) ? v[k <= kMaxSteps ? k : 0] : 0.0;
+    for (int k = 0; k < 32; ++k) t[k] = (k <= j && k <= kMaxSteps) ? v[k <= kMaxSteps ? k : 0] : 0.0;
 #pragma unroll
-  for (int half = 16, m = 16; half >= 1; half >>= 1, m >>= 1) {
-    const bool upper = (lane & m) != 0;
+    for (int half = 16, m = 16; half >= 1; half >>= 1, m >>= 1) {
+      if (half >= V) continue;  // values >= V are zero: skip the exchange
+      const bool upper = (lane & m) != 0;
 #pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const double send = upper ? t[i] : t[i + half];
-      const double keep = upper ? t[i + half] : t[i];
-      t[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      for (int i = 0; i < half; ++i) {
+        const double send = upper ? t[i] : t[i + half];
+        const double keep = upper ? t[i + half] : t[i];
+        t[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      }
     }
+    // lanes l and l ^ (V, 2V, ...) hold the same value index: butterfly over them
+    for (int m = V; m < 32; m <<= 1) t[0] += __shfl_xor_sync(0xffffffffu, t[0], m);
+    sh[w][lane] = t[0];
+  } else {
+    sh[w][lane] = 0.0;
   }
-  __syncthreads();
-  sh[w][lane] = t[0];
   __syncthreads();
   if (threadIdx.x <= j) {
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < kBT / 32; ++q) s += sh[q][threadIdx.x];
-    h[threadIdx.x] = s;
+    out[threadIdx.x] = s;
   }
   __syncthreads();
 }
 
-// Lanczos step j after w = X u: alpha_j, two classical Gram-Schmidt passes
-// (all j + 1 projections of a pass reduced together), beta_j, breakdown test,
-// q_{j+1} = w / beta_j and its split.
 __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
   __shared__ double sh[kBT / 32][32];
   __shared__ double h[32];
@@ -340,6 +377,7 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
   DevState* st = &L.st[b];
   if (st->done) return;
   const BView v = view(L, b);
+  const bool any = (threadIdx.x & ~31) < v.n;  // the warp owns an element
   double w[kEPT];
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
@@ -359,7 +397,7 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
           if (kk <= j) d[kk] += v.Q[static_cast<int64_t>(kk) * v.n + e] * w[k];
       }
     }
-    cta_multi_sum(d, j, sh, h);
+    cta_multi_sum(d, j, any, sh, h);
     if (pass == 0 && threadIdx.x == 0) st->alpha[j] = h[j];
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) {
@@ -367,10 +405,13 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
       if (e < v.n)
         for (int kk = 0; kk <= j; ++kk) w[k] -= h[kk] * v.Q[static_cast<int64_t>(kk) * v.n + e];
     }
+    __syncthreads();  // h is rewritten by the next pass
   }
   double s = 0.0;
+  if (any) {
 #pragma unroll
-  for (int k = 0; k < kEPT; ++k) s += w[k] * w[k];
+    for (int k = 0; k < kEPT; ++k) s += w[k] * w[k];
+  }
   const double beta = sqrt(cta_sum(s, shs));
   const double fro = st->fro;
   const bool brk = !(beta > kBreakdown * fro * fro);
@@ -717,6 +758,7 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
                                      cudaStream_t s) {
   BatchLanczos Lk = L;
   Lk.skip_done = 0;
+  bpack_kernel<<<nsymv, 256, 0, s>>>(Lk, symv_items);
   binit_kernel<<<count, kBT, 0, s>>>(Lk);
   for (int j = 0; j < kMaxSteps; ++j) {
     Lk.skip_done = j == 0 ? 0 : 1;

@@ -156,6 +156,7 @@ struct BatchLanczos {
   float* vec32;           // per block: 2 x n  (hi / lo of the mat-vec input)
   float2* part;           // per block: 2 x nb x n  (row / column partial sums)
   double* tile_fro;       // per mat-vec tile
+  float* xt;              // per mat-vec tile: the block's 128 x 128 tile, packed (64 KB)
   int skip_done;
 };
 
