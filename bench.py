@@ -320,6 +320,7 @@ def batched_leg(dev, prec="bf16", reps=5):
     for _ in range(3):
         b.psd_project_batched(len(sizes), descs, prec, s)
     torch.cuda.synchronize(dev)
+    chosen, cand_ms = b.psd_batched_last_tuning()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ts = []
     for _ in range(reps):
@@ -333,6 +334,9 @@ def batched_leg(dev, prec="bf16", reps=5):
     return {"workload": "512 Wigner blocks, orders log-uniform in [16, 1024] (seed 7; sum n = %d, max %d)"
                         % (sum(sizes), max(sizes)),
             "precision": prec, "ms": ms, "ms_all": ts, "blocks_per_s": len(sizes) / (ms * 1e-3),
+            "schedule": {"chosen": chosen, "product_ms_per_candidate": cand_ms,
+                         "what": "autotuned order of the grouped products' tiles (6 result-invariant candidates, "
+                                 "one first-stage product timed per candidate at plan build)"},
             "tflops_22n3": flops / (ms * 1e-3) / 1e12}
 
 

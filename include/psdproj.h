@@ -282,6 +282,29 @@ psd_status_t psd_server_stats(psd_server_t *server, psd_server_stats_t *stats);
  * frees the server's memory.  Tickets not yet retired are lost. */
 psd_status_t psd_server_destroy(psd_server_t *server);
 
+/* ---- Schedule autotuning of psd_project_batched ------------------------- */
+/* No counterpart in the paper: an addition of this library.  The tiles of each
+ * grouped product can be dealt to the persistent CTAs in several orders (6
+ * candidates: blocks largest first or all tiles by estimated cost in
+ * boustrophedon rounds, times a raster group of 4, 8 or 16 for a block's
+ * tiles).  No candidate changes any tile's arithmetic: results are
+ * bit-identical under every schedule.  When a plan is built (first call per
+ * device, stream, precision and block orders) the library times one product
+ * of the chain's first stage under each candidate (median of 3 after a
+ * warm-up, on a private stream, synchronising the device) and keeps the
+ * fastest; the choice is cached per (precision, block orders) for the life
+ * of the process, so later plans with the same key are not re-timed. */
+
+/* Forces schedule `index` (0..5) for plans built after the call; -1 restores
+ * autotuning (the default).  Returns the previous setting.  Host-only. */
+int32_t psd_batched_force_schedule(int32_t index);
+
+/* Schedule of the most recently built batched plan: *chosen (0..5),
+ * *candidates (6) and, if ms is not NULL, the measured ms per candidate
+ * (ms[6]; zeros when the schedule was forced or taken from the cache).
+ * PSD_ERR_INVALID_ARG before any plan was built.  Host-only. */
+psd_status_t psd_batched_last_tuning(int32_t *chosen, int32_t *candidates, float *ms);
+
 /* ---- Deflation of dominant eigenpairs ------------------------------------ */
 /* Projection with the dominant eigenpairs taken out first: the remedy Sec. 6
  * (Limitations) names for spectra where a few eigenvalues of large modulus

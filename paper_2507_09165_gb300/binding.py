@@ -83,6 +83,8 @@ _SIGS = {
     "psd_server_stats": ([_VP, ctypes.POINTER(psd_server_stats_t)], _I32),
     "psd_server_destroy": ([_VP], _I32),
     "psd_project_deflate": ([_I64, _VP, _I64, _VP, _I64, _I32, _I32, _VP, _VP, _VP], _I32),
+    "psd_batched_force_schedule": ([_I32], _I32),
+    "psd_batched_last_tuning": ([ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)], _I32),
 }
 
 
@@ -149,6 +151,19 @@ def psd_project_deflate(n, X, ld, out, ld_out, precision="fp16", kmax=8, d_info=
                         stream=None):
     _check(lib().psd_project_deflate(n, _ptr(X), ld, _ptr(out), ld_out, _prec(precision), kmax, _ptr(d_info),
                                      _ptr(d_kused), _stream(stream)), "psd_project_deflate")
+
+
+def psd_batched_force_schedule(index):
+    """Force grouped-product schedule `index` (0..5) for batched plans built next; -1: autotune."""
+    return int(lib().psd_batched_force_schedule(int(index)))
+
+
+def psd_batched_last_tuning():
+    """(chosen, [ms per candidate]) of the most recently built batched plan."""
+    chosen, ncand = _I32(), _I32()
+    ms = (ctypes.c_float * 16)()
+    _check(lib().psd_batched_last_tuning(ctypes.byref(chosen), ctypes.byref(ncand), ms), "psd_batched_last_tuning")
+    return int(chosen.value), [float(ms[i]) for i in range(ncand.value)]
 
 
 def psd_workspace_size(n, precision="fp16"):

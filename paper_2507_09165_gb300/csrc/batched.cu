@@ -79,6 +79,52 @@ void free_bplan(BatchPlan* p) {
   delete p;
 }
 
+// Schedules of the grouped products: the order in which their tiles are dealt
+// to the persistent CTAs (tile t goes to CTA t mod grid).  None changes a
+// tile's arithmetic, so every schedule gives bit-identical results; they
+// differ in load balance and L2 reuse, which the autotuner measures.
+//   order 0: blocks largest first, each block's tiles in its grouped raster;
+//   order 1: all tiles by estimated cost (K-steps x width, plus a fixed
+//            epilogue share), dealt in boustrophedon rounds of `grid` tiles.
+// Index = 3 order + g, raster group kTileGroups[g].
+constexpr int kTileGroups[3] = {4, 8, 16};
+constexpr int kNumSchedules = 6;
+
+std::vector<int4> schedule_tiles(const std::vector<int>& sizes, int cand, int grid) {
+  const int count = static_cast<int>(sizes.size());
+  const int order = cand / 3, group = kTileGroups[cand % 3];
+  std::vector<int> blocks(count);
+  for (int b = 0; b < count; ++b) blocks[b] = b;
+  std::stable_sort(blocks.begin(), blocks.end(), [&](int x, int y) { return sizes[x] > sizes[y]; });
+  std::vector<int4> tiles;
+  for (int b : blocks) {
+    std::vector<int4> tl = make_tile_list(sizes[b], b, group);
+    tiles.insert(tiles.end(), tl.begin(), tl.end());
+  }
+  if (order == 0 || grid <= 1) return tiles;
+  auto cost = [&](const int4& t) {
+    const int64_t k = (sizes[t.z] + 63) / 64;
+    return (k + 4) * static_cast<int64_t>(t.w);
+  };
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const int4& x, const int4& y) { return cost(x) > cost(y); });
+  std::vector<int4> out(tiles.size());
+  const int64_t T = static_cast<int64_t>(tiles.size());
+  for (int64_t r0 = 0, k = 0; r0 < T; r0 += grid, ++k) {
+    const int64_t len = std::min<int64_t>(grid, T - r0);
+    for (int64_t c = 0; c < len; ++c) out[r0 + c] = tiles[r0 + ((k & 1) ? len - 1 - c : c)];
+  }
+  return out;
+}
+
+struct TuneReport {
+  int chosen = -1;
+  int ncand = 0;
+  float ms[kNumSchedules] = {};
+};
+int g_force_schedule = -1;                                  // for plans built next; -1: autotune
+std::map<std::pair<int, std::vector<int>>, int> g_tuned;   // (precision, block orders) -> schedule
+TuneReport g_last_tune;
+
 psd_status_t build_bplan(BatchPlan* p) {
   if (!get_schedule(p->prec, p->sched)) return PSD_ERR_INVALID_ARG;
   const int count = p->count;
@@ -115,15 +161,8 @@ psd_status_t build_bplan(BatchPlan* p) {
     toff += bb[b].ntiles;
   }
   p->R = off;
-  // product tiles of all blocks, largest blocks first (their tiles carry the most K-steps)
-  std::vector<int> order(count);
-  for (int b = 0; b < count; ++b) order[b] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p->sizes[x] > p->sizes[y]; });
-  std::vector<int4> tiles;
-  for (int b : order) {
-    std::vector<int4> tl = make_tile_list(p->sizes[b], b);
-    tiles.insert(tiles.end(), tl.begin(), tl.end());
-  }
+  // product tiles of all blocks in the default schedule (the autotuner may reorder them)
+  std::vector<int4> tiles = schedule_tiles(p->sizes, 0, num_sms());
   p->ntiles = static_cast<int>(tiles.size());
   p->nsymv = static_cast<int>(symv.size());
   p->ncast = static_cast<int>(cast.size());
@@ -267,6 +306,69 @@ cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
   return run_chain(p->prec, p->sched, p->nslots, dt16_for(p->prec), ops);
 }
 
+// Picks the plan's product schedule: the forced one, the one tuned earlier for
+// the same (precision, block orders), or the fastest of all candidates on one
+// product of the chain's first stage (median of 3 after a warm-up, on a
+// private stream; the slots hold zeros, which leaves the timing unchanged).
+psd_status_t tune_bplan(BatchPlan* p) {
+  const int grid = std::max(1, std::min(num_sms(), p->ntiles));
+  const auto key = std::make_pair(static_cast<int>(p->prec), p->sizes);
+  TuneReport rep;
+  rep.ncand = kNumSchedules;
+  int chosen = 0;
+  if (g_force_schedule >= 0 && g_force_schedule < kNumSchedules) {
+    chosen = g_force_schedule;
+  } else if (g_tuned.count(key)) {
+    chosen = g_tuned[key];
+  } else {
+    cudaStream_t ts;
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) return PSD_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const StageKinds k = stage_kinds(p->prec, 0, p->sched.T);
+    Mat A, Y;
+    A.kind = k.x;
+    A.slot = 0;
+    A.dt16 = dt16_for(p->prec);
+    Y.kind = k.y;
+    Y.slot = kind_slots(k.x);
+    Y.dt16 = A.dt16;
+    float best = 0.f;
+    bool ok = true;
+    for (int c = 0; c < kNumSchedules && ok; ++c) {
+      const std::vector<int4> t = schedule_tiles(p->sizes, c, grid);
+      ok = cudaMemcpyAsync(p->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice, ts) ==
+           cudaSuccess;
+      float ms[3] = {};
+      for (int r = -1; r < 3 && ok; ++r) {
+        cudaEventRecord(e0, ts);
+        ok = bgemm(p, EPI_COPY, A, A, &Y, nullptr, 0.f, 0.f, 0.f, 1.f, false, ts) == cudaSuccess;
+        cudaEventRecord(e1, ts);
+        ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+        if (ok && r >= 0) cudaEventElapsedTime(&ms[r], e0, e1);
+      }
+      std::sort(ms, ms + 3);
+      rep.ms[c] = ms[1];
+      if (ok && (c == 0 || ms[1] < best)) {
+        best = ms[1];
+        chosen = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(ts);
+    if (!ok) return PSD_ERR_CUDA;
+    g_tuned[key] = chosen;
+  }
+  const std::vector<int4> t = schedule_tiles(p->sizes, chosen, grid);
+  if (cudaMemcpy(p->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PSD_ERR_CUDA;
+  rep.chosen = chosen;
+  g_last_tune = rep;
+  return PSD_OK;
+}
+
 void ensure_bgraph(BatchPlan* p) {
   if (p->graph_tried) return;
   p->graph_tried = true;
@@ -289,9 +391,33 @@ void ensure_bgraph(BatchPlan* p) {
 }
 
 }  // namespace
+
+void release_batched_plans() {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  for (auto& kv : g_bplans) free_bplan(kv.second);
+  g_bplans.clear();
+}
+
 }  // namespace psd
 
 using namespace psd;
+
+extern "C" int32_t psd_batched_force_schedule(int32_t index) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  const int prev = g_force_schedule;
+  g_force_schedule = (index >= 0 && index < kNumSchedules) ? index : -1;
+  return prev;
+}
+
+extern "C" psd_status_t psd_batched_last_tuning(int32_t* chosen, int32_t* candidates, float* ms) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  if (g_last_tune.chosen < 0) return PSD_ERR_INVALID_ARG;
+  if (chosen) *chosen = g_last_tune.chosen;
+  if (candidates) *candidates = g_last_tune.ncand;
+  if (ms)
+    for (int c = 0; c < g_last_tune.ncand; ++c) ms[c] = g_last_tune.ms[c];
+  return PSD_OK;
+}
 
 extern "C" psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t* d_descs,
                                             psd_precision_t precision, psd_stream_t stream) {
@@ -337,6 +463,7 @@ extern "C" psd_status_t psd_project_batched(int32_t count, const psd_block_desc_
     p->count = count;
     p->sizes = sizes;
     psd_status_t st = build_bplan(p);
+    if (st == PSD_OK) st = tune_bplan(p);
     if (st != PSD_OK) {
       free_bplan(p);
       return st;

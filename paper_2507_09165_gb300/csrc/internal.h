@@ -108,7 +108,9 @@ struct GemmParams {
 // Upper-triangle tiles of one order-n matrix: 256 x 256 blocks (I <= J) split
 // into two 128-row tiles; the lower-right tile of a diagonal block starts at
 // its diagonal (128 columns); tile widths are trimmed at n (multiples of 16).
-std::vector<int4> make_tile_list(int64_t n, int block = 0);
+std::vector<int4> make_tile_list(int64_t n, int block = 0, int group = 8);
+// Frees the cached plans of psd_project_batched (device synchronised by the caller).
+void release_batched_plans();
 
 // Coefficients of the run-time filter (Tables 1 and 2) and the per-stage
 // divisors s_t of Sec. 3.4 for a precision (psdproj.cu).

@@ -434,6 +434,7 @@ psd_status_t psd_release_workspaces(void) {
   }
   g_prod.clear();
   release_deflate_plans();
+  release_batched_plans();
   return PSD_OK;
 }
 

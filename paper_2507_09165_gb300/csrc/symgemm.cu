@@ -663,15 +663,16 @@ bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t col
 }
 
 // Upper-triangle tiles of 256 x 256 blocks, each split into two 128-row
-// tiles, in a grouped raster: block rows are taken in groups of 8, and inside
+// tiles, in a grouped raster: block rows are taken in groups of `group` (8),
+// and inside
 // a group the columns advance first so that the tiles resident at one time
 // share their operand panels in L2.  The lower tile of a diagonal block only
 // needs its right half (columns >= its first row), and every tile is trimmed
 // to the columns below n (rounded up to 16, the MMA's N granularity).
-std::vector<int4> make_tile_list(int64_t n, int block) {
+std::vector<int4> make_tile_list(int64_t n, int block, int group) {
   std::vector<int4> tiles;
   const int nb = static_cast<int>((n + kBN - 1) / kBN);
-  const int G = 8;
+  const int G = group > 0 ? group : 8;
   auto width = [&](int n0, int w) { return std::min(w, static_cast<int>((n - n0 + 15) / 16 * 16)); };
   for (int g0 = 0; g0 < nb; g0 += G) {
     for (int J = g0; J < nb; ++J) {

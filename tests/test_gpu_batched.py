@@ -128,3 +128,39 @@ def test_batched_rejects_bad_blocks():
         b.psd_project_batched(1, b.block_descs([(8, Y, 7, Y, 8, None)]), "bf16")
     with pytest.raises(b.PsdError):
         b.psd_project_batched(1, b.block_descs([(8, Y, 8, Y, 8, None)]), "fp8_early")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "mixed"])
+def test_every_schedule_gives_the_same_bits_and_autotune_picks_one(prec):
+    # The autotuner only reorders which persistent CTA takes which tile of a
+    # grouped product: every candidate schedule must give bit-identical
+    # outputs and reports.  A batch with a signature of its own, so the
+    # autotuned run below times all candidates instead of reusing a choice.
+    sizes = [900, 17, 640, 256, 1000, 3, 450, 128, 777, 64, 300 + (prec == "mixed")]
+    mats = [synth.wigner(n, 4400 + i) for i, n in enumerate(sizes)]
+    ref = None
+    try:
+        for idx in range(6):
+            b.psd_batched_force_schedule(idx)
+            b.psd_release_workspaces()
+            outs, infos = Batch(mats).run(prec)
+            chosen, _ = b.psd_batched_last_tuning()
+            assert chosen == idx
+            assert all(i["status"] == 0 for i in infos)
+            if ref is None:
+                ref = (outs, infos)
+            else:
+                for o, r in zip(outs, ref[0]):
+                    assert np.array_equal(o, r), idx
+                for i, r in zip(infos, ref[1]):
+                    assert i == r, idx
+        b.psd_batched_force_schedule(-1)
+        b.psd_release_workspaces()
+        outs, _ = Batch(mats).run(prec)
+        chosen, ms = b.psd_batched_last_tuning()
+        assert 0 <= chosen < 6 and len(ms) == 6
+        assert all(t > 0 for t in ms) and ms[chosen] == min(ms)
+        for o, r in zip(outs, ref[0]):
+            assert np.array_equal(o, r)
+    finally:
+        b.psd_batched_force_schedule(-1)
