@@ -634,7 +634,7 @@ def run_ours(args):
             "serving": serving,
             "bands": bands,
             "deflate": deflate,
-            "info": {k: info[k] for k in ("lambda_bound", "lanczos_steps", "overshoot_max")},
+            "info": {k: info[k] for k in ("lambda_bound", "lanczos_steps", "overshoot_max", "compl_resid")},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -91,6 +91,11 @@ typedef struct {
   double fro_X;          /* ||X||_F (FP64) */
   double max_diag;       /* max_i |X_ii| */
   double overshoot_max;  /* max_ij |X_T(i,j)| of the last stage */
+  double compl_resid;    /* <out, X - out> / ||X||_F^2: 0 for the exact projection Pi(X)
+                            (Pi(X) and X - Pi(X) are orthogonal), so its size measures the
+                            distance from a projection.  Summed in the final product's
+                            epilogue (double-float per thread, FP64 per tile, fixed order).
+                            NaN where not computed: psd_norm_bound* and the request server */
 } psd_info_t;
 
 /* Project one matrix (Algorithm 2).  X: n x n upper triangle read, ld >= n.

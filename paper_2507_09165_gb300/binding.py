@@ -33,7 +33,8 @@ class psd_info_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
                 ("lambda_bound", ctypes.c_double), ("lanczos_sigma", ctypes.c_double),
                 ("lanczos_resid", ctypes.c_double), ("fro_X", ctypes.c_double),
-                ("max_diag", ctypes.c_double), ("overshoot_max", ctypes.c_double)]
+                ("max_diag", ctypes.c_double), ("overshoot_max", ctypes.c_double),
+                ("compl_resid", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

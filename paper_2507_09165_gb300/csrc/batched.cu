@@ -12,6 +12,7 @@
 // any batch.
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <vector>
 
@@ -43,6 +44,9 @@ struct BatchPlan {
   int nsymv = 0;
   int4* d_cast = nullptr;
   int ncast = 0;
+  double* d_cres = nullptr;  // 4 per tile position: shares of <out, X - out> (final product)
+  int* d_cidx = nullptr;     // per block, in its own tile order: positions in the tile list
+  int2* d_crange = nullptr;  // per block: (first entry of d_cidx, count)
   uint8_t* small = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
@@ -201,7 +205,10 @@ psd_status_t build_bplan(BatchPlan* p) {
   const size_t o_tiles = o_status + 256;
   const size_t o_symv = o_tiles + rup(sizeof(int4) * tiles.size(), 256);
   const size_t o_cast = o_symv + rup(sizeof(int4) * symv.size(), 256);
-  const size_t smallb = o_cast + rup(sizeof(int4) * cast.size(), 256);
+  const size_t o_cres = o_cast + rup(sizeof(int4) * cast.size(), 256);
+  const size_t o_cidx = o_cres + rup(sizeof(double) * 4 * std::max<size_t>(tiles.size(), 1), 256);
+  const size_t o_crange = o_cidx + rup(sizeof(int) * std::max<size_t>(tiles.size(), 1), 256);
+  const size_t smallb = o_crange + rup(sizeof(int2) * count, 256);
   if (cudaMalloc(&p->small, smallb) != cudaSuccess) {
     cudaGetLastError();
     p->small = nullptr;
@@ -215,6 +222,9 @@ psd_status_t build_bplan(BatchPlan* p) {
   p->d_tiles = reinterpret_cast<int4*>(p->small + o_tiles);
   p->d_symv = reinterpret_cast<int4*>(p->small + o_symv);
   p->d_cast = reinterpret_cast<int4*>(p->small + o_cast);
+  p->d_cres = reinterpret_cast<double*>(p->small + o_cres);
+  p->d_cidx = reinterpret_cast<int*>(p->small + o_cidx);
+  p->d_crange = reinterpret_cast<int2*>(p->small + o_crange);
   for (int b = 0; b < count; ++b) rec[b].st = p->d_st + b;
   bool ok = cudaMemcpy(p->d_rec, rec.data(), sizeof(BlockRec) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(p->d_bb, bb.data(), sizeof(BatchBlock) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -257,6 +267,7 @@ cudaError_t bgemm(BatchPlan* p, int epi, const Mat& A, const Mat& B, const Mat* 
     g.ep.ldy = p->ldm;
   }
   g.ep.in_scale = g.ep.y_scale = g.ep.out_scale = 1.f;
+  if (epi == EPI_FINAL) g.ep.cres = p->d_cres;
   const int grid = num_sms();
   const int64_t cols = p->ldm, rows = p->R;
   const GemmRoute route = gemm_route(A, B);
@@ -296,7 +307,9 @@ struct BatchOps {
                    float sc, bool track) {
     return bgemm(p, epi, A, B, out, Y, a, b, c, sc, track, s);
   }
-  cudaError_t finish() { return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, s); }
+  cudaError_t finish() {
+    return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, p->d_cres, p->d_cidx, p->d_crange, s);
+  }
 };
 
 cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
@@ -363,6 +376,19 @@ psd_status_t tune_bplan(BatchPlan* p) {
   }
   const std::vector<int4> t = schedule_tiles(p->sizes, chosen, grid);
   if (cudaMemcpy(p->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PSD_ERR_CUDA;
+  // each block's final-product shares, in the block's own tile order (schedule-independent sums)
+  std::map<std::tuple<int, int, int>, int> pos;
+  for (int i = 0; i < static_cast<int>(t.size()); ++i) pos[std::make_tuple(t[i].z, t[i].x, t[i].y)] = i;
+  std::vector<int> cidx;
+  std::vector<int2> crange(p->count);
+  for (int b = 0; b < p->count; ++b) {
+    crange[b].x = static_cast<int>(cidx.size());
+    for (const int4& c : make_tile_list(p->sizes[b], b, 8)) cidx.push_back(pos.at(std::make_tuple(b, c.x, c.y)));
+    crange[b].y = static_cast<int>(cidx.size()) - crange[b].x;
+  }
+  if (cudaMemcpy(p->d_cidx, cidx.data(), sizeof(int) * cidx.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_crange, crange.data(), sizeof(int2) * crange.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return PSD_ERR_CUDA;
   rep.chosen = chosen;
   g_last_tune = rep;

@@ -633,6 +633,7 @@ __global__ void __launch_bounds__(kBT) bbound_kernel(BatchLanczos L) {
     info->max_diag = md;
     info->lanczos_steps = st->m;
     info->status = st->status;
+    info->compl_resid = __longlong_as_double(0x7ff8000000000000ll);  // set by the last step
   }
 }
 
@@ -733,7 +734,13 @@ __global__ void __launch_bounds__(256) bcast_kernel(BatchCast c, const BatchBloc
 }
 
 // Status and overshoot of every block into its report.
-__global__ void bfinalize_kernel(const BatchBlock* __restrict__ blk, DevState* st, int count) {
+// Per block: status and overshoot, and the complementarity residual from the
+// shares of the block's final-product tiles, added in the block's own tile
+// order (cidx: positions of its tiles in the launch's tile list, range crange[b])
+// so that the sum does not depend on the schedule or the rest of the batch.
+__global__ void bfinalize_kernel(const BatchBlock* __restrict__ blk, DevState* st, int count,
+                                 const double* __restrict__ cres, const int* __restrict__ cidx,
+                                 const int2* __restrict__ crange) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count) return;
   const float amax = __uint_as_float(st[b].absmax_bits);
@@ -749,6 +756,12 @@ __global__ void bfinalize_kernel(const BatchBlock* __restrict__ blk, DevState* s
   if (info) {
     info->overshoot_max = static_cast<double>(amax);
     info->status = status;
+    double v = 0.0;
+    const int2 rg = crange[b];
+    for (int k = rg.x; k < rg.x + rg.y; ++k)
+      for (int w = 0; w < 4; ++w) v += cres[4 * static_cast<int64_t>(cidx[k]) + w];
+    const double f2 = st[b].fro * st[b].fro;
+    info->compl_resid = f2 > 0.0 ? v / f2 : 0.0;
   }
 }
 
@@ -793,8 +806,9 @@ cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* 
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, cudaStream_t s) {
-  bfinalize_kernel<<<(count + 127) / 128, 128, 0, s>>>(blk, st, count);
+cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, const double* cres,
+                                   const int* cidx, const int2* crange, cudaStream_t s) {
+  bfinalize_kernel<<<(count + 127) / 128, 128, 0, s>>>(blk, st, count, cres, cidx, crange);
   return cudaGetLastError();
 }
 

@@ -95,7 +95,36 @@ struct EpiParams {
   float in_scale, y_scale, out_scale;
   unsigned* absmax;      // if set: atomic max of |output| into this word instead
   int* status;           // device status word for timeouts
+  double* cres;         // EPI_FINAL, if set: tile t's epilogue warp w writes its share of
+                         // <out, X - out> to cres[4 t + w]
 };
+
+// Share of <out, X - out> (whole symmetric matrix) of upper-triangle element
+// (r, c) with output o and input x: weight 1 on the diagonal, 2 above it (the
+// element stands for (c, r) too).  Per-thread double-float sum: the rounded
+// product and its FMA error are added with TwoSum, so the cancellation of the
+// total (zero for an exact projection) is resolved far below FP32's rounding.
+struct ComplAcc {
+  float h = 0.f, l = 0.f;
+};
+__device__ __forceinline__ void compl_add(ComplAcc& a, float o, float x, float w) {
+  const float d = __fsub_rn(x, o);
+  const float p = __fmul_rn(o, d);
+  const float e = fmaf(o, d, -p);
+  const float pw = __fmul_rn(p, w), ew = __fmul_rn(e, w);  // w is 1 or 2: exact
+  const float s = __fadd_rn(a.h, pw);
+  const float z = __fsub_rn(s, a.h);
+  const float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, z)), __fsub_rn(pw, z));
+  a.h = s;
+  a.l = __fadd_rn(a.l, __fadd_rn(err, ew));
+}
+// Warp sum (fixed order) of the lanes' shares; valid in every lane.
+__device__ __forceinline__ double compl_warp_sum(const ComplAcc& a) {
+  double v = static_cast<double>(a.h) + static_cast<double>(a.l);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 struct GemmParams {
   int num_tiles;
@@ -172,7 +201,8 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
                                      cudaStream_t stream);
 cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* blk, const DevState* st,
                                const int4* items, int nitems, cudaStream_t stream);
-cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, cudaStream_t stream);
+cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, const double* cres,
+                                   const int* cidx, const int2* crange, cudaStream_t stream);
 bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t cols, int64_t rows, int64_t ld,
                       int box_rows);
 
@@ -210,7 +240,10 @@ cudaError_t enqueue_scale_cast(int dtype, const DevArgs* args, const DevState* s
 cudaError_t enqueue_set_args(DevArgs* d_args, const DevArgs& h, cudaStream_t stream, BlockRec* blk = nullptr);
 cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t stream);
 cudaError_t enqueue_state_reset(DevState* st, cudaStream_t stream);
-cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t stream);
+// Status, overshoot and (if cres is set) the complementarity residual from the
+// ncompl per-warp shares of the final product.
+cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t stream, const double* cres = nullptr,
+                             int ncompl = 0);
 
 // Status and overshoot of the last stage: a non-finite or overshooting X_T
 // (max |X_T(i,j)| > kOvershootLimit) turns an OK status into an error; the

@@ -663,6 +663,7 @@ __global__ void bound_final_kernel(int n, const double* norms, int nctas, DevSta
     info->max_diag = md;
     info->lanczos_steps = st->m;
     info->status = st->status;
+    info->compl_resid = __longlong_as_double(0x7ff8000000000000ll);  // set by a projection's last step
   }
 }
 
@@ -802,8 +803,23 @@ __global__ void set_args_kernel(DevArgs* d, DevArgs h, BlockRec* blk) {
 
 __global__ void set_block_kernel(BlockRec* dst, BlockRec v) { *dst = v; }
 
-// Status word and overshoot of the last stage into the report.
-__global__ void finalize_kernel(const DevArgs* args, DevState* st) { finalize_report(st, args->info); }
+// Status word and overshoot of the last stage into the report, and the
+// complementarity residual from the final product's per-warp shares (one warp,
+// lane-strided then a fixed shuffle tree).
+__global__ void finalize_kernel(const DevArgs* args, DevState* st, const double* cres, int ncompl) {
+  psd_info_t* info = args->info;
+  double v = 0.0;
+  if (cres)
+    for (int i = threadIdx.x; i < ncompl; i += 32) v += cres[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x != 0) return;
+  finalize_report(st, info);
+  if (info) {
+    const double f2 = st->fro * st->fro;
+    info->compl_resid = !cres ? __longlong_as_double(0x7ff8000000000000ll) : (f2 > 0.0 ? v / f2 : 0.0);
+  }
+}
 
 }  // namespace
 
@@ -915,8 +931,8 @@ cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t s) {
-  finalize_kernel<<<1, 1, 0, s>>>(args, st);
+cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t s, const double* cres, int ncompl) {
+  finalize_kernel<<<1, 32, 0, s>>>(args, st, cres, ncompl);
   return cudaGetLastError();
 }
 

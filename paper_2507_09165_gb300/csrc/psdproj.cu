@@ -127,6 +127,7 @@ struct Plan {
   BlockRec* d_block = nullptr;   // the one block of a single projection
   int4* d_tiles = nullptr;
   int ntiles = 0;
+  double* d_compl = nullptr;  // 4 per tile: shares of <out, X - out> from the final product
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
   int launches = 0;  // kernel launches of one projection (graph nodes + argument block)
@@ -175,7 +176,8 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   const size_t o_info = o_state + round_up(sizeof(DevState), 256);
   const size_t o_block = o_info + round_up(sizeof(psd_info_t), 256);
   const size_t o_tiles = o_block + round_up(sizeof(BlockRec), 256);
-  const size_t small = o_tiles + sizeof(int4) * std::max<size_t>(tiles.size(), 1);
+  const size_t o_compl = o_tiles + round_up(sizeof(int4) * std::max<size_t>(tiles.size(), 1), 256);
+  const size_t small = o_compl + sizeof(double) * 4 * std::max<size_t>(tiles.size(), 1);
   uint8_t* sm = nullptr;
   if (cudaMalloc(&sm, small) != cudaSuccess) {
     cudaGetLastError();
@@ -187,6 +189,7 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   p->d_info = reinterpret_cast<psd_info_t*>(sm + o_info);
   p->d_block = reinterpret_cast<BlockRec*>(sm + o_block);
   p->d_tiles = reinterpret_cast<int4*>(sm + o_tiles);
+  p->d_compl = reinterpret_cast<double*>(sm + o_compl);
   if (!tiles.empty() &&
       cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return PSD_ERR_CUDA;
@@ -232,6 +235,7 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
     g.ep.Y_lo = kind_is_pair(Y->kind) ? part_ptr(p, *Y, 1) : nullptr;
     g.ep.ldy = ldm;
   }
+  if (epi == EPI_FINAL) g.ep.cres = p->d_compl;
   g.ep.in_scale = 1.f / (A.scale * B.scale);
   g.ep.y_scale = Y ? 1.f / Y->scale : 1.f;
   g.ep.out_scale = out ? out->scale : 1.f;
@@ -272,7 +276,7 @@ struct PlanOps {
                    float sc, bool track) {
     return psd::gemm(p, epi, A, B, out, Y, a, b, c, sc, track ? &p->d_state->absmax_bits : nullptr, s);
   }
-  cudaError_t finish() { return enqueue_finalize(p->d_args, p->d_state, s); }
+  cudaError_t finish() { return enqueue_finalize(p->d_args, p->d_state, s, p->d_compl, 4 * p->ntiles); }
 };
 
 // Enqueue the whole projection (used for graph capture and for direct launch).

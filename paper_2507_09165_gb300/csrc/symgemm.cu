@@ -294,7 +294,7 @@ __device__ __forceinline__ void epilogue_chunk16(const GemmParams& p, const Bloc
 // reading only the upper triangle of the caller's X (column-major).
 __device__ __forceinline__ void epilogue_chunk_final(const BlockRec& br, int r0, int c0,
                                                      const uint32_t (&v)[32], uint8_t* wbuf,
-                                                     int lane, float lam) {
+                                                     int lane, float lam, ComplAcc* ca) {
   uint32_t* stg = reinterpret_cast<uint32_t*>(wbuf);
   const int n = br.n;
   const float* X = br.X;
@@ -312,6 +312,7 @@ __device__ __forceinline__ void epilogue_chunk_final(const BlockRec& br, int r0,
     const bool upper = !diag || j >= lane;
     if (row_ok && c < n && upper) x = X[static_cast<int64_t>(c) * ld + r];
     o[j] = 0.5f * fmaf(lam, __uint_as_float(v[j]), x);
+    if (ca && row_ok && c < n && upper) compl_add(*ca, o[j], x, c == r ? 1.f : 2.f);
   }
   float* sf = reinterpret_cast<float*>(stg);
   if (diag) {
@@ -526,6 +527,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
+      ComplAcc cacc;
+      ComplAcc* cap = (EPI == EPI_FINAL && p.ep.cres) ? &cacc : nullptr;
 #pragma unroll 1
       for (int ch = ch_begin; ch < ch_end; ++ch) {
         const int c0 = tc.y + 32 * ch;
@@ -536,10 +539,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
         if (EPI == EPI_FINAL)
-          epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam);
+          epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam, cap);
         else
           epilogue_chunk16<EPI, IN8, OUTK>(p, br, bf16, n, C, C_lo, r0, c0, v, wbuf, ycur, lane, track,
                                            amax_bits);
+      }
+      if (EPI == EPI_FINAL && p.ep.cres) {
+        const double cs = compl_warp_sum(cacc);
+        if (lane == 0) p.ep.cres[4 * t + ew] = cs;
       }
       tc_fence_before();
       __syncwarp();

@@ -134,7 +134,7 @@ __device__ __forceinline__ void store_chunk(void* C, int64_t ldc, int n, int r0,
 template <int ET, int EPI, int OUT>
 __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const BlockRec& br, int r0, int c0,
                                                   const uint32_t (&v)[32], float* S, float* YB, int lane, float lam,
-                                                  bool track, unsigned& amax_bits) {
+                                                  bool track, unsigned& amax_bits, ComplAcc* cacc_out = nullptr) {
   constexpr bool TF32 = ET == DT_TF32X3;
   const int n = br.n;
   const int64_t off = br.off;
@@ -182,8 +182,10 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
     } else if (EPI == EPI_FINAL) {
       const int c = c0 + j;
       float x = 0.f;
-      if (row_ok && c < n && (!diag || j >= lane)) x = X[static_cast<int64_t>(c) * ldx + r];
+      const bool upper = !diag || j >= lane;
+      if (row_ok && c < n && upper) x = X[static_cast<int64_t>(c) * ldx + r];
       val = 0.5f * fmaf(lam, acc, x);
+      if (cacc_out && row_ok && c < n && upper) compl_add(*cacc_out, val, x, c == r ? 1.f : 2.f);
     } else {
       val = acc;
     }
@@ -518,11 +520,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           acc_ph ^= 1u;
         }
         if (!ok) break;
+        ComplAcc cacc;
+        ComplAcc* cap = (EPI == EPI_FINAL && p.ep.cres) ? &cacc : nullptr;
 #pragma unroll 1
         for (int ch = ch_begin; ch < ch_end; ++ch) {
           uint32_t v[32];
           tmem_ld32(tmem_base + lanes + kBN + 32 * ch, v);
-          epilogue_chunk_x3<ET, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits);
+          epilogue_chunk_x3<ET, EPI, OUT>(p, br, r0, tc.y + 32 * ch, v, S, YB, lane, lam, track, amax_bits, cap);
+        }
+        if (EPI == EPI_FINAL && p.ep.cres) {
+          const double cs = compl_warp_sum(cacc);
+          if (lane == 0) p.ep.cres[4 * t + ew] = cs;
         }
       } else {
         if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;

@@ -76,6 +76,9 @@ def test_batched_matches_oracle(mats, prec):
             continue
         rel = oracle.rel_err(o, F)
         assert rel <= TOL_F[prec], (n, prec, rel)
+        X64 = X.astype(np.float64)
+        c_ref = float(np.sum(o * (X64 - o))) / float(np.sum(X64 * X64))
+        assert abs(inf["compl_resid"] - c_ref) <= 1e-7, (n, inf["compl_resid"], c_ref)
 
 
 @pytest.mark.parametrize("prec", ["bf16", "mixed"])

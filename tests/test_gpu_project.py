@@ -107,6 +107,34 @@ def test_project_matches_filter(cases, n, prec):
                                                                      info["lambda_bound"],
                                                                      info["overshoot_max"]))
     assert rel_f <= TOL_F[prec]
+    # the reported complementarity residual is <out, X - out> / ||X||_F^2 of
+    # the very output (FP64 here; the epilogue sums in double-float)
+    X64 = X.astype(np.float64)
+    c_ref = float(np.sum(o * (X64 - o))) / float(np.sum(X64 * X64))
+    assert abs(info["compl_resid"] - c_ref) <= 1e-7, (info["compl_resid"], c_ref)
+    # and it is small: the filter output is close to the projection, for
+    # which the residual is exactly 0 (Pi(X) and X - Pi(X) are orthogonal)
+    assert abs(info["compl_resid"]) <= 10 * TOL_F[prec]
+
+
+def test_compl_resid_of_the_exact_filter_output():
+    # Against the oracle's F = Q diag(phi) Q^T: <F, X - F> = sum phi (lam - phi).
+    n = 300
+    X32, Q, lam = synth.spectral_matrix("uniform", n, 71)
+    for prec, sched in (("fp32", "single"), ("mixed", "half")):
+        o, info = run_project(X32, prec)
+        coefs, scales = oracle.schedules.schedule(sched)
+        phi = oracle.phi(lam, info["lambda_bound"], coefs, scales)
+        c_f = float(np.sum(phi * (lam - phi)) / np.sum(lam * lam))
+        assert abs(info["compl_resid"] - c_f) <= 5 * TOL_F[prec], (prec, info["compl_resid"], c_f)
+
+
+def test_norm_bound_alone_reports_no_compl_resid(cases):
+    X, _ = cases[64]
+    info = torch.zeros(b.INFO_BYTES, dtype=torch.uint8, device=DEV)
+    b.psd_norm_bound(64, torch.from_numpy(X).to(DEV), 64, info)
+    torch.cuda.synchronize()
+    assert np.isnan(b.info_from_bytes(info.cpu().numpy())["compl_resid"])
 
 
 def test_fp32_error_does_not_grow_with_n():
