@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=10000)
     ap.add_argument("--precision", default="mixed",
-                    help="mixed (BF16x3 early stages + FP16, meets rel err <= 1e-3), fp16, bf16, fp32")
+                    help="mixed (FP16 iterates, Y and P as FP16 hi/lo pairs in stages 1-4; meets rel err <= 1e-3), "
+                         "fp16, bf16, fp32, fp8_late")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the full-size accuracy check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp32-path", action="store_true", help="skip timing the FP32 comparator path")

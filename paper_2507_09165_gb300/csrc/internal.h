@@ -53,8 +53,8 @@ struct DevState {
 // Epilogue kinds of the symmetric product (fused into the tensor-core kernel).
 enum Epi : int { EPI_COPY = 0, EPI_POLY = 1, EPI_SCALE = 2, EPI_FINAL = 3 };
 
-// Operand storage of the chain: single 16-bit matrices, TF32 hi/lo pairs
-// (FP32 containers), BF16 hi/lo pairs.
+// Operand storage of the chain: single 16-bit or e4m3 matrices, TF32 hi/lo
+// pairs (FP32 containers), FP16 hi/lo pairs.
 // Element types; the X2/X3 names are hi/lo pairs (DT_F16X2: FP16 hi + FP16 lo).
 enum Dtype : int { DT_F16 = 0, DT_BF16 = 1, DT_TF32X3 = 2, DT_E4M3 = 4, DT_F16X2 = 5 };
 

@@ -22,8 +22,9 @@ DEV = torch.device("cuda")
 # and a CPU emulation of the chain with BF16-rounded operands lands at
 # rel_F ~ 1.3e-2 for these inputs; the BF16 tolerance is 2x that floor.
 TOL_F = {"fp16": 2e-3, "bf16": 2.5e-2}
-# FP32 path (TF32x3 products, f~*_single): the 1e-5 bar.  Mixed (BF16x3 for
-# the first three stages, then FP16): the 1e-3 accuracy target of the headline.
+# FP32 path (TF32x3 products, f~*_single): the 1e-5 bar.  Mixed (Y and P as FP16
+# hi/lo pairs in the first four stages, FP16 iterates): the 1e-3 accuracy target
+# of the headline.
 TOL_F.update({"fp32": 1e-5, "mixed": 1e-3})
 SCHED = {"fp16": "half", "bf16": "half", "mixed": "half", "fp32": "single"}
 
