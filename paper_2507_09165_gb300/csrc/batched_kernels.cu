@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "tridiag.cuh"
 
 namespace psd {
 
@@ -439,135 +440,21 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
   }
 }
 
-// Sturm count (division-free leading minors) on the unit-scaled tridiagonal.
-__device__ int bsturm(const double* a, const double* b, int m, double x) {
-  double pm = 1.0, p = a[0] - x;
-  int cnt = (p < 0.0) ? 1 : 0;
-  for (int k = 1; k < m; ++k) {
-    const double pn = (a[k] - x) * p - b[k - 1] * b[k - 1] * pm;
-    const bool change = (pn == 0.0) ? (p > 0.0) : ((pn < 0.0) != (p < 0.0));
-    if (p != 0.0 || pn != 0.0) cnt += change ? 1 : 0;
-    pm = p;
-    p = pn;
-    if (fabs(p) + fabs(pm) > 1e150) {
-      p *= 1e-150;
-      pm *= 1e-150;
-    }
-  }
-  return cnt;
-}
-
 // Largest Ritz pair of each block's tridiagonal (one warp per block):
 // multisection on the Sturm count, inverse iteration with partial pivoting,
 // then q = Q_m y, normalised, split.
 __global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
-  __shared__ double a[kMaxSteps], bt[kMaxSteps], y[kMaxSteps];
-  __shared__ double lo_s, hi_s, scale_s;
+  __shared__ double y[kMaxSteps];
+  __shared__ float a32[kMaxSteps], b32[kMaxSteps];
   __shared__ double sh[kBT / 32];
   const int b = blockIdx.x;
   DevState* st = &L.st[b];
   const int m = st->m;
-  const int lane = threadIdx.x;
   if (threadIdx.x < 32) {
-    if (lane == 0) {
-      double sc = 0.0;
-      for (int k = 0; k < m; ++k) sc = fmax(sc, fabs(st->alpha[k]) + (k < m - 1 ? fabs(st->beta[k]) : 0.0));
-      scale_s = sc > 0.0 ? sc : 1.0;
-    }
-    __syncwarp();
-    const double inv_sc = 1.0 / scale_s;
-    if (lane < m) {
-      a[lane] = st->alpha[lane] * inv_sc;
-      bt[lane] = lane < m - 1 ? st->beta[lane] * inv_sc : 0.0;
-    }
-    __syncwarp();
-    if (lane == 0) {
-      double lo = a[0], hi = a[0];
-      for (int k = 0; k < m; ++k) {
-        const double r = (k > 0 ? fabs(bt[k - 1]) : 0.0) + (k < m - 1 ? fabs(bt[k]) : 0.0);
-        lo = fmin(lo, a[k] - r);
-        hi = fmax(hi, a[k] + r);
-      }
-      lo_s = lo;
-      hi_s = hi;
-    }
-    __syncwarp();
-    for (int round = 0; round < 24; ++round) {
-      const double lo = lo_s, hi = hi_s;
-      if (!(hi - lo > 4.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi)))) break;
-      const double x = lo + (hi - lo) * (lane + 1) / 33.0;
-      const int all_below = bsturm(a, bt, m, x) >= m;
-      const unsigned mask = __ballot_sync(0xffffffffu, all_below);
-      __syncwarp();
-      if (lane == 0) {
-        const int first = mask ? __ffs(mask) - 1 : 32;
-        lo_s = first == 0 ? lo : lo + (hi - lo) * first / 33.0;
-        hi_s = first == 32 ? hi : lo + (hi - lo) * (first + 1) / 33.0;
-      }
-      __syncwarp();
-    }
-    if (lane == 0) {
-      const double sigma = 0.5 * (lo_s + hi_s);
-      const double tiny = 1e-15;
-      double d[kMaxSteps], du[kMaxSteps], du2[kMaxSteps], l[kMaxSteps], rd[kMaxSteps], yy[kMaxSteps];
-      bool piv[kMaxSteps];
-      for (int k = 0; k < m; ++k) {
-        d[k] = a[k] - sigma;
-        du[k] = k < m - 1 ? bt[k] : 0.0;
-        du2[k] = 0.0;
-        piv[k] = false;
-      }
-      for (int k = 0; k < m - 1; ++k) {
-        const double dl = bt[k];
-        if (fabs(d[k]) >= fabs(dl)) {
-          if (d[k] == 0.0) d[k] = tiny;
-          l[k] = dl / d[k];
-          d[k + 1] -= l[k] * du[k];
-        } else {
-          piv[k] = true;
-          l[k] = d[k] / dl;
-          d[k] = dl;
-          const double t = d[k + 1];
-          d[k + 1] = du[k] - l[k] * t;
-          du[k] = t;
-          if (k < m - 2) {
-            du2[k] = du[k + 1];
-            du[k + 1] = -l[k] * du[k + 1];
-          }
-        }
-      }
-      if (d[m - 1] == 0.0) d[m - 1] = tiny;
-      for (int k = 0; k < m; ++k) rd[k] = 1.0 / d[k];
-      for (int k = 0; k < m; ++k) yy[k] = 1.0;
-      for (int it = 0; it < 3; ++it) {
-        for (int k = 0; k < m - 1; ++k) {
-          if (piv[k]) {
-            const double t = yy[k];
-            yy[k] = yy[k + 1];
-            yy[k + 1] = t - l[k] * yy[k];
-          } else {
-            yy[k + 1] -= l[k] * yy[k];
-          }
-        }
-        for (int k = m - 1; k >= 0; --k) {
-          double sacc = yy[k];
-          if (k + 1 < m) sacc -= du[k] * yy[k + 1];
-          if (k + 2 < m) sacc -= du2[k] * yy[k + 2];
-          yy[k] = sacc * rd[k];
-        }
-        double nrm = 0.0;
-        for (int k = 0; k < m; ++k) nrm += yy[k] * yy[k];
-        nrm = sqrt(nrm);
-        if (!(nrm > 0.0) || !isfinite(nrm)) {
-          for (int k = 0; k < m; ++k) yy[k] = k == 0 ? 1.0 : 0.0;
-          break;
-        }
-        const double inv = 1.0 / nrm;
-        for (int k = 0; k < m; ++k) yy[k] *= inv;
-      }
-      for (int k = 0; k < m; ++k) y[k] = yy[k];
-      st->sigma = sigma * scale_s;
-      for (int k = 0; k < kMaxSteps; ++k) st->y[k] = k < m ? yy[k] : 0.0;
+    const double sigma = tridiag_top_eig(st->alpha, st->beta, m, y, a32, b32);
+    if (threadIdx.x == 0) {
+      st->sigma = sigma;
+      for (int k = 0; k < kMaxSteps; ++k) st->y[k] = y[k];
     }
   }
   __syncthreads();

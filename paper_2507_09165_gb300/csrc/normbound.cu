@@ -27,6 +27,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "tridiag.cuh"
 
 namespace psd {
 
@@ -451,139 +452,16 @@ __global__ void lanczos_next_kernel(int n, const double* w, double* Qv, int64_t 
   }
 }
 
-// Sturm count: number of eigenvalues of T (m x m, diag a, off-diag b) below x,
-// = sign changes of the leading principal minors p_k = det(T_k - x I),
-// p_k = (a_k - x) p_{k-1} - b_{k-1}^2 p_{k-2} (no divisions; T is scaled to
-// unit size beforehand so the minors stay in range).
-__device__ int sturm_count(const double* a, const double* b, int m, double x) {
-  double pm = 1.0, p = a[0] - x;
-  int cnt = (p < 0.0) ? 1 : 0;
-  for (int k = 1; k < m; ++k) {
-    const double pn = (a[k] - x) * p - b[k - 1] * b[k - 1] * pm;
-    const bool change = (pn == 0.0) ? (p > 0.0) : ((pn < 0.0) != (p < 0.0));
-    if (p != 0.0 || pn != 0.0) cnt += change ? 1 : 0;
-    pm = p;
-    p = pn;
-    const double mag = fabs(p) + fabs(pm);
-    if (mag > 1e150) {
-      p *= 1e-150;
-      pm *= 1e-150;
-    }
-  }
-  return cnt;
-}
-
-// Largest eigenpair of the Lanczos tridiagonal: multisection on the Sturm
-// count (32 points per round), then inverse iteration with partial pivoting.
+// Largest eigenpair of the Lanczos tridiagonal (tridiag.cuh): sigma and the
+// Ritz vector's coordinates y in the Lanczos basis.
 __global__ void tridiag_kernel(DevState* st) {
-  __shared__ double a[kMaxSteps], b[kMaxSteps];
-  __shared__ double lo_s, hi_s, scale_s;
-  const int lane = threadIdx.x;
-  const int m = st->m;
-  if (lane == 0) {
-    double sc = 0.0;
-    for (int k = 0; k < m; ++k) sc = fmax(sc, fabs(st->alpha[k]) + (k < m - 1 ? fabs(st->beta[k]) : 0.0));
-    scale_s = sc > 0.0 ? sc : 1.0;
+  __shared__ double y[kMaxSteps];
+  __shared__ float a32[kMaxSteps], b32[kMaxSteps];
+  const double sigma = tridiag_top_eig(st->alpha, st->beta, st->m, y, a32, b32);
+  if (threadIdx.x == 0) {
+    st->sigma = sigma;
+    for (int k = 0; k < kMaxSteps; ++k) st->y[k] = y[k];
   }
-  __syncwarp();
-  const double inv_sc = 1.0 / scale_s;
-  if (lane < m) {
-    a[lane] = st->alpha[lane] * inv_sc;
-    b[lane] = lane < m - 1 ? st->beta[lane] * inv_sc : 0.0;
-  }
-  __syncwarp();
-  if (lane == 0) {
-    double lo = a[0], hi = a[0];
-    for (int k = 0; k < m; ++k) {
-      const double r = (k > 0 ? fabs(b[k - 1]) : 0.0) + (k < m - 1 ? fabs(b[k]) : 0.0);
-      lo = fmin(lo, a[k] - r);
-      hi = fmax(hi, a[k] + r);
-    }
-    lo_s = lo;
-    hi_s = hi;
-  }
-  __syncwarp();
-  for (int round = 0; round < 24; ++round) {
-    const double lo = lo_s, hi = hi_s;
-    if (!(hi - lo > 4.0 * 2.2e-16 * fmax(fabs(lo), fabs(hi)))) break;
-    const double x = lo + (hi - lo) * (lane + 1) / 33.0;
-    const int all_below = sturm_count(a, b, m, x) >= m;  // x is above every eigenvalue
-    const unsigned mask = __ballot_sync(0xffffffffu, all_below);
-    __syncwarp();
-    if (lane == 0) {
-      const int first = mask ? __ffs(mask) - 1 : 32;  // first x above the top eigenvalue
-      const double nlo = first == 0 ? lo : lo + (hi - lo) * first / 33.0;
-      const double nhi = first == 32 ? hi : lo + (hi - lo) * (first + 1) / 33.0;
-      lo_s = nlo;
-      hi_s = nhi;
-    }
-    __syncwarp();
-  }
-  if (lane != 0) return;
-  const double sigma = 0.5 * (lo_s + hi_s);
-  // inverse iteration on (T - sigma I): Gaussian elimination with partial
-  // pivoting on the tridiagonal (a row swap creates a second super-diagonal);
-  // the pivots' reciprocals are formed once.
-  const double tiny = 1e-15;
-  double d[kMaxSteps], du[kMaxSteps], du2[kMaxSteps], l[kMaxSteps], rd[kMaxSteps];
-  bool piv[kMaxSteps];
-  for (int k = 0; k < m; ++k) {
-    d[k] = a[k] - sigma;
-    du[k] = k < m - 1 ? b[k] : 0.0;
-    du2[k] = 0.0;
-    piv[k] = false;
-  }
-  for (int k = 0; k < m - 1; ++k) {
-    const double dl = b[k];
-    if (fabs(d[k]) >= fabs(dl)) {
-      if (d[k] == 0.0) d[k] = tiny;
-      l[k] = dl / d[k];
-      d[k + 1] -= l[k] * du[k];
-    } else {
-      piv[k] = true;
-      l[k] = d[k] / dl;
-      d[k] = dl;
-      const double t = d[k + 1];
-      d[k + 1] = du[k] - l[k] * t;
-      du[k] = t;
-      if (k < m - 2) {
-        du2[k] = du[k + 1];
-        du[k + 1] = -l[k] * du[k + 1];
-      }
-    }
-  }
-  if (d[m - 1] == 0.0) d[m - 1] = tiny;
-  for (int k = 0; k < m; ++k) rd[k] = 1.0 / d[k];
-  double y[kMaxSteps];
-  for (int k = 0; k < m; ++k) y[k] = 1.0;
-  for (int it = 0; it < 3; ++it) {
-    for (int k = 0; k < m - 1; ++k) {
-      if (piv[k]) {
-        const double t = y[k];
-        y[k] = y[k + 1];
-        y[k + 1] = t - l[k] * y[k];
-      } else {
-        y[k + 1] -= l[k] * y[k];
-      }
-    }
-    for (int k = m - 1; k >= 0; --k) {
-      double sacc = y[k];
-      if (k + 1 < m) sacc -= du[k] * y[k + 1];
-      if (k + 2 < m) sacc -= du2[k] * y[k + 2];
-      y[k] = sacc * rd[k];
-    }
-    double nrm = 0.0;
-    for (int k = 0; k < m; ++k) nrm += y[k] * y[k];
-    nrm = sqrt(nrm);
-    if (!(nrm > 0.0) || !isfinite(nrm)) {
-      for (int k = 0; k < m; ++k) y[k] = k == 0 ? 1.0 : 0.0;
-      break;
-    }
-    const double inv = 1.0 / nrm;
-    for (int k = 0; k < m; ++k) y[k] *= inv;
-  }
-  st->sigma = sigma * scale_s;
-  for (int k = 0; k < kMaxSteps; ++k) st->y[k] = k < m ? y[k] : 0.0;
 }
 
 // q = sum_k y_k q_k, partial ||q||^2.
@@ -804,16 +682,23 @@ __global__ void set_args_kernel(DevArgs* d, DevArgs h, BlockRec* blk) {
 __global__ void set_block_kernel(BlockRec* dst, BlockRec v) { *dst = v; }
 
 // Status word and overshoot of the last stage into the report, and the
-// complementarity residual from the final product's per-warp shares (one warp,
-// lane-strided then a fixed shuffle tree).
-__global__ void finalize_kernel(const DevArgs* args, DevState* st, const double* cres, int ncompl) {
+// complementarity residual from the final product's per-warp shares (256
+// threads: strided sums, warp trees, then the 8 warp sums in order).
+constexpr int kFinThreads = 256;
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const DevArgs* args, DevState* st,
+                                                                const double* cres, int ncompl) {
+  __shared__ double wsum[kFinThreads / 32];
   psd_info_t* info = args->info;
   double v = 0.0;
   if (cres)
-    for (int i = threadIdx.x; i < ncompl; i += 32) v += cres[i];
+    for (int i = threadIdx.x; i < ncompl; i += kFinThreads) v += cres[i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  v = 0.0;
+  for (int w = 0; w < kFinThreads / 32; ++w) v += wsum[w];
   finalize_report(st, info);
   if (info) {
     const double f2 = st->fro * st->fro;
@@ -932,7 +817,7 @@ cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t s
 }
 
 cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t s, const double* cres, int ncompl) {
-  finalize_kernel<<<1, 32, 0, s>>>(args, st, cres, ncompl);
+  finalize_kernel<<<1, kFinThreads, 0, s>>>(args, st, cres, ncompl);
   return cudaGetLastError();
 }
 
