@@ -37,6 +37,26 @@ ROOFLINE_TRAFFIC = {
 }
 
 
+# Tensor-core products of one projection per precision (each symmetric product does
+# n^3 (1 + 256/n) flops): fp16/bf16 22 (3T + 1, T = 7); mixed 34 (stages 1-4: Y with a pair
+# output 1, Y^2 of pairs 3, P X 2; stages 5-7 three each; final 1); fp32 93 TF32 products
+# (31 split products of 3), whose peak is half the bf16 rate.
+CHAIN_PRODUCTS = {"fp16": (22, 1.0), "bf16": (22, 1.0), "mixed": (34, 1.0), "fp32": (93, 0.5)}
+
+
+def step_roofline(prec, n, ms_step, peak_bf16):
+    """The whole projection against the tensor peak: all its products' flops over the step time
+    (the norm bound, cast and epilogues included in the time)."""
+    if prec not in CHAIN_PRODUCTS:
+        return None
+    products, rate = CHAIN_PRODUCTS[prec]
+    flops = products * n ** 3 * (1 + 256 / n)
+    achieved = flops / (ms_step * 1e-3) / 1e12
+    return {"tensor_products": products, "flops": flops, "achieved_tflops": achieved,
+            "peak_tflops": peak_bf16 * rate, "frac": achieved / (peak_bf16 * rate),
+            "paper_count_22n3_tflops": 22 * n ** 3 / (ms_step * 1e-3) / 1e12}
+
+
 def roofline_traffic(prec, n):
     t = ROOFLINE_TRAFFIC.get(prec)
     if t is None or n != 10000:
@@ -180,7 +200,33 @@ def cpu_baseline(n_target, sample_n=1024, seed=2):
             "sample": "one oracle projection (20-step FP64 Lanczos bound, cyclic Jacobi eigen-decomposition, "
                       "Pi and F) of a Wigner n=%d matrix, %.2f s, scaled by (n/%d)^3 to n=%d"
                       % (sample_n, dt, sample_n, n_target),
-            "sample_seconds": dt}
+            "sample_seconds": dt,
+            "also": cpu_more(sample_n, seed, n_target)}
+
+
+def cpu_more(sample_n, seed, n_target):
+    """Beside the oracle projection: the oracle at n = 256 (unscaled, the size of the small
+    config), and the same composite chain as the GPU (Algorithm 2 stage by stage, FP64 numpy
+    products on the host cores, the oracle's chain_fp64) at sample_n, scaled by n^3 -- the
+    method itself on the CPU, apples to apples with the GPU path."""
+    import numpy as np
+    import oracle
+    from paper_2507_09165_gb300 import synth
+    X256 = synth.gaussian_symmetric(256, 1).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.oracle_project(X256, "half")
+    t256 = time.perf_counter() - t0
+    X = synth.wigner(sample_n, seed).astype(np.float64)
+    coefs, scales = oracle.schedules.schedule("half")
+    lt = oracle.lanczos_bound(X)["lam_tilde"]
+    t0 = time.perf_counter()
+    oracle.chain_fp64(X, lt, coefs, scales)
+    tc = time.perf_counter() - t0
+    return {"oracle_n256_ms": t256 * 1e3,
+            "chain_fp64_ms": tc * 1e3 * (n_target / sample_n) ** 3,
+            "chain_fp64_sample": "Algorithm 2's 22 products in FP64 (numpy) on a Wigner n=%d matrix, %.3f s, "
+                                 "scaled by (n/%d)^3 to n=%d (norm bound excluded)" % (sample_n, tc, sample_n,
+                                                                                       n_target)}
 
 
 def exact_references(lam, Q, lam_tilde, coefs, post):
@@ -617,6 +663,7 @@ def run_ours(args):
                          "peak_source": "%s bf16 burst (MEASURED_PEAKS.json)%s"
                                         % (peak_src, ", x0.5 nominal tf32/bf16 ratio" if prec == "fp32" else ""),
                          "algorithmic_flops_per_launch": alg_flops},
+            "step_roofline": step_roofline(prec, n, ms_step, peaks["bf16_tflops"]),
             "e2e": None if e2e_ms is None else {"value": job_ms_per_projection(e2e_ms, world), "unit": "ms",
                                                 "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": n * n * 4,
                                                 "steps": e2e_steps,
