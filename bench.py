@@ -30,9 +30,9 @@ METRIC = "ms per n=10k PSD projection at rel err ≤1e-3 vs FP32 path; tensor-pi
 # one ncu capture of the bench's own roofline launch, n = 10,000), valid only while the kernel's
 # sources are the ones captured (sha256 over the files below); null otherwise.
 ROOFLINE_TRAFFIC = {
-    "mixed": {"bytes": 2414739968 + 382744576,
+    "mixed": {"bytes": 2342610176 + 382430464,
               "sources": ("paper_2507_09165_gb300/csrc/symgemm_x3.cu", "paper_2507_09165_gb300/csrc/ptx.cuh"),
-              "sha256": "15e6459036472916a25a3f3db652e0c9a97b28d6a0e4ceb96ab0f12318734895",
+              "sha256": "83f90ab0bcee2691522545e049e9d988b5cf04e7317306208ad2e7d81e7a75b3",
               "profile": "profiles/symgemm_x3_f16pairs_traffic_n10000.md"},
 }
 
