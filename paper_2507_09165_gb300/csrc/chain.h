@@ -48,8 +48,11 @@ inline bool kind_is_pair(int kind) { return kind == MK_TF32X3 || kind == MK_F16X
 
 // Mixed precision: Y and P of the first kMixedPairStages stages as FP16 pairs
 // (X_t stays FP16; a CPU emulation of the chain shows the roundings of Y and P
-// in the early stages carry the error, those of X_t do not), the rest FP16.
-constexpr int kMixedPairStages = 4;
+// in the early stages carry the error, those of X_t do not), then
+// kMixedPStages stages with only P as a pair (Y = X^2 single, P formed from
+// it with a pair output: 4 tensor products instead of 6), the rest FP16.
+constexpr int kMixedPairStages = 3;
+constexpr int kMixedPStages = 1;
 // FP8_LATE: the last kFp8Stages stages on e4m3 operands.  The first stages
 // cannot be: their coefficients (a_1 = 8.29, b_1 = -22.6) amplify the e4m3
 // rounding of X^2 (u = 2^-4) beyond the composite's basin.
@@ -86,6 +89,9 @@ inline StageKinds stage_kinds(psd_precision_t prec, int t, int T) {
   k.x = xk(t);
   if (prec == PSD_PREC_MIXED && t < kMixedPairStages) {
     k.y = k.p = MK_F16X2;
+  } else if (prec == PSD_PREC_MIXED && t < kMixedPairStages + kMixedPStages) {
+    k.y = MK_16;
+    k.p = MK_F16X2;
   } else {
     k.y = k.p = k.x;
   }

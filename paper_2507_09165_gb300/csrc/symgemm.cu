@@ -590,7 +590,10 @@ Kernel16 kernel16_for(int epi, bool in8, int outk) {
       default: return nullptr;
     }
   }
-  if (!in8 && outk == 2) return epi == EPI_COPY ? symgemm16_kernel<EPI_COPY, false, 2> : nullptr;
+  if (!in8 && outk == 2)
+    return epi == EPI_COPY ? symgemm16_kernel<EPI_COPY, false, 2>
+           : epi == EPI_POLY ? symgemm16_kernel<EPI_POLY, false, 2>
+                             : nullptr;
   if (epi != EPI_SCALE) return nullptr;
   return in8 ? symgemm16_kernel<EPI_SCALE, true, 0> : symgemm16_kernel<EPI_SCALE, false, 1>;
 }
