@@ -187,7 +187,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def cpu_baseline(n_target, sample_n=1024, seed=2):
+def cpu_baseline(n_target, sample_n=2048, seed=2):
     """The CPU FP64 oracle (Jacobi projection + filter output) on a bounded sample,
     scaled by n^3 to one n_target projection."""
     import numpy as np
