@@ -228,3 +228,46 @@ def test_fp8_early_is_refused():
     with pytest.raises(b.PsdError) as e:
         b.psd_project(8, X, 8, X, "fp8_early")
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("prec", ["fp16", "mixed", "fp32"])
+@pytest.mark.parametrize("c", [2.5, -0.75])
+def test_multiple_of_identity_closed_form(prec, c):
+    # X = c I: every Ritz value of X^2 is c^2 (the mat-vec's FP32 rounding of
+    # the Lanczos vectors keeps the run from an exact breakdown; its residual is
+    # ~1e-7 c^2), so lam~ = |c| to 1e-6 and never below (Theorem 2); the filter
+    # output is phi(c) I with phi(l) = l (1 + g(l / lam~)) / 2, exactly 0 off
+    # the diagonal.
+    n = 300
+    X = (c * np.eye(n)).astype(np.float32)
+    o, info = run_project(X, prec)
+    assert info["status"] == 0
+    lt = info["lambda_bound"]
+    assert abs(c) * (1 - 1e-12) <= lt <= abs(c) * (1 + 1e-6)
+    coefs, scales = oracle.schedules.schedule(SCHED[prec])
+    want = float(oracle.phi(np.array([c]), lt, coefs, scales)[0])
+    assert np.all(o[~np.eye(n, dtype=bool)] == 0.0)
+    d = np.diag(o)
+    assert np.max(np.abs(d - want)) <= TOL_F[prec] * abs(c)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "mixed", "fp32"])
+def test_rank_one_closed_form(prec):
+    # X = s u u^T (|u| = 1): one nonzero eigenvalue s, so F = phi(s) u u^T and
+    # Pi = max(s, 0) u u^T
+    n = 257
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(n)
+    u /= np.linalg.norm(u)
+    for s in (3.0, -3.0):
+        X = (s * np.outer(u, u)).astype(np.float32)
+        o, info = run_project(X, prec)
+        assert info["status"] == 0
+        coefs, scales = oracle.schedules.schedule(SCHED[prec])
+        F = float(oracle.phi(np.array([s]), info["lambda_bound"], coefs, scales)[0]) * np.outer(u, u)
+        # the roundings of the chain spread over the n - 1 zero eigenvalues, where
+        # phi(x) ~ x / 2 passes them through, while ||X||_F = |s| is one eigenvalue:
+        # relative to ||X||_F this is the noise floor of the precision (FP16
+        # iterates: ~3e-3 here, against ~1.3e-3 on a full spectrum)
+        tol = {"fp16": 5e-3, "mixed": 1e-3, "fp32": 1e-5}[prec]
+        assert np.linalg.norm(o - F) <= tol * abs(s), (s, np.linalg.norm(o - F))
