@@ -299,8 +299,9 @@ psd_status_t psd_server_destroy(psd_server_t *server);
  * device, stream, precision and block orders) the library times one product
  * of the chain's first stage under each candidate (median of 3 after a
  * warm-up, on a private stream, synchronising the device) and keeps the
- * fastest; the choice is cached per (precision, block orders) for the life
- * of the process, so later plans with the same key are not re-timed. */
+ * fastest; the choice is cached for the life of the process per precision and
+ * size profile (the number of blocks per order bucket n in (2^(k-1), 2^k]), so
+ * later plans with the same profile are not re-timed. */
 
 /* Forces schedule `index` (0..5) for plans built after the call; -1 restores
  * autotuning (the default).  Returns the previous setting.  Host-only. */

@@ -126,7 +126,20 @@ struct TuneReport {
   float ms[kNumSchedules] = {};
 };
 int g_force_schedule = -1;                                  // for plans built next; -1: autotune
-std::map<std::pair<int, std::vector<int>>, int> g_tuned;   // (precision, block orders) -> schedule
+std::map<std::pair<int, std::vector<int>>, int> g_tuned;   // (precision, order buckets) -> schedule
+
+// Tuning key: the precision and the number of blocks per order bucket
+// (n in (2^(k-1), 2^k]), so that batches with the same size profile share a
+// choice (every schedule gives the same results, so sharing is always safe).
+std::pair<int, std::vector<int>> tune_key(const BatchPlan* p) {
+  std::vector<int> hist(12, 0);
+  for (int n : p->sizes) {
+    int k = 0;
+    while ((1 << k) < n && k < 11) ++k;
+    ++hist[k];
+  }
+  return std::make_pair(static_cast<int>(p->prec), hist);
+}
 TuneReport g_last_tune;
 
 psd_status_t build_bplan(BatchPlan* p) {
@@ -325,7 +338,7 @@ cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
 // private stream; the slots hold zeros, which leaves the timing unchanged).
 psd_status_t tune_bplan(BatchPlan* p) {
   const int grid = std::max(1, std::min(num_sms(), p->ntiles));
-  const auto key = std::make_pair(static_cast<int>(p->prec), p->sizes);
+  const auto key = tune_key(p);
   TuneReport rep;
   rep.ncand = kNumSchedules;
   int chosen = 0;
