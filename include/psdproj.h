@@ -97,7 +97,7 @@ typedef struct {
                             (Pi(X) and X - Pi(X) are orthogonal), so its size measures the
                             distance from a projection.  Summed in the final product's
                             epilogue (double-float per thread, FP64 per tile, fixed order).
-                            NaN where not computed: psd_norm_bound* and the request server */
+                            NaN where not computed (psd_norm_bound*) */
 } psd_info_t;
 
 /* Project one matrix (Algorithm 2).  X: n x n upper triangle read, ld >= n.
@@ -205,7 +205,9 @@ psd_status_t psd_symm_product(int64_t n, const void *A, const void *B, int64_t l
  * creation into
  *   - an arena of 16-bit rows (row length ldm = max_order rounded up to 64):
  *     a request of order n holds 4 n contiguous rows for X_0, two rotating
- *     iterates and the stage polynomial, the four matrices of one stage;
+ *     iterates and the stage polynomial, the four matrices of one stage, and
+ *     ceil(32 T / (2 ldm)) more for the shares of <out, X - out> of its T
+ *     final-product tiles (T = nb (nb + 1), nb = ceil(n / 256), an upper bound);
  *   - per-request records (argument block, device state, report), max_batch
  *     of them;
  *   - the Lanczos scratch of two preparation streams (norm bound of order up

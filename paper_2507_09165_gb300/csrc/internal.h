@@ -75,6 +75,11 @@ struct BlockRec {
   // relative to `off` (the A operand's first row).  Zero when every operand of
   // the block sits at the same rows of its own buffer.
   int64_t db, dc, dy;
+  // EPI_FINAL with EpiParams::cres unset: if set, warp w of the tile at launch
+  // position t writes its share of <out, X - out> to cres[4 (t + cres_shift) + w]
+  // (a served request: its tiles' positions in its own tile list).
+  double* cres;
+  int64_t cres_shift;
 };
 
 struct EpiParams {
@@ -123,6 +128,28 @@ __device__ __forceinline__ double compl_warp_sum(const ComplAcc& a) {
   double v = static_cast<double>(a.h) + static_cast<double>(a.l);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Threads of the CTA that sums a projection's shares of <out, X - out> (the
+// single-projection finalize and the request server use the same order, so a
+// served request reports the same residual as the direct call).
+constexpr int kComplSumThreads = 256;
+
+// Sum of ncompl shares by a CTA of NT threads (fixed order: strided sums per
+// thread, warp trees, then the warp sums in order); valid in thread 0.  wsum:
+// shared scratch of NT / 32 doubles.
+template <int NT>
+__device__ __forceinline__ double compl_cta_sum(const double* cres, int ncompl, double* wsum) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < ncompl; i += NT) v += cres[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) v += wsum[w];
   return v;
 }
 

@@ -684,21 +684,12 @@ __global__ void set_block_kernel(BlockRec* dst, BlockRec v) { *dst = v; }
 // Status word and overshoot of the last stage into the report, and the
 // complementarity residual from the final product's per-warp shares (256
 // threads: strided sums, warp trees, then the 8 warp sums in order).
-constexpr int kFinThreads = 256;
-__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const DevArgs* args, DevState* st,
-                                                                const double* cres, int ncompl) {
-  __shared__ double wsum[kFinThreads / 32];
+__global__ void __launch_bounds__(kComplSumThreads)
+    finalize_kernel(const DevArgs* args, DevState* st, const double* cres, int ncompl) {
+  __shared__ double wsum[kComplSumThreads / 32];
   psd_info_t* info = args->info;
-  double v = 0.0;
-  if (cres)
-    for (int i = threadIdx.x; i < ncompl; i += kFinThreads) v += cres[i];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
-  __syncthreads();
+  const double v = compl_cta_sum<kComplSumThreads>(cres, cres ? ncompl : 0, wsum);
   if (threadIdx.x != 0) return;
-  v = 0.0;
-  for (int w = 0; w < kFinThreads / 32; ++w) v += wsum[w];
   finalize_report(st, info);
   if (info) {
     const double f2 = st->fro * st->fro;
@@ -817,7 +808,7 @@ cudaError_t enqueue_set_block(BlockRec* d_blk, const BlockRec& v, cudaStream_t s
 }
 
 cudaError_t enqueue_finalize(const DevArgs* args, DevState* st, cudaStream_t s, const double* cres, int ncompl) {
-  finalize_kernel<<<1, kFinThreads, 0, s>>>(args, st, cres, ncompl);
+  finalize_kernel<<<1, kComplSumThreads, 0, s>>>(args, st, cres, ncompl);
   return cudaGetLastError();
 }
 

@@ -8,7 +8,9 @@
 //   staging: the block tables and tile lists of one scheduler step
 //   arena: rows of ldm 16-bit elements; a request of order n holds the 4 n
 //          rows [row, row + 4n): X_0, R1, P, R3 (X_0, the two rotating
-//          iterates, the stage polynomial).
+//          iterates, the stage polynomial), then the rows that hold the
+//          per-warp shares of <out, X - out> of its final product (4 doubles
+//          per tile, at the tile's position in the request's tile list).
 //
 // Stage t of a request (cur: X_{t-1}; R1/R3 alternate):
 //   cur = X_0 (t = 0), R1 (t odd), R3 (t even > 0);  Y = R1 (t even), R3 (t odd)
@@ -75,6 +77,7 @@ struct Request {
   int k = 0;         // tiles of that product done
   int ntiles = 0;    // bound on the tile count (admission)
   std::vector<int4> tl;  // tile list of order n
+  double* cres = nullptr;  // shares of <out, X - out>, 4 per tile of tl (arena rows after the matrices)
   Clock::time_point t_submit;
   double latency_ms = 0.0;
   psd_info_t info{};
@@ -122,6 +125,13 @@ struct RowAllocator {
 int64_t tiles_of(int64_t n) {
   const int64_t nb = (n + 255) / 256;
   return nb * (nb + 1);
+}
+
+// Arena rows of a request of order n: its four matrices, then its shares of
+// <out, X - out> (4 doubles per tile) in whole rows of ldm 16-bit elements.
+int64_t rows_of(int64_t ldm, int64_t n) {
+  const int64_t share_bytes = 4 * static_cast<int64_t>(sizeof(double)) * tiles_of(n);
+  return 4 * n + (share_bytes + 2 * ldm - 1) / (2 * ldm);
 }
 
 struct StepDone;
@@ -191,24 +201,38 @@ __global__ void adopt_kernel(DevArgs* dst_args, DevState* dst_st, const DevArgs*
   *dst_st = *src_st;
 }
 
-// Report of every request that finished in a step: status and overshoot
-// (finalize_report), with a timed-out launch of the step as the status of an
-// otherwise clean request, copied into the step's report array.
-__global__ void server_finalize_kernel(uint8_t* recs, const int* slots, int count, const int* launch_status,
-                                       psd_info_t* out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= count) return;
-  uint8_t* r = recs + static_cast<size_t>(slots[k]) * kRecBytes;
+// A request that finishes in a step: its record slot and its shares of
+// <out, X - out> (ncompl = 4 per tile).
+struct FinRec {
+  int slot;
+  int ncompl;
+  const double* cres;
+};
+
+// Report of every request that finished in a step (one CTA each): status and
+// overshoot (finalize_report), with a timed-out launch of the step as the
+// status of an otherwise clean request, and the complementarity residual
+// summed in the order of the single-projection finalize; copied into the
+// step's report array.
+__global__ void __launch_bounds__(kComplSumThreads)
+    server_finalize_kernel(uint8_t* recs, const FinRec* fin, const int* launch_status, psd_info_t* out) {
+  __shared__ double wsum[kComplSumThreads / 32];
+  const FinRec f = fin[blockIdx.x];
+  const double v = compl_cta_sum<kComplSumThreads>(f.cres, f.ncompl, wsum);
+  if (threadIdx.x != 0) return;
+  uint8_t* r = recs + static_cast<size_t>(f.slot) * kRecBytes;
   DevState* st = reinterpret_cast<DevState*>(r + 256);
   psd_info_t* info = reinterpret_cast<psd_info_t*>(r + 1024);
   if (st->status == 0 && *launch_status != 0) st->status = *launch_status;
   finalize_report(st, info);
-  out[k] = *info;
+  const double f2 = st->fro * st->fro;
+  info->compl_resid = f2 > 0.0 ? v / f2 : 0.0;
+  out[blockIdx.x] = *info;
 }
 
 // Staging layout of one step (host and device copies are identical):
 //   BlockRec blocks[4][max_batch]   GEMM 1, 2, 3 and the final product
-//   int fin_slots[max_batch]        record slots of the requests that finish
+//   FinRec fin[max_batch]           the requests that finish (slot, shares)
 //   int4 tiles[4 tile_cap]          tile lists of the step's launches
 //   psd_info_t infos[max_batch]     reports of the finishing requests (device -> host)
 struct StageLayout {
@@ -218,7 +242,7 @@ StageLayout stage_layout(int max_batch, int64_t tile_cap) {
   StageLayout L{};
   L.blocks = 0;
   L.fin = round_up(4 * sizeof(BlockRec) * max_batch, 256);
-  L.tiles = L.fin + round_up(sizeof(int) * max_batch, 256);
+  L.tiles = L.fin + round_up(sizeof(FinRec) * max_batch, 256);
   L.infos = L.tiles + round_up(sizeof(int4) * 4 * tile_cap, 256);  // up to 4 product slots per request
   L.total = L.infos + round_up(sizeof(psd_info_t) * max_batch, 256);
   return L;
@@ -246,7 +270,7 @@ void CUDART_CB on_step_done(void* arg) {
       r->info = d->infos[k];
       r->latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
       r->state = RQ_DONE;
-      s->rows_alloc.release(r->row, 4 * r->n);
+      s->rows_alloc.release(r->row, rows_of(s->ldm, r->n));
       s->tiles_held -= r->ntiles;
       s->free_slots.push_back(r->slot);
       s->lat.push_back(r->latency_ms);
@@ -367,7 +391,7 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
   uint8_t* h = s->h_stage[slot];
   uint8_t* d = s->d_stage[slot];
   BlockRec* hb = reinterpret_cast<BlockRec*>(h + SL.blocks);
-  int* hfin = reinterpret_cast<int*>(h + SL.fin);
+  FinRec* hfin = reinterpret_cast<FinRec*>(h + SL.fin);
   int4* ht = reinterpret_cast<int4*>(h + SL.tiles);
   const int T = s->sched.T;
   const int mb = s->max_batch;
@@ -413,6 +437,7 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
     f.ld = r->ld;
     f.out = r->out;
     f.ld_out = r->ld_out;
+    f.cres = r->cres;  // cres_shift: set with the tile list below
     hb[3 * mb + i] = f;
   }
   // tile allotment, smallest requests first
@@ -473,6 +498,8 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
       for (auto it = parts[g].rbegin(); it != parts[g].rend(); ++it) {
         const Request* r = run[it->req];
         if ((r->dt == DT_BF16 ? 1 : 0) != dti) continue;
+        // final product: tile q of the request sits at launch position q - cres_shift
+        if (g == 3) hb[3 * mb + it->req].cres_shift = it->begin - (nt_all - start);
         for (int q = it->begin; q < it->end; ++q) {
           int4 tc = r->tl[q];
           tc.z = it->req;
@@ -486,7 +513,7 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
   int nf = 0;
   for (int i = 0; i < nrun; ++i)
     if (next[i].done) {
-      hfin[nf++] = run[i]->slot;
+      hfin[nf++] = FinRec{run[i]->slot, 4 * static_cast<int>(run[i]->tl.size()), run[i]->cres};
       fin_ids.push_back(run[i]->id);
     }
   {
@@ -517,9 +544,9 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
       off += cnt[g][dti];
     }
   if (nf > 0) {
-    server_finalize_kernel<<<(nf + 127) / 128, 128, 0, ms>>>(s->recs, reinterpret_cast<const int*>(d + SL.fin), nf,
-                                                             s->d_launch_status,
-                                                             reinterpret_cast<psd_info_t*>(d + SL.infos));
+    server_finalize_kernel<<<nf, kComplSumThreads, 0, ms>>>(s->recs, reinterpret_cast<const FinRec*>(d + SL.fin),
+                                                            s->d_launch_status,
+                                                            reinterpret_cast<psd_info_t*>(d + SL.infos));
     ++launches;
     if (cudaGetLastError() != cudaSuccess) return false;
     if (cudaMemcpyAsync(h + SL.infos, d + SL.infos, sizeof(psd_info_t) * nf, cudaMemcpyDeviceToHost, ms) !=
@@ -546,7 +573,7 @@ void fail_all(psd_server* s) {
     for (Request* r : *v) {
       r->info.status = PSD_ERR_CUDA;
       r->state = RQ_DONE;
-      s->rows_alloc.release(r->row, 4 * r->n);
+      s->rows_alloc.release(r->row, rows_of(s->ldm, r->n));
       s->tiles_held -= r->ntiles;
       s->free_slots.push_back(r->slot);
     }
@@ -573,10 +600,11 @@ void scheduler(psd_server* s) {
         while (!s->queue.empty()) {
           Request* r = s->queue.front();
           if (s->free_slots.empty() || s->tiles_held + r->ntiles > s->tile_cap) break;
-          const int64_t row = s->rows_alloc.alloc(4 * r->n);
+          const int64_t row = s->rows_alloc.alloc(rows_of(s->ldm, r->n));
           if (row < 0) break;
           s->peak_rows = std::max(s->peak_rows, s->rows_alloc.used);
           r->row = row;
+          r->cres = reinterpret_cast<double*>(s->arena + (row + 4 * r->n) * s->ldm);
           r->slot = s->free_slots.back();
           s->free_slots.pop_back();
           s->tiles_held += r->ntiles;
@@ -736,7 +764,7 @@ extern "C" psd_status_t psd_server_create(size_t hbm_budget_bytes, int32_t devic
     tile_cap = 2 * static_cast<int64_t>(max_batch) + (max_order / 256 + 3) * (rows / 1024 + 1);
   }
   while (rows > 0 && fixed_for(tile_cap) + static_cast<size_t>(rows) * row_bytes > hbm_budget_bytes) --rows;
-  if (rows < 4 * max_order) {
+  if (rows < rows_of(s->ldm, max_order)) {
     delete s;
     cudaSetDevice(prev);
     return PSD_ERR_NO_MEMORY;

@@ -527,8 +527,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
+      // shares of <out, X - out>: at the launch position, or at the tile's
+      // position in the block's own list (served requests)
+      double* cdst = nullptr;
+      if (EPI == EPI_FINAL)
+        cdst = p.ep.cres ? p.ep.cres + 4 * t : br.cres ? br.cres + 4 * (t + br.cres_shift) : nullptr;
       ComplAcc cacc;
-      ComplAcc* cap = (EPI == EPI_FINAL && p.ep.cres) ? &cacc : nullptr;
+      ComplAcc* cap = cdst ? &cacc : nullptr;
 #pragma unroll 1
       for (int ch = ch_begin; ch < ch_end; ++ch) {
         const int c0 = tc.y + 32 * ch;
@@ -544,9 +549,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           epilogue_chunk16<EPI, IN8, OUTK>(p, br, bf16, n, C, C_lo, r0, c0, v, wbuf, ycur, lane, track,
                                            amax_bits);
       }
-      if (EPI == EPI_FINAL && p.ep.cres) {
+      if (EPI == EPI_FINAL && cdst) {
         const double cs = compl_warp_sum(cacc);
-        if (lane == 0) p.ep.cres[4 * t + ew] = cs;
+        if (lane == 0) cdst[ew] = cs;
       }
       tc_fence_before();
       __syncwarp();

@@ -147,7 +147,7 @@ def test_server_order_8000_served_equals_direct():
         info, lat = b.psd_server_wait(h, b.psd_server_submit(h, n, V, n, out, n, "bf16"))
         assert info["status"] == 0 and lat > 0
         assert torch.equal(out, ref)
-        for k in ("lambda_bound", "lanczos_sigma", "lanczos_resid", "fro_X", "overshoot_max"):
+        for k in ("lambda_bound", "lanczos_sigma", "lanczos_resid", "fro_X", "overshoot_max", "compl_resid"):
             assert info[k] == r_info[k], k
     finally:
         b.psd_server_destroy(h)

@@ -19,7 +19,7 @@ from paper_2507_09165_gb300 import binding as b, synth  # noqa: E402
 
 GB = 1 << 30
 INFO_KEYS = ("status", "lanczos_steps", "lambda_bound", "lanczos_sigma", "lanczos_resid", "fro_X", "max_diag",
-             "overshoot_max")
+             "overshoot_max", "compl_resid")
 
 
 def make(n, seed, ld=None):
@@ -38,7 +38,8 @@ def single(n, X, ld, prec):
 
 
 def same_info(a, c):
-    return all(a[k] == c[k] for k in INFO_KEYS)
+    # compl_resid: the final product's per-tile shares, summed in the same order
+    return all(a[k] == c[k] for k in INFO_KEYS) and np.isfinite(a["compl_resid"])
 
 
 @pytest.fixture
@@ -93,6 +94,11 @@ def test_served_matches_oracle(server):
     F = ref["F"]
     rel = np.linalg.norm(out.cpu().double().numpy() - F) / np.linalg.norm(F)
     assert rel < 2e-3, rel
+    # the report's <out, X - out> / ||X||_F^2 against the exact filter output's
+    coefs, scales = oracle.schedules.schedule("half")
+    phi = oracle.phi(lam, info["lambda_bound"], coefs, scales)
+    c_f = float(np.sum(phi * (lam - phi)) / np.sum(lam * lam))
+    assert abs(info["compl_resid"] - c_f) <= 1e-2, (info["compl_resid"], c_f)
 
 
 def test_tight_budget_admission_and_reuse():
