@@ -545,7 +545,8 @@ def run_ours(args):
     # projects it with psd_project and reads the result back into pinned host memory.  The
     # steps are pipelined as a stream of projections would be: the copy-in of step k + 1 and
     # the copy-out of step k - 1 run on their own streams while step k projects (two device
-    # buffers each way, ordered by events).
+    # buffers each way, ordered by events).  One untimed pass first: the second buffers and
+    # host pages see their first copies outside the timed region.
     out_h = [torch.empty_like(Xh).pin_memory() for _ in range(2)]
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
     Xb = [Xd, torch.empty_like(Xd)]
@@ -554,34 +555,40 @@ def run_ours(args):
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
-    torch.cuda.synchronize(dev)
-    barrier()
-    ev0.record(s)
-    s_in.wait_stream(s)
-    s_out.wait_stream(s)
-    if e2e_steps:
+
+    def e2e_pass(steps):
+        s_in.wait_stream(s)
+        s_out.wait_stream(s)
         with torch.cuda.stream(s_in):
             Xb[0].copy_(Xh, non_blocking=True)
             ev_in[0].record(s_in)
-    for k in range(e2e_steps):
-        i = k & 1
-        if k + 1 < e2e_steps:
-            with torch.cuda.stream(s_in):
-                if k >= 1:
-                    s_in.wait_event(ev_done[1 - i])  # step k - 1 has finished reading its buffer
-                Xb[1 - i].copy_(Xh, non_blocking=True)
-                ev_in[1 - i].record(s_in)
-        s.wait_event(ev_in[i])
-        if k >= 2:
-            s.wait_event(ev_out[i])  # the copy-out of step k - 2 has left Ob[i]
-        b.psd_project(n, Xb[i], n, Ob[i], prec, s)
-        ev_done[i].record(s)
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_done[i])
-            out_h[i].copy_(Ob[i], non_blocking=True)
-            ev_out[i].record(s_out)
-    s.wait_stream(s_out)
-    s.wait_stream(s_in)
+        for k in range(steps):
+            i = k & 1
+            if k + 1 < steps:
+                with torch.cuda.stream(s_in):
+                    if k >= 1:
+                        s_in.wait_event(ev_done[1 - i])  # step k - 1 has finished reading its buffer
+                    Xb[1 - i].copy_(Xh, non_blocking=True)
+                    ev_in[1 - i].record(s_in)
+            s.wait_event(ev_in[i])
+            if k >= 2:
+                s.wait_event(ev_out[i])  # the copy-out of step k - 2 has left Ob[i]
+            b.psd_project(n, Xb[i], n, Ob[i], prec, s)
+            ev_done[i].record(s)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_done[i])
+                out_h[i].copy_(Ob[i], non_blocking=True)
+                ev_out[i].record(s_out)
+        s.wait_stream(s_out)
+        s.wait_stream(s_in)
+
+    if e2e_steps:
+        e2e_pass(2)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ev0.record(s)
+    if e2e_steps:
+        e2e_pass(e2e_steps)
     ev1.record(s)
     torch.cuda.synchronize(dev)
     barrier()
