@@ -32,7 +32,7 @@ METRIC = "ms per n=10k PSD projection at rel err ≤1e-3 vs FP32 path; tensor-pi
 ROOFLINE_TRAFFIC = {
     "mixed": {"bytes": 2342610176 + 382430464,
               "sources": ("paper_2507_09165_gb300/csrc/symgemm_x3.cu", "paper_2507_09165_gb300/csrc/ptx.cuh"),
-              "sha256": "83f90ab0bcee2691522545e049e9d988b5cf04e7317306208ad2e7d81e7a75b3",
+              "sha256": "bcf6568341a42220c8329c34874071046abfc4bbf1503aaecc8629a97a9dbe78",
               "profile": "profiles/symgemm_x3_f16pairs_traffic_n10000.md"},
 }
 

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -608,31 +609,30 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                               CUtensorMapFloatOOBfill);
 
+// Resolved once (a function-local static: thread-safe initialisation; the
+// request server's thread and callers' threads encode maps concurrently).
 EncodeFn get_encode() {
-  static EncodeFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const EncodeFn fn = [] {
     void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(ptr);
-  }
+      return reinterpret_cast<EncodeFn>(ptr);
+    return static_cast<EncodeFn>(nullptr);
+  }();
   return fn;
 }
 
 }  // namespace
 
 int num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return sms;
 }
 
@@ -718,13 +718,17 @@ cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUt
   if (outk == 2 && dtype != DT_F16) return cudaErrorNotSupported;
   Kernel16 k = kernel16_for(epi, in8, outk);
   if (!k) return cudaErrorNotSupported;
+  static std::mutex attr_mu;  // launches come from callers' threads and the request server's
   static bool attr_set[24] = {};
   const int idx = epi * 6 + (in8 ? 3 : 0) + outk;
   const int smem = smem_bytes16();
-  if (!attr_set[idx]) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set[idx] = true;
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    if (!attr_set[idx]) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      attr_set[idx] = true;
+    }
   }
   const int g = std::max(1, std::min(grid, p.num_tiles));
   k<<<g, kThreads, smem, stream>>>(tmA, tmB, p, out_dtype == DT_BF16 ? 1 : 0);

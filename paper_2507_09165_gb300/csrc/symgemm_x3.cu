@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -597,14 +598,18 @@ cudaError_t launch_symgemm_x3(int et, bool b_single, int epi, int out, const CUt
   KernelX3 k = pick(et, b_single, epi, out);
   if (!k) return cudaErrorNotSupported;
   const int smem = b_single ? X3Cfg<true>::smem() : X3Cfg<false>::smem();
+  static std::mutex done_mu;  // launches come from callers' threads and the request server's
   static KernelX3 done[32];
   static int ndone = 0;
-  bool set = false;
-  for (int i = 0; i < ndone; ++i) set = set || done[i] == k;
-  if (!set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    if (ndone < 32) done[ndone++] = k;
+  {
+    std::lock_guard<std::mutex> lk(done_mu);
+    bool set = false;
+    for (int i = 0; i < ndone; ++i) set = set || done[i] == k;
+    if (!set) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      if (ndone < 32) done[ndone++] = k;
+    }
   }
   GemmParams q = p;
   const uint32_t fmt = et == DT_TF32X3 ? 2u : 0u;  // kind::tf32, or kind::f16 with FP16 operands
