@@ -36,6 +36,33 @@ ROOFLINE_TRAFFIC = {
               "profile": "profiles/symgemm_x3_f16pairs_traffic_n10000.md"},
 }
 
+# Tensor-pipe utilisation of one whole projection (sm__pipe_tensor_cycles_active, percent of
+# peak over elapsed cycles, weighted by launch time) from one ncu capture of the bench's own
+# timed projection at n = 10,000: over all its launches and over its product launches.  Valid
+# only while the library's sources are the ones captured (sha256 over every csrc file).
+TENSOR_PIPE = {
+    "mixed": {"projection_pct": 63.04, "products_pct": 72.74,
+              "sha256": "ffa6dd5b84862eef22e0cc57440cc25eddba4cb845d98ab0ba90d6f969ec433d",
+              "profile": "profiles/tensor_pipe_mixed_n10000.md"},
+}
+
+
+def tensor_pipe(prec, n):
+    t = TENSOR_PIPE.get(prec)
+    if t is None or n != 10000:
+        return None
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2507_09165_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    if h.hexdigest() != t["sha256"]:
+        return None
+    return {"projection_pct": t["projection_pct"], "products_pct": t["products_pct"], "source": "ncu",
+            "profile": t["profile"]}
+
 
 # Tensor-core products of one projection per precision (each symmetric product does
 # n^3 (1 + 256/n) flops): fp16/bf16 22 (3T + 1, T = 7); mixed 32 (stages 1-3: Y with a pair
@@ -673,6 +700,7 @@ def run_ours(args):
                                         % (peak_src, ", x0.5 nominal tf32/bf16 ratio" if prec == "fp32" else ""),
                          "algorithmic_flops_per_launch": alg_flops},
             "step_roofline": step_roofline(prec, n, ms_step, peaks["bf16_tflops"]),
+            "tensor_pipe": tensor_pipe(prec, n),
             "e2e": None if e2e_ms is None else {"value": job_ms_per_projection(e2e_ms, world), "unit": "ms",
                                                 "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": n * n * 4,
                                                 "steps": e2e_steps,
