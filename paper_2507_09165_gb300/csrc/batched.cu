@@ -300,10 +300,11 @@ cudaError_t bgemm(BatchPlan* p, int epi, const Mat& A, const Mat& B, const Mat* 
   const Mat& PB = b1 ? A : B;
   const int dt = kind_dtype(PA);
   CUtensorMap tm[4];
-  if (!encode_tmap_rows(&tm[0], dt, bpart(p, PA, 0), cols, rows, p->ldm, 128) ||
-      !encode_tmap_rows(&tm[1], dt, bpart(p, PA, 1), cols, rows, p->ldm, 128) ||
-      !encode_tmap_rows(&tm[2], dt, bpart(p, PB, 0), cols, rows, p->ldm, 256) ||
-      !encode_tmap_rows(&tm[3], dt, bpart(p, PB, b1 ? 0 : 1), cols, rows, p->ldm, 256))
+  const int rb = x3_row_bytes(b1);
+  if (!encode_tmap_rows(&tm[0], dt, bpart(p, PA, 0), cols, rows, p->ldm, 128, rb) ||
+      !encode_tmap_rows(&tm[1], dt, bpart(p, PA, 1), cols, rows, p->ldm, 128, rb) ||
+      !encode_tmap_rows(&tm[2], dt, bpart(p, PB, 0), cols, rows, p->ldm, 256, rb) ||
+      !encode_tmap_rows(&tm[3], dt, bpart(p, PB, b1 ? 0 : 1), cols, rows, p->ldm, 256, rb))
     return cudaErrorInvalidValue;
   const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
   return launch_symgemm_x3(dt, b1, epi, out_mode, tm, g, grid, s);

@@ -178,7 +178,18 @@ struct Schedule {
 bool get_schedule(psd_precision_t prec, Schedule& s);
 
 // --- host helpers (symgemm.cu) ---
-bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows);
+// Bytes of K per operand row in a pipeline stage (one swizzle row) and per
+// tensor-map box row, by kernel: the 16-bit / e4m3 product keeps 128-byte
+// rows (4 stages of 48 KB; 8 stages of 64-byte rows measured 20% slower); the
+// split product with a pair B takes 64-byte rows (4 stages of 48 KB in place
+// of 2 of 96 KB: three stages in flight instead of one, 10% faster); with a
+// single B, kRowBytesX3Single.
+constexpr int kRowBytes16 = 128;
+constexpr int kRowBytesX3Single = 128;
+inline int x3_row_bytes(bool b_single) { return b_single ? kRowBytesX3Single : 64; }
+// row_bytes: bytes of K per box row, 128 (128-byte swizzle) or 64 (64-byte swizzle).
+bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows,
+                 int row_bytes = kRowBytes16);
 // dtype: operand type (DT_F16, DT_BF16 or DT_E4M3); out_dtype: type of the
 // EPI_COPY/POLY/SCALE output (DT_F16, DT_BF16, DT_E4M3, or DT_F16X2 for an FP16
 // pair written to ep.C / ep.C_lo; -1: the operand type).
@@ -231,7 +242,7 @@ cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* 
 cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, const double* cres,
                                    const int* cidx, const int2* crange, cudaStream_t stream);
 bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t cols, int64_t rows, int64_t ld,
-                      int box_rows);
+                      int box_rows, int row_bytes = kRowBytes16);
 
 // --- norm bound and cast (normbound.cu) ---
 struct LanczosBufs {

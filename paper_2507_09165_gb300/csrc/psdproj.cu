@@ -256,10 +256,11 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
   const Mat& PB = b1 ? A : B;
   const int dt = kind_dtype(PA);
   CUtensorMap tm[4];
-  if (!encode_tmap(&tm[0], dt, part_ptr(p, PA, 0), n, ldm, 128) ||
-      !encode_tmap(&tm[1], dt, part_ptr(p, PA, 1), n, ldm, 128) ||
-      !encode_tmap(&tm[2], dt, part_ptr(p, PB, 0), n, ldm, 256) ||
-      !encode_tmap(&tm[3], dt, part_ptr(p, PB, b1 ? 0 : 1), n, ldm, 256))
+  const int rb = x3_row_bytes(b1);
+  if (!encode_tmap(&tm[0], dt, part_ptr(p, PA, 0), n, ldm, 128, rb) ||
+      !encode_tmap(&tm[1], dt, part_ptr(p, PA, 1), n, ldm, 128, rb) ||
+      !encode_tmap(&tm[2], dt, part_ptr(p, PB, 0), n, ldm, 256, rb) ||
+      !encode_tmap(&tm[3], dt, part_ptr(p, PB, b1 ? 0 : 1), n, ldm, 256, rb))
     return cudaErrorInvalidValue;
   const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
   return launch_symgemm_x3(dt, b1, epi, out_mode, tm, g, grid, s);
@@ -558,8 +559,9 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     CUtensorMap tm[4];
     const uint8_t* a8 = static_cast<const uint8_t*>(A);
     const uint8_t* b8 = static_cast<const uint8_t*>(B);
-    if (!encode_tmap(&tm[0], dtype, a8, n, ld, 128) || !encode_tmap(&tm[1], dtype, a8 + pair, n, ld, 128) ||
-        !encode_tmap(&tm[2], dtype, b8, n, ld, 256) || !encode_tmap(&tm[3], dtype, b8 + pair, n, ld, 256))
+    const int rb = x3_row_bytes(false);
+    if (!encode_tmap(&tm[0], dtype, a8, n, ld, 128, rb) || !encode_tmap(&tm[1], dtype, a8 + pair, n, ld, 128, rb) ||
+        !encode_tmap(&tm[2], dtype, b8, n, ld, 256, rb) || !encode_tmap(&tm[3], dtype, b8 + pair, n, ld, 256, rb))
       return PSD_ERR_CUDA;
     e = launch_symgemm_x3(dtype, false, epi, epi == 3 ? 2 : 0, tm, g, num_sms(), s);
   }

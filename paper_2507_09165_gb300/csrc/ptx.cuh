@@ -229,6 +229,21 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t smem_addr) {
   return d;
 }
 
+// The same for a tile stored with the 64-byte swizzle (rows of 64 bytes,
+// 8-row groups 512 bytes apart), as TMA writes it with
+// CU_TENSOR_MAP_SWIZZLE_64B: stride byte offset 512, swizzle mode 4 = 64B.
+// The tile base must be 512-byte aligned; a K step inside the 64-byte row is
+// a plain address offset.
+__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((smem_addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1u) << 16;
+  d |= static_cast<uint64_t>(512u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(4u) << 61;
+  return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16 / kind::tf32 with FP32
 // accumulation, both operands K-major, dense: D format (bits 4-5) = F32,
 // A/B format (7-9, 10-12), N >> 3 (17-22), M >> 4 (24-28).

@@ -38,13 +38,14 @@ constexpr int kBM = 128;
 constexpr int kBN = 256;
 constexpr int kThreads = 192;
 
-// 16-bit operands: 64 K-elements per stage (one 128-byte swizzle row); e4m3
-// operands: 128.  The stage layout in bytes is the same for both.
-constexpr int kBK16 = 64;
-constexpr int kBK8 = 128;
-constexpr int kStages16 = 4;
-constexpr int kABytes16 = kBM * kBK16 * 2;          // 16 KB
-constexpr int kBBytes16 = kBN * kBK16 * 2;          // 32 KB
+// One swizzle row of kRowBytes16 (128) bytes of K per operand row and stage:
+// 64 K-elements for 16-bit operands, 128 for e4m3 (the same stage layout in
+// bytes); 4 stages of 48 KB.
+constexpr int kBK16 = kRowBytes16 / 2;
+constexpr int kBK8 = kRowBytes16;
+constexpr int kStages16 = 4 * (128 / kRowBytes16);
+constexpr int kABytes16 = kBM * kRowBytes16;          // 16 KB
+constexpr int kBBytes16 = kBN * kRowBytes16;          // 32 KB
 constexpr int kStageBytes16 = kABytes16 + kBBytes16;  // 48 KB
 
 // Epilogue staging per warp.  16-bit outputs: the chunk row-major (S),
@@ -61,6 +62,7 @@ __host__ __device__ constexpr int smem_bytes16() {
   return 1024 /* alignment slack */ + kStages16 * kStageBytes16 + 4 * kEpiWarpBytes +
          8 * (2 * kStages16 + 5) + 16;
 }
+static_assert(smem_bytes16() <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ uint16_t to16(float v, bool bf16) {
   return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
@@ -453,14 +455,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
           const uint32_t a_addr = smem_u32(stages + s * kStageBytes16);
           const uint32_t b_addr = a_addr + kABytes16;
+          auto desc = [](uint32_t a) { return kRowBytes16 == 64 ? sw64_kmajor_desc(a) : sw128_kmajor_desc(a); };
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction (16 halves or 32 e4m3)
+          for (int k = 0; k < kRowBytes16 / 32; ++k) {  // 32 bytes of K per instruction (16 halves or 32 e4m3)
             if (IN8)
-              mma_f8(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k), idesc,
-                     (kb | k) != 0 ? 1u : 0u);
+              mma_f8(d_tmem, desc(a_addr + 32 * k), desc(b_addr + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
             else
-              mma_f16(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k), idesc,
-                      (kb | k) != 0 ? 1u : 0u);
+              mma_f16(d_tmem, desc(a_addr + 32 * k), desc(b_addr + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
           }
           mma_commit(empty_bar(s));
         }
@@ -637,9 +638,11 @@ int num_sms() {
 }
 
 // Tensor map of an n x n symmetric operand with row stride ld elements.  The
-// box is 128 bytes of K (one swizzle row) by box_rows rows; boxes that reach
-// past n are zero-filled by the TMA unit.
-bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows) {
+// box is row_bytes (128 or 64) bytes of K -- one swizzle row, 128- or 64-byte
+// swizzle -- by box_rows rows; boxes that reach past n are zero-filled by the
+// TMA unit.
+bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64_t ld, int box_rows,
+                 int row_bytes) {
   EncodeFn fn = get_encode();
   if (!fn) return false;
   const int esz = dtype == DT_TF32X3 ? 4 : (dtype == DT_E4M3 ? 1 : 2);
@@ -647,12 +650,14 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
                                  : dtype == DT_BF16                     ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                  : dtype == DT_E4M3                     ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  if (row_bytes != 128 && row_bytes != 64) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(row_bytes / esz), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -660,7 +665,7 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
 // Tensor map of a stacked buffer of `rows` rows (row stride ld elements) of
 // which the first `cols` columns are addressed; same boxes as encode_tmap.
 bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t cols, int64_t rows, int64_t ld,
-                      int box_rows) {
+                      int box_rows, int row_bytes) {
   EncodeFn fn = get_encode();
   if (!fn) return false;
   const int esz = dtype == DT_TF32X3 ? 4 : (dtype == DT_E4M3 ? 1 : 2);
@@ -668,12 +673,14 @@ bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t col
                                  : dtype == DT_BF16                     ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                  : dtype == DT_E4M3                     ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  if (row_bytes != 128 && row_bytes != 64) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esz};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(row_bytes / esz), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 

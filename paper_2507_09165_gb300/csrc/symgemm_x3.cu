@@ -10,7 +10,7 @@
 //     mixed-precision chain's pair stages.
 // A variant with a single B operand (B1) forms A_hi B + A_lo B: the P X (= X P,
 // the two commute) product of those stages, where only P is a pair; its
-// 64 KB stages (no B_lo) leave room for a third stage.
+// stages (no B_lo) are two thirds the size, so the ring has half again as many.
 // Same symmetric tiling, warp roles and fused stage epilogues as the 16-bit
 // kernel (symgemm.cu); the output is again a pair, or a single FP16 matrix,
 // or the FP32 final result.
@@ -39,30 +39,29 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBN = 256;
 constexpr int kThreads = 192;
-constexpr int kABytes = kBM * 128;  // one 128-byte swizzle row of K per operand row
-constexpr int kBBytes = kBN * 128;
 constexpr int kSW = 33;                                 // staging row stride (words)
 constexpr int kEpiWarpBytes = 2 * 32 * kSW * 4;         // values + Y chunk
 constexpr int kTmemCols = 512;
 constexpr int kPromoteK = 128;  // K elements per promoted chunk (TF32 pairs)
 
-// Pipeline: 2 stages of 96 KB (A_hi | A_lo | B_hi | B_lo), or with a single B
-// 3 stages of 64 KB (A_hi | A_lo | B).
+// Pipeline (x3_row_bytes): with a pair B, 4 stages of 48 KB (A_hi | A_lo |
+// B_hi | B_lo) of 64-byte rows of K, 64-byte swizzle (3 stages in flight while
+// the MMAs read the fourth: three times the lookahead of 2 stages of 128-byte
+// rows in the same space); with a single B, 3 stages of 64 KB (A_hi | A_lo |
+// B) of kRowBytesX3Single-byte rows (or 6 of 32 KB).
 template <bool B1>
 struct X3Cfg {
-  static constexpr int kStages = B1 ? 3 : 2;
+  static constexpr int kRowBytes = B1 ? kRowBytesX3Single : 64;
+  static constexpr bool kSW64 = kRowBytes == 64;
+  static constexpr int kABytes = kBM * kRowBytes;
+  static constexpr int kBBytes = kBN * kRowBytes;
+  static constexpr int kStages = (B1 ? 3 : 2) * (128 / kRowBytes);
   static constexpr int kStageBytes = B1 ? 2 * kABytes + kBBytes : 2 * kABytes + 2 * kBBytes;
   static constexpr int smem() {
     return 1024 + kStages * kStageBytes + 4 * kEpiWarpBytes + 8 * (2 * kStages + 5) + 16;
   }
 };
 static_assert(X3Cfg<false>::smem() <= 232448 && X3Cfg<true>::smem() <= 232448, "shared memory per CTA");
-
-template <int ET>
-__device__ __forceinline__ float ld_elem(const void* p, int64_t idx) {
-  if (ET == DT_TF32X3) return static_cast<const float*>(p)[idx];
-  return __half2float(__ushort_as_half(static_cast<const uint16_t*>(p)[idx]));
-}
 
 __device__ __forceinline__ float tf32_rn(float v) {
   if (!isfinite(v)) return v;
@@ -131,6 +130,90 @@ __device__ __forceinline__ void store_chunk(void* C, int64_t ldc, int n, int r0,
   }
 }
 
+// The Y chunk (r0..r0+31) x (c0..c0+31) of a symmetric pair, value hi + lo
+// (FP32 sum of the two parts), into YB[j * kSW + t] = Y(r0 + t, c0 + j); zeros
+// outside n.  Read as memory rows c0 + j with 16-byte loads, all of a lane's
+// loads issued before any is used (the epilogue of the polynomial stage is
+// otherwise bound by the latency of 2-byte loads).  The caller synchronises
+// the warp before YB is read.
+template <int ET>
+__device__ __forceinline__ void load_y_pair_chunk(const void* Yh, const void* Yl, int64_t ldy, int n, int r0, int c0,
+                                                  int lane, float* YB) {
+  if constexpr (ET == DT_TF32X3) {
+    const int q = lane & 7;  // rows r0 + 4 q .. + 3
+    const int r = r0 + 4 * q;
+    float4 h[8], l[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = c0 + (lane >> 3) + 4 * k;
+      h[k] = l[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c < n && r < n) {
+        const int64_t idx = static_cast<int64_t>(c) * ldy + r;
+        const float* ph = static_cast<const float*>(Yh) + idx;
+        const float* pl = static_cast<const float*>(Yl) + idx;
+        if (r + 3 < n && ((reinterpret_cast<uintptr_t>(ph) | reinterpret_cast<uintptr_t>(pl)) & 15) == 0) {
+          h[k] = __ldg(reinterpret_cast<const float4*>(ph));
+          l[k] = __ldg(reinterpret_cast<const float4*>(pl));
+        } else {
+          float th[4] = {0.f, 0.f, 0.f, 0.f}, tl[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int e = 0; e < 4 && r + e < n; ++e) {  // the edge at n, or an unaligned caller buffer
+            th[e] = ph[e];
+            tl[e] = pl[e];
+          }
+          h[k] = make_float4(th[0], th[1], th[2], th[3]);
+          l[k] = make_float4(tl[0], tl[1], tl[2], tl[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float* d = YB + ((lane >> 3) + 4 * k) * kSW + 4 * q;
+      d[0] = h[k].x + l[k].x;
+      d[1] = h[k].y + l[k].y;
+      d[2] = h[k].z + l[k].z;
+      d[3] = h[k].w + l[k].w;
+    }
+  } else {
+    const int q = lane & 3;  // rows r0 + 8 q .. + 7
+    const int r = r0 + 8 * q;
+    uint4 h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = c0 + (lane >> 2) + 8 * k;
+      h[k] = l[k] = make_uint4(0u, 0u, 0u, 0u);
+      if (c < n && r < n) {
+        const int64_t idx = static_cast<int64_t>(c) * ldy + r;
+        const uint16_t* ph = static_cast<const uint16_t*>(Yh) + idx;
+        const uint16_t* pl = static_cast<const uint16_t*>(Yl) + idx;
+        if (r + 7 < n && ((reinterpret_cast<uintptr_t>(ph) | reinterpret_cast<uintptr_t>(pl)) & 15) == 0) {
+          h[k] = __ldg(reinterpret_cast<const uint4*>(ph));
+          l[k] = __ldg(reinterpret_cast<const uint4*>(pl));
+        } else {
+          uint32_t th[4] = {0u, 0u, 0u, 0u}, tl[4] = {0u, 0u, 0u, 0u};
+          for (int e = 0; e < 8 && r + e < n; ++e) {  // the edge at n, or an unaligned caller buffer
+            th[e >> 1] |= static_cast<uint32_t>(ph[e]) << (16 * (e & 1));
+            tl[e >> 1] |= static_cast<uint32_t>(pl[e]) << (16 * (e & 1));
+          }
+          h[k] = make_uint4(th[0], th[1], th[2], th[3]);
+          l[k] = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float* d = YB + ((lane >> 2) + 8 * k) * kSW + 8 * q;
+      const uint32_t wh[4] = {h[k].x, h[k].y, h[k].z, h[k].w};
+      const uint32_t wl[4] = {l[k].x, l[k].y, l[k].z, l[k].w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const uint16_t uh = static_cast<uint16_t>(wh[e >> 1] >> (16 * (e & 1)));
+        const uint16_t ul = static_cast<uint16_t>(wl[e >> 1] >> (16 * (e & 1)));
+        d[e] = __half2float(__ushort_as_half(uh)) + __half2float(__ushort_as_half(ul));
+      }
+    }
+  }
+}
+
 // OUT: 0 = split pair of the operand kind, 1 = single FP16, 2 = FP32 final output.
 template <int ET, int EPI, int OUT>
 __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const BlockRec& br, int r0, int c0,
@@ -153,17 +236,8 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
   const bool row_ok = r < n;
   float o[32];
   if (EPI == EPI_POLY) {
-    // Y chunk (value = hi + lo), read coalesced as memory rows c0 + j
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j) {
-      const int c = c0 + j;
-      float y = 0.f;
-      if (row_ok && c < n) {
-        const int64_t idx = static_cast<int64_t>(c) * p.ep.ldy + r;
-        y = ld_elem<ET>(Yh, idx) + ld_elem<ET>(Yl, idx);
-      }
-      YB[j * kSW + lane] = y;
-    }
+    load_y_pair_chunk<ET>(Yh, Yl, p.ep.ldy, n, r0, c0, lane, YB);
+    __syncwarp();
   }
   const float* X = nullptr;
   int64_t ldx = 0;
@@ -257,6 +331,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const GemmParams p) {
   constexpr int kStages = X3Cfg<B1>::kStages;
   constexpr int kStageBytes = X3Cfg<B1>::kStageBytes;
+  constexpr int kABytes = X3Cfg<B1>::kABytes;
+  constexpr int kBBytes = X3Cfg<B1>::kBBytes;
+  constexpr bool kSW64 = X3Cfg<B1>::kSW64;
+  auto desc = [](uint32_t a) { return kSW64 ? sw64_kmajor_desc(a) : sw128_kmajor_desc(a); };
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -300,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
   constexpr bool TF32 = ET == DT_TF32X3;
-  constexpr int kKElems = TF32 ? 32 : 64;  // K elements per 128-byte row
+  constexpr int kKElems = X3Cfg<B1>::kRowBytes / (TF32 ? 4 : 2);  // K elements per stage
   constexpr int kKStep = TF32 ? 8 : 16;    // K per MMA instruction (32 bytes)
   constexpr bool kPromote = TF32;
 
@@ -373,9 +451,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int k = 0; k < kKElems / kKStep; ++k) {
               const uint32_t off = 32 * k;
               const uint32_t first = ((kb - kc) | k) == 0 ? 0u : 1u;
-              mma_tf32(tmem_base, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
-              mma_tf32(tmem_base, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
-              mma_tf32(tmem_base, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
+              mma_tf32(tmem_base, desc(ah + off), desc(bh + off), idesc, first);
+              mma_tf32(tmem_base, desc(ah + off), desc(bl + off), idesc, 1u);
+              mma_tf32(tmem_base, desc(al + off), desc(bh + off), idesc, 1u);
             }
             mma_commit(empty_bar(s));
           }
@@ -425,13 +503,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t off = 32 * k;
             const uint32_t first = (kb | k) == 0 ? 0u : 1u;
             if (TF32) {
-              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
-              mma_tf32(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
-              mma_tf32(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
+              mma_tf32(d_tmem, desc(ah + off), desc(bh + off), idesc, first);
+              mma_tf32(d_tmem, desc(ah + off), desc(bl + off), idesc, 1u);
+              mma_tf32(d_tmem, desc(al + off), desc(bh + off), idesc, 1u);
             } else {
-              mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bh + off), idesc, first);
-              if (!B1) mma_f16(d_tmem, sw128_kmajor_desc(ah + off), sw128_kmajor_desc(bl + off), idesc, 1u);
-              mma_f16(d_tmem, sw128_kmajor_desc(al + off), sw128_kmajor_desc(bh + off), idesc, 1u);
+              mma_f16(d_tmem, desc(ah + off), desc(bh + off), idesc, first);
+              if (!B1) mma_f16(d_tmem, desc(ah + off), desc(bl + off), idesc, 1u);
+              mma_f16(d_tmem, desc(al + off), desc(bh + off), idesc, 1u);
             }
           }
           mma_commit(empty_bar(s));
