@@ -30,9 +30,9 @@ METRIC = "ms per n=10k PSD projection at rel err ≤1e-3 vs FP32 path; tensor-pi
 # one ncu capture of the bench's own roofline launch, n = 10,000), valid only while the kernel's
 # sources are the ones captured (sha256 over the files below); null otherwise.
 ROOFLINE_TRAFFIC = {
-    "mixed": {"bytes": 2342610176 + 382430464,
+    "mixed": {"bytes": 1897260800 + 381659392,
               "sources": ("paper_2507_09165_gb300/csrc/symgemm_x3.cu", "paper_2507_09165_gb300/csrc/ptx.cuh"),
-              "sha256": "bcf6568341a42220c8329c34874071046abfc4bbf1503aaecc8629a97a9dbe78",
+              "sha256": "723920b5d3f1d5b77ab97207224becb831b8fb7f33eb1093294139542cc9d1b9",
               "profile": "profiles/symgemm_x3_f16pairs_traffic_n10000.md"},
 }
 
@@ -41,8 +41,8 @@ ROOFLINE_TRAFFIC = {
 # timed projection at n = 10,000: over all its launches and over its product launches.  Valid
 # only while the library's sources are the ones captured (sha256 over every csrc file).
 TENSOR_PIPE = {
-    "mixed": {"projection_pct": 63.04, "products_pct": 72.74,
-              "sha256": "ffa6dd5b84862eef22e0cc57440cc25eddba4cb845d98ab0ba90d6f969ec433d",
+    "mixed": {"projection_pct": 65.81, "products_pct": 76.37,
+              "sha256": "f6a8d1f28d618c096094bcc3713d07e4f6466c8d74fd7a26d84e86d78812207b",
               "profile": "profiles/tensor_pipe_mixed_n10000.md"},
 }
 
