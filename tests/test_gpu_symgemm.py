@@ -213,6 +213,49 @@ def test_split_product(n, prec):
     assert np.linalg.norm(err) / np.linalg.norm(D[iu]) < bound
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("n", [97, 300, 513])
+def test_split_product_poly_and_scale_epilogues(n, prec):
+    # The stage epilogues of the split product on pair operands, ld a multiple of 8
+    # (not of 64) and n not a multiple of 32, so the Y chunks have ragged edges:
+    # P = a I + b Y + c Y^2 (polynomial, Y read as a pair in the epilogue) and
+    # s A B (scale), both split into pairs again.
+    ld = (n + 7) // 8 * 8
+    rng = np.random.default_rng(1000 + n)
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    Y64 = 0.5 * (G + G.T)
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    B64 = 0.5 * (G + G.T)
+    Y, B = split_pair(Y64, prec, n, ld), split_pair(B64, prec, n, ld)
+    dev = torch.device("cuda")
+    Yd, Bd = Y.to(dev), B.to(dev)
+    Yv = Y.double().numpy()[0, :, :n] + Y.double().numpy()[1, :, :n]
+    Bv = B.double().numpy()[0, :, :n] + B.double().numpy()[1, :, :n]
+    a, bb, c, sc = 1.5, -0.7, 0.3, 1.0 / 1.01
+    iu = np.triu_indices(n)
+    rel = 2.0 ** -18 if prec == "mixed" else 2.0 ** -20
+    for epi, params, B_d, Bval in ((1, (a, bb, c), Yd, Yv), (2, (sc,), Bd, Bv)):
+        Cd = torch.full_like(Yd, float("nan"))
+        if epi == 1:
+            b.psd_symm_product(n, Yd, B_d, ld, Cd, 0, prec, 1, params=params, aux=Yd, ld_aux=ld)
+        else:
+            b.psd_symm_product(n, Yd, B_d, ld, Cd, 0, prec, 2, params=params)
+        torch.cuda.synchronize()
+        Cc = Cd.cpu().double().numpy()
+        C = Cc[0, :, :n] + Cc[1, :, :n]
+        prod = Yv @ Bval
+        acc = 4 * n * 2.0 ** -24 * (np.abs(Yv) @ np.abs(Bval))
+        if epi == 1:
+            D = a * np.eye(n) + bb * Yv + c * prod
+            tol = abs(c) * (rel * np.abs(prod) + acc) + rel * np.abs(D) + 2.0 ** -22 * (abs(bb) * np.abs(Yv) + a)
+        else:
+            D = sc * prod
+            tol = sc * (rel * np.abs(prod) + acc) + rel * np.abs(D)
+        assert np.array_equal(C, C.T), epi
+        err = np.abs(C - D)[iu]
+        assert np.all(err <= tol[iu]), (epi, np.max(err / tol[iu]))
+
+
 F8 = getattr(torch, "float8_e4m3fn", None)
 
 
