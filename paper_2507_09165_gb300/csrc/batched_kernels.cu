@@ -117,11 +117,14 @@ __device__ __forceinline__ void bsymv_tile(const float* __restrict__ T, int n, i
     vj[k] = (jb + k < n) ? __ldg(vh + jb + k) : 0.f;
   }
   // the packed tile: column c of the tile at T + 128 c, zeros outside n x n
+  // (the zeros are not read: small blocks fill a few rows of their tile)
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float* col = T + (8 * tcol + c) * kSymvTile + 8 * tr;
-    const float4 a4 = __ldg(reinterpret_cast<const float4*>(col));
-    const float4 b4 = __ldg(reinterpret_cast<const float4*>(col + 4));
+    const bool live = jb + c < n && ib < n;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 a4 = live ? __ldg(reinterpret_cast<const float4*>(col)) : z;
+    const float4 b4 = live && ib + 4 < n ? __ldg(reinterpret_cast<const float4*>(col + 4)) : z;
     x[c][0] = a4.x; x[c][1] = a4.y; x[c][2] = a4.z; x[c][3] = a4.w;
     x[c][4] = b4.x; x[c][5] = b4.y; x[c][6] = b4.z; x[c][7] = b4.w;
   }
