@@ -292,7 +292,7 @@ cudaError_t bgemm(BatchPlan* p, int epi, const Mat& A, const Mat& B, const Mat* 
       return cudaErrorInvalidValue;
     const uint32_t fmt = dt == DT_BF16 ? 1u : 0u;
     g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);
-    return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? kind_dtype(*out) : -1);
+    return launch_symgemm(dt, epi, ta, tb, g, grid, s, out ? kind_dtype(*out) : -1, /*many_small=*/true);
   }
   if (route == ROUTE_NONE) return cudaErrorNotSupported;
   const bool b1 = route == ROUTE_X2;

@@ -193,8 +193,12 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
 // dtype: operand type (DT_F16, DT_BF16 or DT_E4M3); out_dtype: type of the
 // EPI_COPY/POLY/SCALE output (DT_F16, DT_BF16, DT_E4M3, or DT_F16X2 for an FP16
 // pair written to ep.C / ep.C_lo; -1: the operand type).
+// many_small: a launch over many small matrices (the blocks of a block-diagonal
+// cone, orders <= 1024), run with 8 epilogue warps and a 3-stage ring where an
+// instance exists.
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                           const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1);
+                           const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1,
+                           bool many_small = false);
 // split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
 // out: 0 = split pair, 1 = single FP16, (EPI_FINAL) FP32 to the caller's output.
 // Split-operand products: et = DT_TF32X3 (TF32 pairs) or DT_F16X2 (FP16

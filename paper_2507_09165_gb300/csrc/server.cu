@@ -367,6 +367,7 @@ cudaError_t step_gemm(psd_server* s, int dti, int epi, const BlockRec* d_blocks,
   g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);
   const int grid = std::min(num_sms(), ntiles);
   ++launches;
+  // (4 epilogue warps: served steps mix large requests, whose main loops want the 4-stage ring)
   return launch_symgemm(dti == 1 ? DT_BF16 : DT_F16, epi, s->tmA[dti], s->tmB[dti], g, grid, s->main);
 }
 

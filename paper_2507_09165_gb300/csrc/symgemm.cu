@@ -36,7 +36,6 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBN = 256;
-constexpr int kThreads = 192;
 
 // One swizzle row of kRowBytes16 (128) bytes of K per operand row and stage:
 // 64 K-elements for 16-bit operands, 128 for e4m3 (the same stage layout in
@@ -58,11 +57,19 @@ constexpr int kEpiWarpBytes = 3 * 32 * kH * 2;  // 7680 >= 32 * 33 * 4
 
 constexpr int kTmemCols = 512;
 
-__host__ __device__ constexpr int smem_bytes16() {
-  return 1024 /* alignment slack */ + kStages16 * kStageBytes16 + 4 * kEpiWarpBytes +
-         8 * (2 * kStages16 + 5) + 16;
+// Epilogue warps: 4 (one per 32-lane quarter of tensor memory) with a 4-stage
+// ring, or 8 (two per quarter, taking alternate 32-column chunks) with a
+// 3-stage ring.  The second form is for launches over the small blocks of a
+// block-diagonal cone, whose short tiles leave the epilogue, not the main
+// loop, as the bound (512 blocks of orders 16-1024: 6.14 -> 5.79 ms); served
+// steps, which mix in large requests, lost 12% throughput with it.
+__host__ __device__ constexpr int stages16(int ew) { return ew == 4 ? kStages16 : 3; }
+__host__ __device__ constexpr int threads16(int ew) { return 64 + 32 * ew; }
+__host__ __device__ constexpr int smem_bytes16(int ew = 4) {
+  return 1024 /* alignment slack */ + stages16(ew) * kStageBytes16 + ew * kEpiWarpBytes +
+         8 * (2 * stages16(ew) + 5) + 16;
 }
-static_assert(smem_bytes16() <= 232448, "shared memory per CTA");
+static_assert(smem_bytes16(4) <= 232448 && smem_bytes16(8) <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ uint16_t to16(float v, bool bf16) {
   return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
@@ -346,16 +353,18 @@ __device__ __forceinline__ void epilogue_chunk_final(const BlockRec& br, int r0,
   }
 }
 
-template <int EPI, bool IN8, int OUTK>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int EPI, bool IN8, int OUTK, int EW = 4>
+__global__ void __launch_bounds__(threads16(EW), 1)
     symgemm16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const GemmParams p, const int bf16_flag) {
+  static_assert(EW == 4 || (EW == 8 && EPI != EPI_FINAL), "8 epilogue warps: stage products only");
+  constexpr int kStages16 = stages16(EW);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* stages = smem;
   uint8_t* epi_stg = smem + kStages16 * kStageBytes16;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages16 * kStageBytes16 + 4 * kEpiWarpBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages16 * kStageBytes16 + EW * kEpiWarpBytes);
   // bars: full[S] | empty[S] | tfull[2] | tempty[2] | drain
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStages16 + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
@@ -376,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 4);
+      mbar_init(tempty_bar(a), EW);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -486,8 +495,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    const int ew = warp & 3;
-    uint8_t* wbuf = epi_stg + ew * kEpiWarpBytes;
+    const int ew = warp & 3;                  // tensor-memory lane quarter (warp % 4)
+    const int ewi = warp - 2;                 // epilogue warp 0 .. EW - 1
+    constexpr int kChStep = EW / 4;           // chunks of a quarter, dealt to its EW / 4 warps
+    const int ch_first = ewi / 4;
+    uint8_t* wbuf = epi_stg + ewi * kEpiWarpBytes;
     uint32_t acc = 0, acc_ph = 0;
     unsigned amax_bits = 0;  // max |output| of the current block (absmax_blocks) or of the launch
     int amax_block = -1;
@@ -525,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         else
           load_y_chunk(reinterpret_cast<const uint16_t*>(Yb), p.ep.ldy, n, r0, c0, lane, dst);
       };
-      if (EPI == EPI_POLY && ch_begin < ch_end) load_y(tc.y + 32 * ch_begin, ynext);
+      if (EPI == EPI_POLY && ch_begin + ch_first < ch_end) load_y(tc.y + 32 * (ch_begin + ch_first), ynext);
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
@@ -537,12 +549,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       ComplAcc cacc;
       ComplAcc* cap = cdst ? &cacc : nullptr;
 #pragma unroll 1
-      for (int ch = ch_begin; ch < ch_end; ++ch) {
+      for (int ch = ch_begin + ch_first; ch < ch_end; ch += kChStep) {
         const int c0 = tc.y + 32 * ch;
         uint4 ycur[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) ycur[k] = ynext[k];
-        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y(c0 + 32, ynext);
+        if (EPI == EPI_POLY && ch + kChStep < ch_end) load_y(c0 + 32 * kChStep, ynext);
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
         if (EPI == EPI_FINAL)
@@ -580,6 +592,21 @@ using Kernel16 = void (*)(const CUtensorMap, const CUtensorMap, const GemmParams
 // and 16-bit operands with e4m3 output (EPI_SCALE only: the last FP8 stage and
 // the stage before the first one); FP16 operands with an FP16 pair output
 // (EPI_COPY: Y = X^2 of the mixed precision's pair stages).
+// With 8 epilogue warps: 16-bit operands with a 16-bit or FP16-pair output,
+// COPY / POLY / SCALE.
+Kernel16 kernel16_for8(int epi, int outk) {
+  if (outk == 0)
+    return epi == EPI_COPY    ? symgemm16_kernel<EPI_COPY, false, 0, 8>
+           : epi == EPI_POLY  ? symgemm16_kernel<EPI_POLY, false, 0, 8>
+           : epi == EPI_SCALE ? symgemm16_kernel<EPI_SCALE, false, 0, 8>
+                              : nullptr;
+  if (outk == 2)
+    return epi == EPI_COPY ? symgemm16_kernel<EPI_COPY, false, 2, 8>
+           : epi == EPI_POLY ? symgemm16_kernel<EPI_POLY, false, 2, 8>
+                             : nullptr;
+  return nullptr;
+}
+
 Kernel16 kernel16_for(int epi, bool in8, int outk) {
   if (!in8 && outk == 0) {
     switch (epi) {
@@ -715,7 +742,7 @@ std::vector<int4> make_tile_list(int64_t n, int block, int group) {
 }
 
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                           const GemmParams& p, int grid, cudaStream_t stream, int out_dtype) {
+                           const GemmParams& p, int grid, cudaStream_t stream, int out_dtype, bool many_small) {
   if (p.num_tiles == 0) return cudaSuccess;
   if (dtype != DT_F16 && dtype != DT_BF16 && dtype != DT_E4M3) return cudaErrorNotSupported;
   if (out_dtype < 0) out_dtype = dtype;
@@ -723,12 +750,16 @@ cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUt
   const bool in8 = dtype == DT_E4M3;
   const int outk = epi == EPI_FINAL ? 0 : out_dtype == DT_E4M3 ? 1 : out_dtype == DT_F16X2 ? 2 : 0;
   if (outk == 2 && dtype != DT_F16) return cudaErrorNotSupported;
-  Kernel16 k = kernel16_for(epi, in8, outk);
+  // 8 epilogue warps where the launch has one (the final product keeps 4: its
+  // per-warp shares of <out, X - out> are four per tile)
+  Kernel16 k8 = many_small && !in8 ? kernel16_for8(epi, outk) : nullptr;
+  const int ew = k8 ? 8 : 4;
+  Kernel16 k = k8 ? k8 : kernel16_for(epi, in8, outk);
   if (!k) return cudaErrorNotSupported;
   static std::mutex attr_mu;  // launches come from callers' threads and the request server's
-  static bool attr_set[24] = {};
-  const int idx = epi * 6 + (in8 ? 3 : 0) + outk;
-  const int smem = smem_bytes16();
+  static bool attr_set[48] = {};
+  const int idx = (epi * 6 + (in8 ? 3 : 0) + outk) * 2 + (ew == 8 ? 1 : 0);
+  const int smem = smem_bytes16(ew);
   {
     std::lock_guard<std::mutex> lk(attr_mu);
     if (!attr_set[idx]) {
@@ -738,7 +769,7 @@ cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUt
     }
   }
   const int g = std::max(1, std::min(grid, p.num_tiles));
-  k<<<g, kThreads, smem, stream>>>(tmA, tmB, p, out_dtype == DT_BF16 ? 1 : 0);
+  k<<<g, threads16(ew), smem, stream>>>(tmA, tmB, p, out_dtype == DT_BF16 ? 1 : 0);
   return cudaGetLastError();
 }
 
