@@ -10,12 +10,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
+from oracle import emulate  # noqa: E402
 from paper_2507_09165_gb300 import binding as b  # noqa: E402
 from paper_2507_09165_gb300 import synth  # noqa: E402
 
 DEV = torch.device("cuda")
-TOL_F = {"fp16": 2e-3, "bf16": 2.5e-2, "mixed": 1e-3, "fp32": 1e-5}
-SCHED = {"fp16": "half", "bf16": "half", "mixed": "half", "fp32": "single"}
+from _bars import SCHED, TOL_F, check_all  # noqa: E402
 SIZES = [1, 7, 33, 64, 100, 128, 129, 200, 256, 300, 513, 1024]
 
 
@@ -66,19 +66,27 @@ def mats():
 def test_batched_matches_oracle(mats, prec):
     B = Batch([m for m, _ in mats])
     outs, infos = B.run(prec)
+    results = []
     for (X, ref), o, inf, n in zip(mats, outs, infos, SIZES):
         assert inf["status"] == 0, (n, inf)
         assert inf["lambda_bound"] == pytest.approx(ref["lam_tilde"], rel=1e-6)
         assert np.array_equal(o, o.T)
         F = ref["F_single"] if SCHED[prec] == "single" else ref["F"]
-        if n == 1:
-            assert abs(o[0, 0] - F[0, 0]) <= TOL_F[prec] * abs(X[0, 0]) + 1e-30
-            continue
-        rel = oracle.rel_err(o, F)
-        assert rel <= TOL_F[prec], (n, prec, rel)
         X64 = X.astype(np.float64)
+        if n == 1:
+            # n = 1: the error relative to |x| (F = phi(x) can be ~0)
+            err = abs(o[0, 0] - F[0, 0]) / abs(X64[0, 0])
+            coefs, scales = oracle.schedules.schedule(SCHED[prec])
+
+            def model(X64=X64, F=F, lt=inf["lambda_bound"]):
+                out_m, _, _ = emulate.chain_rounded(X64, lt, coefs, scales, emulate.named_plan(prec))
+                return abs(out_m[0, 0] - F[0, 0]) / abs(X64[0, 0])
+            results.append((err, None, None, "n = 1", None, model if prec != "fp32" else None))
+            continue
+        results.append((oracle.rel_err(o, F), X64, inf["lambda_bound"], "n = %d" % n))
         c_ref = float(np.sum(o * (X64 - o))) / float(np.sum(X64 * X64))
         assert abs(inf["compl_resid"] - c_ref) <= 1e-7, (n, inf["compl_resid"], c_ref)
+    check_all(prec, results)
 
 
 @pytest.mark.parametrize("prec", ["bf16", "mixed"])
@@ -108,18 +116,23 @@ def test_batched_leading_dims_and_inplace(mats):
         assert np.array_equal(a, c)
 
 
-def test_batched_config_workload_sampled():
-    # 512 Wigner blocks, orders log-uniform in [16, 1024] (seed 7); parity on a sample
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_batched_config_workload_sampled(prec):
+    # 512 Wigner blocks, orders log-uniform in [16, 1024] (seed 7); parity on a
+    # sample.  The block-diagonal workload runs in FP16, which meets the 2e-3
+    # bar on it; BF16 is checked against the same bar (a known miss).
     sizes = synth.block_sizes(512, 7)
     rng = np.random.default_rng(0)
     mats = [synth.wigner(n, 7000 + i) for i, n in enumerate(sizes)]
     B = Batch(mats)
-    outs, infos = B.run("bf16")
+    outs, infos = B.run(prec)
     assert all(inf["status"] == 0 for inf in infos)
-    for i in rng.choice(512, size=4, replace=False):
+    results = []
+    for i in rng.choice(512, size=6, replace=False):
         X = mats[i].astype(np.float64)
         ref = oracle.oracle_project(X, "half")
-        assert oracle.rel_err(outs[i], ref["F"]) <= TOL_F["bf16"]
+        results.append((oracle.rel_err(outs[i], ref["F"]), X, infos[i]["lambda_bound"], "block %d, n = %d" % (i, sizes[i])))
+    check_all(prec, results)
 
 
 def test_batched_rejects_bad_blocks():

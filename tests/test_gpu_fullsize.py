@@ -26,8 +26,7 @@ from paper_2507_09165_gb300 import synth  # noqa: E402
 
 DEV = torch.device("cuda")
 N = 10000
-TOL_F = {"fp16": 2e-3, "mixed": 1e-3, "fp32": 1e-5}
-SCHED = {"fp16": "half", "mixed": "half", "fp32": "single"}
+from _bars import SCHED, TOL_F, check_all  # noqa: E402
 GB = 1 << 30
 
 
@@ -119,32 +118,36 @@ def test_512_block_batch_sampled_blocks_and_all_properties():
     O = [torch.full_like(x, float("nan")) for x in X]
     infos = [torch.zeros(b.INFO_BYTES, dtype=torch.uint8, device=DEV) for _ in sizes]
     d = b.block_descs([(n, x, n, o, n, i) for n, x, o, i in zip(sizes, X, O, infos)])
-    b.psd_project_batched(len(sizes), d, "bf16")
+    # the block-diagonal workload runs in FP16, which meets the 2e-3 bar on it
+    b.psd_project_batched(len(sizes), d, "fp16")
     torch.cuda.synchronize()
     reps = [b.info_from_bytes(i.cpu().numpy()) for i in infos]
     for n, o, r in zip(sizes, O, reps):
         assert r["status"] == 0, (n, r)
         assert torch.equal(o, o.T)
-        assert np.isfinite(r["compl_resid"]) and abs(r["compl_resid"]) < 0.05
+        assert np.isfinite(r["compl_resid"]) and abs(r["compl_resid"]) < 0.01
     order = np.argsort(sizes)
     picks = sorted({int(order[0]), int(order[len(order) // 4]), int(order[len(order) // 2]),
                     int(order[3 * len(order) // 4]), int(order[-1])})
+    results = []
     for k in picks:
-        ref = oracle.oracle_project(mats[k].astype(np.float64), "half")
+        X64 = mats[k].astype(np.float64)
+        ref = oracle.oracle_project(X64, "half")
         assert reps[k]["lambda_bound"] == pytest.approx(ref["lam_tilde"], rel=1e-6)
         rel = oracle.rel_err(O[k].cpu().numpy().astype(np.float64), ref["F"])
-        assert rel <= 2.5e-2, (sizes[k], rel)  # the BF16 tolerance of the batched tests
+        results.append((rel, X64, reps[k]["lambda_bound"], "block %d, n = %d" % (k, sizes[k])))
+    check_all("fp16", results)
 
 
 def test_server_order_8000_served_equals_direct():
     n = 8000
     L = synth.er_laplacian(n, 8)
     V = torch.from_numpy((L - np.eye(n)).astype(np.float32)).to(DEV)  # an ADMM projection input
-    ref, r_info = project(V, "bf16")
+    ref, r_info = project(V, "fp16")
     h = b.psd_server_create(4 * GB, 0, n, 4)
     try:
         out = torch.full_like(V, float("nan"))
-        info, lat = b.psd_server_wait(h, b.psd_server_submit(h, n, V, n, out, n, "bf16"))
+        info, lat = b.psd_server_wait(h, b.psd_server_submit(h, n, V, n, out, n, "fp16"))
         assert info["status"] == 0 and lat > 0
         assert torch.equal(out, ref)
         for k in ("lambda_bound", "lanczos_sigma", "lanczos_resid", "fro_X", "overshoot_max", "compl_resid"):
