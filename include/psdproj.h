@@ -141,7 +141,9 @@ psd_status_t psd_norm_bound(int64_t n, const float *X, int64_t ld, psd_info_t *d
  * static device array of about 3 MB that every GPU loading the library holds
  * until exit.  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * capture.  The address is kept with the CUDA context it was found in and
+ * looked up again when the device's current context is another one (after
+ * cudaDeviceReset).  All calls share the array: calls whose work overlaps on the GPU
  * (different streams) race and must not be issued; calls on one stream are
  * ordered.  X, d_info: caller-owned device memory as in psd_norm_bound. */
 psd_status_t psd_norm_bound_noalloc(int64_t n, const float *X, int64_t ld, psd_info_t *d_info,
@@ -171,6 +173,16 @@ psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
                                  psd_precision_t precision, psd_stream_t stream);
 
 /* ---- Building block exposed for tests and users ------------------------- */
+/* Flags or-ed into psd_symm_product's `epi` (FP16 / BF16 operands, epi 0-2):
+ *   PSD_EPI_GROUPED: run the kernel instance the grouped launches over many
+ *     small matrices use (block-diagonal cones; 8 epilogue warps and a shallower
+ *     operand ring) -- the same arithmetic per element, so the same bits;
+ *   PSD_EPI_F16_PAIR_OUT (FP16, epi 0-1): write C as an FP16 hi/lo pair (hi
+ *     at C, lo at C + n*ld elements), the Y and P outputs of the mixed
+ *     precision. */
+#define PSD_EPI_GROUPED 0x100
+#define PSD_EPI_F16_PAIR_OUT 0x200
+
 /* Symmetric product C = epi(A * B) of two n x n symmetric matrices in the
  * chain's storage (A, B, C share the leading dimension ld, a multiple of 8;
  * pointers 16-byte aligned).  Only the upper tiles of A * B are formed on the
@@ -193,6 +205,7 @@ psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
  *     in_scale, Y by y_scale, and C is rounded (saturating) from
  *     value * out_scale.
  * params: {a, b, c} for epi 1, {s} for epi 2, {lam} for epi 3 (then the FP8 scales).
+ * epi may carry the PSD_EPI_* flags above.
  * d_absmax (may be NULL): device float receiving max |C(i,j)| (atomic max). */
 psd_status_t psd_symm_product(int64_t n, const void *A, const void *B, int64_t ld, void *C,
                               int64_t ld_out, psd_precision_t precision, int32_t epi,

@@ -207,23 +207,28 @@ def _check_extent(t, need, what):
             raise ValueError("%s holds %d bytes, the product needs %d" % (what, have, need))
 
 
+EPI_GROUPED = 0x100         # PSD_EPI_GROUPED
+EPI_F16_PAIR_OUT = 0x200    # PSD_EPI_F16_PAIR_OUT
+
+
 def psd_symm_product(n, A, B, ld, C, ld_out=0, precision="fp16", epi=0, params=(), aux=None, ld_aux=0,
                      d_absmax=None, stream=None):
     pname = precision if isinstance(precision, str) else {v: k for k, v in PRECISION.items()}.get(precision)
+    kind = epi & 0xFF  # the epilogue; the bits above are PSD_EPI_* flags
     if pname in _PRODUCT_BYTES and n > 0:
         parts, esz = _PRODUCT_BYTES[pname]
         need = ((parts - 1) * n * ld + (n - 1) * ld + n) * esz  # pairs: hi, then lo at + n * ld
         _check_extent(A, need, "A")
         _check_extent(B, need, "B")
-        if epi == 3:
+        if kind == 3:
             _check_extent(C, ((n - 1) * ld_out + n) * 4, "C (FP32 output)")
             _check_extent(aux, ((n - 1) * ld_aux + n) * 4, "aux (FP32 input)")
         else:
-            _check_extent(C, need, "C")
-            if epi == 1:
+            _check_extent(C, need + (n * ld * esz if epi & EPI_F16_PAIR_OUT else 0), "C")
+            if kind == 1:
                 _check_extent(aux, need, "aux (Y)")
-    if pname == "fp8_late" and len(params) < _FP8_PARAMS.get(epi, 0):
-        raise ValueError("fp8_late epilogue %d takes %d params" % (epi, _FP8_PARAMS[epi]))
+    if pname == "fp8_late" and len(params) < _FP8_PARAMS.get(kind, 0):
+        raise ValueError("fp8_late epilogue %d takes %d params" % (kind, _FP8_PARAMS[kind]))
     arr = (ctypes.c_double * max(1, len(params)))(*params) if params else None
     _check(lib().psd_symm_product(n, _ptr(A), _ptr(B), ld, _ptr(C), ld_out, _prec(precision), epi, arr,
                                   _ptr(aux), ld_aux, _ptr(d_absmax), _stream(stream)), "psd_symm_product")

@@ -13,8 +13,12 @@
 // the Lanczos buffers for orders up to kNoAllocMaxOrder (about 3 MB); every
 // GPU that loads the library holds it until the process exits.  In host code
 // the array's name is only a host-side stand-in, so the device address is
-// looked up with cudaGetSymbolAddress, once per device, on the first call made
-// with that device current (make that first call before any stream capture).
+// looked up with cudaGetSymbolAddress on the first call made with a device
+// current (make that first call before any stream capture).  The address is
+// kept per device together with the CUDA context it belongs to; if the
+// device's current context is a different one (the primary context was torn
+// down, e.g. by cudaDeviceReset, and the module loaded anew), it is looked up
+// again.
 //
 // All calls share the array and it keeps the last call's contents: the first
 // kernel of each call resets the device state record, and every other scratch
@@ -53,6 +57,22 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 std::mutex g_setup_mu;
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// cuCtxGetCurrent through the runtime's driver entry point (the library does
+// not link libcuda directly).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      ptr = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(ptr);
+  }();
+  return fn;
+}
 
 }  // namespace
 }  // namespace psd
@@ -73,13 +93,21 @@ extern "C" psd_status_t psd_norm_bound_noalloc(int64_t n, const float* X, int64_
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    CtxGetCurrentFn get_ctx = ctx_get_current();
+    if (!get_ctx) return PSD_ERR_CUDA;
+    // null until the runtime has made the device's primary context current on
+    // this thread; cudaGetSymbolAddress does that
+    CUcontext ctx = nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS) return PSD_ERR_CUDA;
+    if (!ctx || !g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return PSD_ERR_CUDA;
       }
+      if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return PSD_ERR_CUDA;
       g_scratch_addr[dev] = p;
+      g_scratch_ctx[dev] = ctx;
     }
     base = g_scratch_addr[dev];
   }

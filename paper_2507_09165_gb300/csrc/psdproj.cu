@@ -466,6 +466,12 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   const bool split = precision == PSD_PREC_MIXED || precision == PSD_PREC_FP32;
   const bool f8 = precision == PSD_PREC_FP8_LATE;
   if (precision != PSD_PREC_FP16 && precision != PSD_PREC_BF16 && !split && !f8) return PSD_ERR_INVALID_ARG;
+  const int flags = epi & ~0xFF;
+  epi &= 0xFF;
+  const bool grouped = (flags & PSD_EPI_GROUPED) != 0, pair_out = (flags & PSD_EPI_F16_PAIR_OUT) != 0;
+  if (flags & ~(PSD_EPI_GROUPED | PSD_EPI_F16_PAIR_OUT)) return PSD_ERR_INVALID_ARG;
+  if ((grouped || pair_out) && (split || f8 || epi == 3)) return PSD_ERR_INVALID_ARG;
+  if (pair_out && (precision != PSD_PREC_FP16 || epi == 2)) return PSD_ERR_INVALID_ARG;
   if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;
   if (f8 && (epi == 3 || (ld % 16) != 0 || !params)) return PSD_ERR_INVALID_ARG;
   if (precision == PSD_PREC_MIXED && epi == 3) return PSD_ERR_INVALID_ARG;  // FP16 pairs: epi 0-2
@@ -513,7 +519,7 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   g.tiles = ps.tiles[n];
   g.blocks = ps.d_block;
   g.ep.C = C;
-  g.ep.C_lo = split ? static_cast<uint8_t*>(C) + pair : nullptr;
+  g.ep.C_lo = (split || pair_out) ? static_cast<uint8_t*>(C) + pair : nullptr;
   g.ep.ldc = ld;
   g.ep.status = &ps.d_state->status;
   g.ep.absmax = reinterpret_cast<unsigned*>(d_absmax);
@@ -554,7 +560,7 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 256)) return PSD_ERR_CUDA;
     const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;
     g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);  // M = 128; N per tile
-    e = launch_symgemm(dtype, epi, ta, tb, g, num_sms(), s);
+    e = launch_symgemm(dtype, epi, ta, tb, g, num_sms(), s, pair_out ? DT_F16X2 : -1, grouped);
   } else {
     CUtensorMap tm[4];
     const uint8_t* a8 = static_cast<const uint8_t*>(A);

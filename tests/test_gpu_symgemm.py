@@ -309,3 +309,36 @@ def test_fp8_products(n):
     D2 = 0.5 * D
     tol2 = 2.0 ** -4 * np.abs(D2) + 2.0 ** -10 / sC + acc
     assert np.all(np.abs(C2 - D2)[iu] <= tol2[iu])
+
+
+@pytest.mark.parametrize("n", [97, 300, 513])
+@pytest.mark.parametrize("epi,out", [(e, o) for o in ("fp16", "bf16", "fp16 pair") for e in (0, 1, 2)
+                                     if not (o == "fp16 pair" and e == 2)])
+def test_grouped_instance_gives_the_same_bits(n, epi, out):
+    # The grouped launches over many small matrices (block-diagonal cones) run
+    # an instance with 8 epilogue warps, each taking every second 32-column
+    # chunk of its quarter of the tile, and a 3-stage ring; the single-matrix
+    # launches run 4 warps and a 4-stage ring.  Same arithmetic per element:
+    # the outputs must be bit-identical, for every stage epilogue, the 16-bit
+    # and the FP16-pair outputs, and orders whose chunk counts are odd.
+    prec = "bf16" if out == "bf16" else "fp16"
+    ld = (n + 7) // 8 * 8
+    dev = torch.device("cuda")
+    A = sym16(n, ld, 40 + n, prec).to(dev)
+    B = sym16(n, ld, 41 + n, prec).to(dev)
+    Y = sym16(n, ld, 42 + n, prec).to(dev)
+    flag = b.EPI_F16_PAIR_OUT if out == "fp16 pair" else 0
+    params = {0: (), 1: (4.0611848147, -2.9698947955, 0.5492133813), 2: (1 / 1.01,)}[epi]
+    rows = 2 * n if flag else n
+    outs = []
+    for grouped in (0, b.EPI_GROUPED):
+        C = torch.full((rows, ld), float("nan"), dtype=DT[prec], device=dev)
+        b.psd_symm_product(n, A, B if epi != 1 else Y, ld, C, 0, prec, epi | flag | grouped, params,
+                           Y if epi == 1 else None, ld if epi == 1 else 0)
+        torch.cuda.synchronize()
+        outs.append(C.cpu())
+    c4, c8 = outs
+    assert torch.isfinite(c4[:, :n]).all()
+    assert torch.equal(c4.view(torch.int16), c8.view(torch.int16))
+    if flag:  # the pair carries more than the single FP16 rounding: lo is not all zero
+        assert torch.count_nonzero(c4[n:, :n]) > n
