@@ -14,7 +14,7 @@ namespace psd {
 constexpr int kMaxSteps = 20;     // Lanczos steps (Sec. 3.4, Algorithm 2)
 constexpr int kMaxStages = 10;    // T <= 10 (Table 1)
 constexpr int kSymvTile = 128;    // Lanczos mat-vec tile
-constexpr int kVecThreads = 64;   // threads per CTA of the Lanczos vector kernels
+constexpr int kVecThreads = 256;  // elements (threads) per block of the Lanczos vector phases
 constexpr int64_t kMaxOrder = 131072;
 constexpr double kBreakdown = 1e-12;       // beta_j <= 1e-12 ||X||_F^2: invariant subspace
 constexpr float kOvershootLimit = 1.01f;   // max |X_T(i,j)| above this: bound too small
@@ -263,16 +263,22 @@ struct LanczosBufs {
   float* vl;             // npad  lo part
   float2* P1;            // nb x npad row partials
   float2* P2;            // nb x npad column partials
-  double* dots;          // npart x 32 partial dot products
-  double* dots2;         // nvec_ctas x 32
-  double* norms;         // npart (>= nvec_ctas)
+  float2* dots;          // npart x 32 double-float partial dot products (one chunk of 32 elements each)
+  float2* dots2;         // npart x 32 (second Gram-Schmidt pass; slot 31: ||w||^2)
+  double* norms;         // max(npart, nvec_ctas) partial squared norms
   double* tile_fro;      // ntiles
   double* zsave = nullptr;  // if set: X q_j of Lanczos step j kept at zsave + j npad (kMaxSteps x npad)
+  unsigned* sync;        // 2 words: grid barrier of the persistent kernel (zeroed before each launch)
 };
 size_t lanczos_bytes(int64_t n);
 void lanczos_carve(LanczosBufs& b, int64_t n, uint8_t* base);
+// persistent: the whole bound as one cooperative persistent kernel (grid
+// barriers between the phases); otherwise 151 launches (kNormBoundLaunches)
+// that can share the GPU with other work -- the request server's preparation
+// streams run beside product kernels that leave no room for a co-resident
+// grid.  Both paths give identical results.
 cudaError_t enqueue_norm_bound(const LanczosBufs& b, const DevArgs* args, DevState* st,
-                               cudaStream_t stream);
+                               cudaStream_t stream, bool persistent = true);
 // Frees the cached plans of psd_project_deflate (device synchronised by the caller).
 void release_deflate_plans();
 // X_0 = X / lam~ as `dtype` (DT_F16, DT_BF16, or DT_TF32X3 with M = hi, M_lo = lo).
@@ -306,9 +312,9 @@ __device__ __forceinline__ void finalize_report(DevState* st, psd_info_t* info) 
   }
 }
 
-// Kernel launches of one enqueue_norm_bound: start vector (2), the Lanczos
-// steps (7 each, plus the Frobenius norm in the first), the tridiagonal
-// solve, Ritz vector and residual (8).
-constexpr int kNormBoundLaunches = 2 + 7 * kMaxSteps + 1 + 8;
+// Kernel launches of one multi-launch enqueue_norm_bound: start vector (2),
+// the Lanczos steps (6 each, plus the Frobenius norm in the first), the
+// tridiagonal solve, Ritz vector and residual (8).
+constexpr int kNormBoundLaunches = 2 + 6 * kMaxSteps + 1 + 8;
 
 }  // namespace psd

@@ -42,11 +42,11 @@ constexpr size_t lanczos_bound_bytes(int64_t n) {
   const size_t npad = static_cast<size_t>((n + 255) / 256 * 256);
   const size_t nb = static_cast<size_t>((n + 127) / 128);
   const size_t ntiles = nb * (nb + 1) / 2;
-  const size_t nctas = static_cast<size_t>((n + 63) / 64);
+  const size_t nctas = static_cast<size_t>((n + kVecThreads - 1) / kVecThreads);
   const size_t npart = static_cast<size_t>((n + 31) / 32);
   return round256(8 * 21 * npad) + round256(8 * 3 * npad) + round256(4 * 2 * npad) +
-         round256(8 * 2 * nb * npad) + round256(8 * 32 * npart) + round256(8 * 32 * nctas) +
-         round256(8 * npart) + round256(8 * ntiles);
+         round256(8 * 2 * nb * npad) + round256(8 * 32 * npart) + round256(8 * 32 * npart) +
+         round256(8 * (npart > nctas ? npart : nctas)) + round256(8 * ntiles) + round256(4 * 2);
 }
 
 constexpr size_t kNoAllocBytes = kRecordBytes + lanczos_bound_bytes(kNoAllocMaxOrder);

@@ -302,7 +302,9 @@ cudaGraphExec_t norm_bound_graph(psd_server* s, int lane, int64_t n) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    const cudaError_t e = enqueue_norm_bound(L, args, st, cs);
+    // the multi-launch form: these lanes run beside the step's product kernels,
+    // which leave no room for a co-resident persistent grid
+    const cudaError_t e = enqueue_norm_bound(L, args, st, cs, false);
     const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess)
       exec = nullptr;
