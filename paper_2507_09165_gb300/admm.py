@@ -92,7 +92,7 @@ class Solve:
         return max(pinf, dinf, gap), dict(pinf=pinf, dinf=dinf, gap=gap, pobj=pobj, dobj=dobj)
 
 
-def run_serving(server, graphs, precision="bf16", solve_rate=8.0, arrival_seconds=2.5, iters=50,
+def run_serving(server, graphs, precision="fp16", solve_rate=8.0, arrival_seconds=2.5, iters=50,
                 think_ms=0.5, seed=0, sigma_range=(0.5, 2.0), max_solves=None):
     """Interleaved ADMM solves as a request stream against a psd_server.
 
@@ -176,8 +176,13 @@ def summarize(result):
                tflops=flops / wall / 1e12 if wall > 0 else 0.0,
                bad_status=sum(1 for r in recs if r["status"] != 0))
     if result["solves"]:
+        sizes = sorted({s["n"] for s in result["solves"]})
         out["eta_median_by_n"] = {str(n): float(np.median([s["eta"] for s in result["solves"] if s["n"] == n]))
-                                  for n in sorted({s["n"] for s in result["solves"]})}
+                                  for n in sizes}
+        # the surrogate's parts (Sec. 5): primal and dual infeasibility, relative gap
+        out["eta_parts_median_by_n"] = {
+            str(n): {k: float(np.median([s[k] for s in result["solves"] if s["n"] == n]))
+                     for k in ("pinf", "dinf", "gap")} for n in sizes}
     return out
 
 

@@ -18,7 +18,7 @@ def test_served_admm_matches_direct_calls():
     iters = 12
     server = b.psd_server_create(1 << 30, 0, 512, 16)
     try:
-        res = admm.run_serving(server, graphs, "bf16", solve_rate=400.0, arrival_seconds=0.02, iters=iters,
+        res = admm.run_serving(server, graphs, "fp16", solve_rate=400.0, arrival_seconds=0.02, iters=iters,
                                think_ms=0.2, seed=3, max_solves=6)
     finally:
         b.psd_server_destroy(server)
@@ -32,7 +32,7 @@ def test_served_admm_matches_direct_calls():
         for _ in range(iters):
             V = sv.make_input()
             torch.cuda.synchronize()
-            b.psd_project(sv.n, V, sv.n, sv.S, "bf16")
+            b.psd_project(sv.n, V, sv.n, sv.S, "fp16")
             torch.cuda.synchronize()
             sv.finish_iteration()
         eta, _ = sv.surrogate()
