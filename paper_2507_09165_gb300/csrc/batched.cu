@@ -221,7 +221,8 @@ psd_status_t build_bplan(BatchPlan* p) {
   const size_t o_cres = o_cast + rup(sizeof(int4) * cast.size(), 256);
   const size_t o_cidx = o_cres + rup(sizeof(double) * 4 * std::max<size_t>(tiles.size(), 1), 256);
   const size_t o_crange = o_cidx + rup(sizeof(int) * std::max<size_t>(tiles.size(), 1), 256);
-  const size_t smallb = o_crange + rup(sizeof(int2) * count, 256);
+  const size_t o_order = o_crange + rup(sizeof(int2) * count, 256);
+  const size_t smallb = o_order + rup(sizeof(int) * count, 256);
   if (cudaMalloc(&p->small, smallb) != cudaSuccess) {
     cudaGetLastError();
     p->small = nullptr;
@@ -238,14 +239,21 @@ psd_status_t build_bplan(BatchPlan* p) {
   p->d_cres = reinterpret_cast<double*>(p->small + o_cres);
   p->d_cidx = reinterpret_cast<int*>(p->small + o_cidx);
   p->d_crange = reinterpret_cast<int2*>(p->small + o_crange);
+  int* d_order = reinterpret_cast<int*>(p->small + o_order);
+  // per-block kernels take the blocks largest first (the longest CTAs start first)
+  std::vector<int> order(count);
+  for (int b = 0; b < count; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p->sizes[x] > p->sizes[y]; });
   for (int b = 0; b < count; ++b) rec[b].st = p->d_st + b;
   bool ok = cudaMemcpy(p->d_rec, rec.data(), sizeof(BlockRec) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(p->d_bb, bb.data(), sizeof(BatchBlock) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) ==
                 cudaSuccess &&
             cudaMemcpy(p->d_symv, symv.data(), sizeof(int4) * symv.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(p->d_cast, cast.data(), sizeof(int4) * cast.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+            cudaMemcpy(p->d_cast, cast.data(), sizeof(int4) * cast.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) return PSD_ERR_CUDA;
+  p->L.order = d_order;
   p->L.blk = p->d_bb;
   p->L.st = p->d_st;
   p->L.skip_done = 0;

@@ -6,9 +6,12 @@
 // (same per-tile arithmetic as the single-matrix kernel: 8-term FP32 FMA runs
 // combined exactly into double-float partial sums); every vector operation of
 // a block -- the Lanczos recurrence with full re-orthogonalisation, the Ritz
-// vector, the residual and the bound -- runs in one CTA per block in FP64 with
-// a fixed reduction order, so a block's result does not depend on the other
-// blocks of the batch.
+// vector, the residual and the bound -- runs in one CTA per block with a fixed
+// reduction order, so a block's result does not depend on the other blocks of
+// the batch.  The Lanczos vectors and their arithmetic are double-float (an
+// FP32 pair hi + lo, about 48 significant bits: Dekker's products and Knuth's
+// TwoSum): this GPU issues a warp's FP64 instruction every ~19 cycles per SM,
+// and a block's whole step runs on one SM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -40,13 +43,36 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
   return F2{s, __fadd_rn(__fadd_rn(a.l, b.l), e)};
 }
 __device__ __forceinline__ double f2_to_d(F2 a) { return static_cast<double>(a.h) + static_cast<double>(a.l); }
-__device__ __forceinline__ void split_d(double v, float& h, float& l) {
-  h = __double2float_rn(v);
-  l = __double2float_rn(v - static_cast<double>(h));
-}
 __device__ __forceinline__ F2 shfl_xor_f2(F2 a, int m) {
   return F2{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
 }
+// Normalised double-float arithmetic (hi = RN(hi + lo)).
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 df_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ F2 df_neg(F2 a) { return F2{-a.h, -a.l}; }
+__device__ __forceinline__ F2 df_from_d(double v) {
+  const float h = __double2float_rn(v);
+  return F2{h, __double2float_rn(v - static_cast<double>(h))};
+}
+__device__ __forceinline__ F2 ld_f2(const float2* p) {
+  const float2 t = *p;
+  return F2{t.x, t.y};
+}
+__device__ __forceinline__ void st_f2(float2* p, F2 a) { *p = make_float2(a.h, a.l); }
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
   uint64_t z = seed + (i + 1) * kGolden;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -67,10 +93,23 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
   return s;
 }
 
+// Fixed-order double-float sum over the CTA (kBT threads); every thread gets it.
+__device__ __forceinline__ F2 cta_sum_df(F2 v, F2* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_xor_f2(v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  F2 s = sh[0];
+#pragma unroll
+  for (int k = 1; k < kBT / 32; ++k) s = df_add(s, sh[k]);
+  return s;
+}
+
 // Per-block views of the batched Lanczos buffers.
 struct BView {
   int n, nb;
-  double* Q;   // (kMaxSteps + 1) x n
+  float2* Q;   // (kMaxSteps + 1) x n Lanczos vectors, double-float
   double* u;   // n
   double* w;   // n
   double* q;   // n
@@ -84,7 +123,7 @@ __device__ __forceinline__ BView view_of(const BatchLanczos& L, const BatchBlock
   v.n = bb.n;
   v.nb = (bb.n + kSymvTile - 1) / kSymvTile;
   double* base = L.vec64 + bb.voff * (kMaxSteps + 4);
-  v.Q = base;
+  v.Q = reinterpret_cast<float2*>(base);  // same 8 bytes per element
   v.u = base + static_cast<int64_t>(kMaxSteps + 1) * bb.n;
   v.w = v.u + bb.n;
   v.q = v.w + bb.n;
@@ -223,18 +262,24 @@ __global__ void __launch_bounds__(256) bpack_kernel(BatchLanczos L, const int4* 
 }
 
 // work item: (block, bi, bj, tile slot of the block's tile_fro entries)
+// `reverse` deals the items to the CTAs in the opposite order: consecutive
+// products alternate direction, so each starts on the packed tiles the
+// previous one read last, still in L2 (the packed tiles of a large batch
+// exceed L2).  The item -> partial slot mapping does not change: results are
+// identical.
 template <bool STATS>
-__global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int4* __restrict__ items) {
+__global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int4* __restrict__ items, int reverse) {
   __shared__ float2 red[8][kSymvTile];
   __shared__ double fro_sh[8];
-  const int4 it = items[blockIdx.x];
+  const int idx = reverse ? static_cast<int>(gridDim.x) - 1 - static_cast<int>(blockIdx.x) : static_cast<int>(blockIdx.x);
+  const int4 it = items[idx];
   const int b = it.x;
   // the block record and the done flag are independent loads: issue both
   // before the branch
   const BatchBlock bb = L.blk[b];
   const int done = L.st[b].done;
   const BView v = view_of(L, bb);
-  const float* T = L.xt + static_cast<int64_t>(blockIdx.x) * kSymvTile * kSymvTile;
+  const float* T = L.xt + static_cast<int64_t>(idx) * kSymvTile * kSymvTile;
   if (done && !STATS && L.skip_done) return;
   if (it.y == it.z)
     bsymv_tile<STATS, true>(T, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
@@ -244,49 +289,61 @@ __global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int
                              &L.st[b].maxdiag_bits, red, fro_sh);
 }
 
-// y_e of block b from its partial sums (fixed order, double-float), e < n.
-__device__ __forceinline__ double bred(const BView& v, int e) {
+// y_e of block b from its partial sums (fixed order, double-float, normalised), e < n:
+// P1 of the tiles bj = b(e) .. nb - 1, then P2 of bi = 0 .. b(e).  All (at most
+// 2 kMaxBatchOrder / 128) loads are issued before the additions.
+constexpr int kMaxTileBlocks = kMaxBatchOrder / kSymvTile;
+__device__ __forceinline__ F2 bred(const BView& v, int e) {
   const int bk = e / kSymvTile;
+  float2 p1[kMaxTileBlocks], p2[kMaxTileBlocks];
+#pragma unroll
+  for (int i = 0; i < kMaxTileBlocks; ++i) {
+    const int bj = bk + i, bi = i;
+    p1[i] = bj < v.nb ? v.P1[static_cast<int64_t>(bj) * v.n + e] : make_float2(0.f, 0.f);
+    p2[i] = bi <= bk ? v.P2[static_cast<int64_t>(bi) * v.n + e] : make_float2(0.f, 0.f);
+  }
   F2 a{0.f, 0.f};
-  for (int bj = bk; bj < v.nb; ++bj) {
-    const float2 t = v.P1[static_cast<int64_t>(bj) * v.n + e];
-    a = f2_add(a, F2{t.x, t.y});
-  }
-  for (int bi = 0; bi <= bk; ++bi) {
-    const float2 t = v.P2[static_cast<int64_t>(bi) * v.n + e];
-    a = f2_add(a, F2{t.x, t.y});
-  }
-  return f2_to_d(a);
+#pragma unroll
+  for (int i = 0; i < kMaxTileBlocks; ++i)
+    if (bk + i < v.nb) a = f2_add(a, F2{p1[i].x, p1[i].y});
+#pragma unroll
+  for (int i = 0; i < kMaxTileBlocks; ++i)
+    if (i <= bk) a = f2_add(a, F2{p2[i].x, p2[i].y});
+  return fast_two_sum(a.h, a.l);
 }
 
 // ------------------------------------------------------------ per-block CTAs
 // Start vector (SplitMix64, normalised), state reset, split for the first product.
 __global__ void __launch_bounds__(kBT) binit_kernel(BatchLanczos L) {
-  __shared__ double sh[kBT / 32];
-  const int b = blockIdx.x;
+  __shared__ F2 sh[kBT / 32];
+  __shared__ double inv_sh;
+  const int b = L.order[blockIdx.x];
   const BView v = view(L, b);
-  double loc[kEPT];
-  double s = 0.0;
+  F2 loc[kEPT];
+  F2 s{0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
     const int e = threadIdx.x + k * kBT;
-    double x = 0.0;
+    F2 x{0.f, 0.f};
     if (e < v.n) {
       const uint64_t z = splitmix64(kSeed, static_cast<uint64_t>(e));
-      x = 2.0 * (static_cast<double>(z >> 11) * 0x1.0p-53) - 1.0;
+      x = df_from_d(2.0 * (static_cast<double>(z >> 11) * 0x1.0p-53) - 1.0);
     }
     loc[k] = x;
-    s += x * x;
+    s = df_add(s, df_mul(x, x));
   }
-  const double nrm2 = cta_sum(s, sh);
-  const double inv = 1.0 / sqrt(nrm2);
+  const F2 nrm2 = cta_sum_df(s, sh);
+  if (threadIdx.x == 0) inv_sh = 1.0 / sqrt(static_cast<double>(nrm2.h) + static_cast<double>(nrm2.l));
+  __syncthreads();
+  const F2 inv = df_from_d(inv_sh);
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
     const int e = threadIdx.x + k * kBT;
     if (e < v.n) {
-      const double q = loc[k] * inv;
-      v.Q[e] = q;
-      split_d(q, v.vh[e], v.vl[e]);
+      const F2 q = df_mul(loc[k], inv);
+      st_f2(v.Q + e, q);
+      v.vh[e] = q.h;
+      v.vl[e] = q.l;
     }
   }
   if (threadIdx.x == 0) {
@@ -302,7 +359,7 @@ __global__ void __launch_bounds__(kBT) binit_kernel(BatchLanczos L) {
 
 // ||X_b||_F from the block's tile sums (after the first product).
 __global__ void bfro_kernel(BatchLanczos L) {
-  const int b = blockIdx.x;
+  const int b = L.order[blockIdx.x];
   const BatchBlock& bb = L.blk[b];
   double f = 0.0;
   for (int t = threadIdx.x; t < bb.ntiles; t += 32) f += L.tile_fro[bb.toff + t];
@@ -313,110 +370,119 @@ __global__ void bfro_kernel(BatchLanczos L) {
 
 // u = X v: reduce, store, split for the second product.  MODE 1: Ritz pass (no done check).
 __global__ void __launch_bounds__(kBT) breduce_kernel(BatchLanczos L, int mode) {
-  const int b = blockIdx.x;
+  const int b = L.order[blockIdx.x];
   if (mode == 0 && L.st[b].done) return;
   const BView v = view(L, b);
   for (int e = threadIdx.x; e < v.n; e += kBT) {
-    const double y = bred(v, e);
-    v.u[e] = y;
-    split_d(y, v.vh[e], v.vl[e]);
+    const F2 y = bred(v, e);
+    v.u[e] = f2_to_d(y);
+    v.vh[e] = y.h;
+    v.vl[e] = y.l;
   }
 }
 
 // Lanczos step j after w = X u: alpha_j, two classical Gram-Schmidt passes
 // (all j + 1 projections of a pass reduced together), beta_j, breakdown test,
-// q_{j+1} = w / beta_j and its split.  GB300's FP64 pipe is narrow (a warp's
-// FP64 instruction occupies it for 16 cycles), so the step spends FP64 work
-// only where it is needed: warps that own no element add zeros without
-// arithmetic, and the cross-lane sum of the j + 1 partial dots halves only
-// over V = 2^ceil(log2(j + 1)) values (then a plain butterfly), not all 32.
-// Every reduction has a fixed order that depends on j alone, so a block's
-// result does not depend on the rest of the batch.
+// q_{j+1} = w / beta_j and its split, in double-float arithmetic.  Warps that
+// own no element add zeros without arithmetic, and the cross-lane sum of the
+// j + 1 partial dots halves only over V = 2^ceil(log2(j + 1)) values (then a
+// plain butterfly), not all 32.  Every reduction has a fixed order that
+// depends on j alone, so a block's result does not depend on the rest of the
+// batch.
 
 // Sum over the CTA (kBT threads) of v[k], k <= j, into out[k]: recursive
 // halving over V values inside each warp (lane l ends with value l mod V,
 // summed over its V-lane group), a butterfly over the 32 / V groups, then the
 // warp sums of value k added in order by thread k.
-__device__ __forceinline__ void cta_multi_sum(const double (&v)[kMaxSteps + 1], int j, bool warp_active,
-                                              double (*sh)[32], double* out) {
+__device__ __forceinline__ void cta_multi_sum(const F2 (&v)[kMaxSteps + 1], int j, bool warp_active,
+                                              F2 (*sh)[32], F2* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (warp_active) {
     int V = 1;
     while (V < j + 1) V <<= 1;  // uniform across the CTA
-    double t[32];
+    F2 t[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) t[k] = (k <= j && k <= kMaxSteps) ? v[k <= kMaxSteps ? k : 0] : 0.0;
+    for (int k = 0; k < 32; ++k) t[k] = (k <= j && k <= kMaxSteps) ? v[k <= kMaxSteps ? k : 0] : F2{0.f, 0.f};
 #pragma unroll
     for (int half = 16, m = 16; half >= 1; half >>= 1, m >>= 1) {
       if (half >= V) continue;  // values >= V are zero: skip the exchange
       const bool upper = (lane & m) != 0;
 #pragma unroll
       for (int i = 0; i < half; ++i) {
-        const double send = upper ? t[i] : t[i + half];
-        const double keep = upper ? t[i + half] : t[i];
-        t[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        const F2 send = upper ? t[i] : t[i + half];
+        const F2 keep = upper ? t[i + half] : t[i];
+        t[i] = df_add(keep, shfl_xor_f2(send, m));
       }
     }
     // lanes l and l ^ (V, 2V, ...) hold the same value index: butterfly over them
-    for (int m = V; m < 32; m <<= 1) t[0] += __shfl_xor_sync(0xffffffffu, t[0], m);
+    for (int m = V; m < 32; m <<= 1) t[0] = df_add(t[0], shfl_xor_f2(t[0], m));
     sh[w][lane] = t[0];
   } else {
-    sh[w][lane] = 0.0;
+    sh[w][lane] = F2{0.f, 0.f};
   }
   __syncthreads();
   if (threadIdx.x <= j) {
-    double s = 0.0;
+    F2 s = sh[0][threadIdx.x];
 #pragma unroll
-    for (int q = 0; q < kBT / 32; ++q) s += sh[q][threadIdx.x];
+    for (int q = 1; q < kBT / 32; ++q) s = df_add(s, sh[q][threadIdx.x]);
     out[threadIdx.x] = s;
   }
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
-  __shared__ double sh[kBT / 32][32];
-  __shared__ double h[32];
-  __shared__ double shs[kBT / 32];
-  const int b = blockIdx.x;
+  __shared__ F2 sh[kBT / 32][32];
+  __shared__ F2 h[32];
+  __shared__ F2 shs[kBT / 32];
+  __shared__ double beta_sh[2];
+  const int b = L.order[blockIdx.x];
   DevState* st = &L.st[b];
   if (st->done) return;
   const BView v = view(L, b);
   const bool any = (threadIdx.x & ~31) < v.n;  // the warp owns an element
-  double w[kEPT];
+  F2 w[kEPT];
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
     const int e = threadIdx.x + k * kBT;
-    w[k] = e < v.n ? bred(v, e) : 0.0;
+    w[k] = e < v.n ? bred(v, e) : F2{0.f, 0.f};
   }
   for (int pass = 0; pass < 2; ++pass) {
-    double d[kMaxSteps + 1];
+    F2 d[kMaxSteps + 1];
 #pragma unroll
-    for (int kk = 0; kk <= kMaxSteps; ++kk) d[kk] = 0.0;
+    for (int kk = 0; kk <= kMaxSteps; ++kk) d[kk] = F2{0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) {
       const int e = threadIdx.x + k * kBT;
       if (e < v.n) {
 #pragma unroll
         for (int kk = 0; kk <= kMaxSteps; ++kk)
-          if (kk <= j) d[kk] += v.Q[static_cast<int64_t>(kk) * v.n + e] * w[k];
+          if (kk <= j) d[kk] = df_add(d[kk], df_mul(ld_f2(v.Q + static_cast<int64_t>(kk) * v.n + e), w[k]));
       }
     }
     cta_multi_sum(d, j, any, sh, h);
-    if (pass == 0 && threadIdx.x == 0) st->alpha[j] = h[j];
+    if (pass == 0 && threadIdx.x == 0) st->alpha[j] = f2_to_d(h[j]);
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) {
       const int e = threadIdx.x + k * kBT;
       if (e < v.n)
-        for (int kk = 0; kk <= j; ++kk) w[k] -= h[kk] * v.Q[static_cast<int64_t>(kk) * v.n + e];
+        for (int kk = 0; kk <= j; ++kk)
+          w[k] = df_add(w[k], df_neg(df_mul(h[kk], ld_f2(v.Q + static_cast<int64_t>(kk) * v.n + e))));
     }
     __syncthreads();  // h is rewritten by the next pass
   }
-  double s = 0.0;
+  F2 s{0.f, 0.f};
   if (any) {
 #pragma unroll
-    for (int k = 0; k < kEPT; ++k) s += w[k] * w[k];
+    for (int k = 0; k < kEPT; ++k) s = df_add(s, df_mul(w[k], w[k]));
   }
-  const double beta = sqrt(cta_sum(s, shs));
+  const F2 nrm2 = cta_sum_df(s, shs);
+  if (threadIdx.x == 0) {  // FP64 scalar work once per block
+    const double bt = sqrt(f2_to_d(nrm2));
+    beta_sh[0] = bt;
+    beta_sh[1] = 1.0 / bt;
+  }
+  __syncthreads();
+  const double beta = beta_sh[0];
   const double fro = st->fro;
   const bool brk = !(beta > kBreakdown * fro * fro);
   if (brk || j == kMaxSteps - 1) {
@@ -431,14 +497,15 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
     st->beta[j] = beta;
     st->m = j + 1;
   }
-  const double inv = 1.0 / beta;
+  const F2 inv = df_from_d(beta_sh[1]);
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
     const int e = threadIdx.x + k * kBT;
     if (e < v.n) {
-      const double q = w[k] * inv;
-      v.Q[static_cast<int64_t>(j + 1) * v.n + e] = q;
-      split_d(q, v.vh[e], v.vl[e]);
+      const F2 q = df_mul(w[k], inv);
+      st_f2(v.Q + static_cast<int64_t>(j + 1) * v.n + e, q);
+      v.vh[e] = q.h;
+      v.vl[e] = q.l;
     }
   }
 }
@@ -449,8 +516,10 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
 __global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
   __shared__ double y[kMaxSteps];
   __shared__ float a32[kMaxSteps], b32[kMaxSteps];
-  __shared__ double sh[kBT / 32];
-  const int b = blockIdx.x;
+  __shared__ F2 sh[kBT / 32];
+  __shared__ F2 yf[kMaxSteps];
+  __shared__ double inv_sh;
+  const int b = L.order[blockIdx.x];
   DevState* st = &L.st[b];
   const int m = st->m;
   if (threadIdx.x < 32) {
@@ -460,28 +529,35 @@ __global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
       for (int k = 0; k < kMaxSteps; ++k) st->y[k] = y[k];
     }
   }
+  if (threadIdx.x < kMaxSteps) yf[threadIdx.x] = df_from_d(y[threadIdx.x]);
   __syncthreads();
   const BView v = view(L, b);
-  double qv[kEPT];
-  double s = 0.0;
+  F2 qv[kEPT];
+  F2 s{0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
     const int e = threadIdx.x + k * kBT;
-    double t = 0.0;
+    F2 t{0.f, 0.f};
     if (e < v.n)
-      for (int kk = 0; kk < m; ++kk) t += y[kk] * v.Q[static_cast<int64_t>(kk) * v.n + e];
+      for (int kk = 0; kk < m; ++kk) t = df_add(t, df_mul(yf[kk], ld_f2(v.Q + static_cast<int64_t>(kk) * v.n + e)));
     qv[k] = t;
-    s += t * t;
+    s = df_add(s, df_mul(t, t));
   }
-  const double nrm2 = cta_sum(s, sh);
-  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+  const F2 nrm2 = cta_sum_df(s, sh);
+  if (threadIdx.x == 0) {
+    const double n2 = f2_to_d(nrm2);
+    inv_sh = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  }
+  __syncthreads();
+  const F2 inv = df_from_d(inv_sh);
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
     const int e = threadIdx.x + k * kBT;
     if (e < v.n) {
-      const double t = qv[k] * inv;
-      v.q[e] = t;
-      split_d(t, v.vh[e], v.vl[e]);
+      const F2 t = df_mul(qv[k], inv);
+      v.q[e] = f2_to_d(t);
+      v.vh[e] = t.h;
+      v.vl[e] = t.l;
     }
   }
 }
@@ -489,12 +565,12 @@ __global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
 // r = ||X (X q) - sigma q||, lam~ = max(sqrt(sigma + r), ||X||_F / sqrt n, max |X_ii|), report.
 __global__ void __launch_bounds__(kBT) bbound_kernel(BatchLanczos L) {
   __shared__ double sh[kBT / 32];
-  const int b = blockIdx.x;
+  const int b = L.order[blockIdx.x];
   DevState* st = &L.st[b];
   const BView v = view(L, b);
   double s = 0.0;
   for (int e = threadIdx.x; e < v.n; e += kBT) {
-    const double r = bred(v, e) - st->sigma * v.q[e];
+    const double r = f2_to_d(bred(v, e)) - st->sigma * v.q[e];
     s += r * r;
   }
   const double r2 = cta_sum(s, sh);
@@ -663,24 +739,25 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
   Lk.skip_done = 0;
   bpack_kernel<<<nsymv, 256, 0, s>>>(Lk, symv_items);
   binit_kernel<<<count, kBT, 0, s>>>(Lk);
+  int pass = 0;  // products so far: odd ones traverse the items backwards
   for (int j = 0; j < kMaxSteps; ++j) {
     Lk.skip_done = j == 0 ? 0 : 1;
     if (j == 0) {
-      bsymv_kernel<true><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+      bsymv_kernel<true><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
       bfro_kernel<<<count, 32, 0, s>>>(Lk);
     } else {
-      bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+      bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
     }
     breduce_kernel<<<count, kBT, 0, s>>>(Lk, 0);
     Lk.skip_done = 1;
-    bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+    bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
     bstep_kernel<<<count, kBT, 0, s>>>(Lk, j);
   }
   britz_kernel<<<count, kBT, 0, s>>>(Lk);
   Lk.skip_done = 0;
-  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
   breduce_kernel<<<count, kBT, 0, s>>>(Lk, 1);
-  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items);
+  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
   bbound_kernel<<<count, kBT, 0, s>>>(Lk);
   return cudaGetLastError();
 }

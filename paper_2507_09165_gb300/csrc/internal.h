@@ -230,6 +230,8 @@ struct BatchLanczos {
   float2* part;           // per block: 2 x nb x n  (row / column partial sums)
   double* tile_fro;       // per mat-vec tile
   float* xt;              // per mat-vec tile: the block's 128 x 128 tile, packed (64 KB)
+  const int* order;       // per-block kernels: CTA i works on block order[i] (largest blocks first,
+                          // so that they start in the first wave of CTAs)
   int skip_done;
 };
 
