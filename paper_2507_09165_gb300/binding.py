@@ -209,6 +209,7 @@ def _check_extent(t, need, what):
 
 EPI_GROUPED = 0x100         # PSD_EPI_GROUPED
 EPI_F16_PAIR_OUT = 0x200    # PSD_EPI_F16_PAIR_OUT
+EPI_CTA_PAIR = 0x400        # PSD_EPI_CTA_PAIR
 
 
 def psd_symm_product(n, A, B, ld, C, ld_out=0, precision="fp16", epi=0, params=(), aux=None, ld_aux=0,

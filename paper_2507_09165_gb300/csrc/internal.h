@@ -199,6 +199,13 @@ bool encode_tmap(CUtensorMap* map, int dtype, const void* base, int64_t n, int64
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1,
                            bool many_small = false);
+// The same product on CTA pairs (tcgen05.mma.cta_group::2, M = 256): tiles
+// from make_tile_list_pair, tmB with 128-row boxes (each CTA loads half of
+// B), p.idesc with M = 256; 16-bit operands; EPI_COPY / EPI_POLY / EPI_SCALE
+// with a 16-bit (out_dtype = dtype or -1) or FP16-pair output.
+std::vector<int4> make_tile_list_pair(int64_t n, int block = 0, int group = 8);
+cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                                const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1);
 // split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
 // out: 0 = split pair, 1 = single FP16, (EPI_FINAL) FP32 to the caller's output.
 // Split-operand products: et = DT_TF32X3 (TF32 pairs) or DT_F16X2 (FP16

@@ -127,6 +127,8 @@ struct Plan {
   BlockRec* d_block = nullptr;   // the one block of a single projection
   int4* d_tiles = nullptr;
   int ntiles = 0;
+  int4* d_tiles_pair = nullptr;  // 256-row tiles of the CTA-pair form of the 16-bit stage products
+  int ntiles_pair = 0;
   double* d_compl = nullptr;  // 4 per tile: shares of <out, X - out> from the final product
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
@@ -176,8 +178,11 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   const size_t o_info = o_state + round_up(sizeof(DevState), 256);
   const size_t o_block = o_info + round_up(sizeof(psd_info_t), 256);
   const size_t o_tiles = o_block + round_up(sizeof(BlockRec), 256);
+  std::vector<int4> tiles_pair = make_tile_list_pair(n);
+  p->ntiles_pair = static_cast<int>(tiles_pair.size());
   const size_t o_compl = o_tiles + round_up(sizeof(int4) * std::max<size_t>(tiles.size(), 1), 256);
-  const size_t small = o_compl + sizeof(double) * 4 * std::max<size_t>(tiles.size(), 1);
+  const size_t o_pair = o_compl + round_up(sizeof(double) * 4 * std::max<size_t>(tiles.size(), 1), 256);
+  const size_t small = o_pair + sizeof(int4) * std::max<size_t>(tiles_pair.size(), 1);
   uint8_t* sm = nullptr;
   if (cudaMalloc(&sm, small) != cudaSuccess) {
     cudaGetLastError();
@@ -190,8 +195,12 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   p->d_block = reinterpret_cast<BlockRec*>(sm + o_block);
   p->d_tiles = reinterpret_cast<int4*>(sm + o_tiles);
   p->d_compl = reinterpret_cast<double*>(sm + o_compl);
+  p->d_tiles_pair = reinterpret_cast<int4*>(sm + o_pair);
   if (!tiles.empty() &&
       cudaMemcpy(p->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PSD_ERR_CUDA;
+  if (!tiles_pair.empty() && cudaMemcpy(p->d_tiles_pair, tiles_pair.data(), sizeof(int4) * tiles_pair.size(),
+                                        cudaMemcpyHostToDevice) != cudaSuccess)
     return PSD_ERR_CUDA;
   BlockRec br{};
   br.off = 0;
@@ -243,6 +252,18 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
   const GemmRoute route = gemm_route(A, B);
   if (route == ROUTE_16) {
     const int dt = kind_dtype(A);
+    const int odt = out ? kind_dtype(*out) : -1;
+    if (epi != EPI_FINAL && (dt == DT_F16 || dt == DT_BF16) && (odt == dt || (odt == DT_F16X2 && dt == DT_F16))) {
+      // stage products on CTA pairs: M = 256, half of B in each CTA (128-row boxes)
+      CUtensorMap ta, tb;
+      if (!encode_tmap(&ta, dt, part_ptr(p, A, 0), n, ldm, 128) || !encode_tmap(&tb, dt, part_ptr(p, B, 0), n, ldm, 128))
+        return cudaErrorInvalidValue;
+      const uint32_t fmt = dt == DT_BF16 ? 1u : 0u;
+      g.num_tiles = p->ntiles_pair;
+      g.tiles = p->d_tiles_pair;
+      g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (16u << 24);  // M = 256; N per tile
+      return launch_symgemm_pair(dt, epi, ta, tb, g, grid, s, odt);
+    }
     CUtensorMap ta, tb;
     if (!encode_tmap(&ta, dt, part_ptr(p, A, 0), n, ldm, 128) || !encode_tmap(&tb, dt, part_ptr(p, B, 0), n, ldm, 256))
       return cudaErrorInvalidValue;
@@ -469,8 +490,10 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   const int flags = epi & ~0xFF;
   epi &= 0xFF;
   const bool grouped = (flags & PSD_EPI_GROUPED) != 0, pair_out = (flags & PSD_EPI_F16_PAIR_OUT) != 0;
-  if (flags & ~(PSD_EPI_GROUPED | PSD_EPI_F16_PAIR_OUT)) return PSD_ERR_INVALID_ARG;
-  if ((grouped || pair_out) && (split || f8 || epi == 3)) return PSD_ERR_INVALID_ARG;
+  const bool cta_pair = (flags & PSD_EPI_CTA_PAIR) != 0;
+  if (flags & ~(PSD_EPI_GROUPED | PSD_EPI_F16_PAIR_OUT | PSD_EPI_CTA_PAIR)) return PSD_ERR_INVALID_ARG;
+  if ((grouped || pair_out || cta_pair) && (split || f8 || epi == 3)) return PSD_ERR_INVALID_ARG;
+  if (grouped && cta_pair) return PSD_ERR_INVALID_ARG;
   if (pair_out && (precision != PSD_PREC_FP16 || epi == 2)) return PSD_ERR_INVALID_ARG;
   if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;
   if (f8 && (epi == 3 || (ld % 16) != 0 || !params)) return PSD_ERR_INVALID_ARG;
@@ -499,13 +522,14 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     ps.d_state = reinterpret_cast<DevState*>(sm + o_state);
     ps.d_block = reinterpret_cast<BlockRec*>(sm + o_block);
   }
-  if (!ps.tiles.count(n)) {
-    std::vector<int4> tl = make_tile_list(n);
+  const int64_t tkey = cta_pair ? -n : n;  // the pair form's 256-row tiles under -n
+  if (!ps.tiles.count(tkey)) {
+    std::vector<int4> tl = cta_pair ? make_tile_list_pair(n) : make_tile_list(n);
     int4* d = nullptr;
     if (cudaMalloc(&d, sizeof(int4) * tl.size()) != cudaSuccess) return PSD_ERR_NO_MEMORY;
     cudaMemcpy(d, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice);
-    ps.tiles[n] = d;
-    ps.ntiles[n] = static_cast<int>(tl.size());
+    ps.tiles[tkey] = d;
+    ps.ntiles[tkey] = static_cast<int>(tl.size());
   }
   const int dtype = precision == PSD_PREC_BF16    ? DT_BF16
                     : precision == PSD_PREC_MIXED ? DT_F16X2
@@ -515,8 +539,8 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   const size_t esz = dtype == DT_TF32X3 ? 4 : (f8 ? 1 : 2);
   const size_t pair = static_cast<size_t>(n) * static_cast<size_t>(ld) * esz;  // byte offset of the lo part
   GemmParams g{};
-  g.num_tiles = ps.ntiles[n];
-  g.tiles = ps.tiles[n];
+  g.num_tiles = ps.ntiles[tkey];
+  g.tiles = ps.tiles[tkey];
   g.blocks = ps.d_block;
   g.ep.C = C;
   g.ep.C_lo = (split || pair_out) ? static_cast<uint8_t*>(C) + pair : nullptr;
@@ -555,7 +579,13 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   }
   if (enqueue_set_block(ps.d_block, br, s) != cudaSuccess) return PSD_ERR_CUDA;
   cudaError_t e;
-  if (!split) {
+  if (cta_pair) {
+    CUtensorMap ta, tb;
+    if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 128)) return PSD_ERR_CUDA;
+    const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;
+    g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (16u << 24);  // M = 256; N per tile
+    e = launch_symgemm_pair(dtype, epi, ta, tb, g, num_sms(), s, pair_out ? DT_F16X2 : -1);
+  } else if (!split) {
     CUtensorMap ta, tb;
     if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 256)) return PSD_ERR_CUDA;
     const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;

@@ -585,6 +585,243 @@ __global__ void __launch_bounds__(threads16(EW), 1)
   if (threadIdx.x == 0 && *abort_flag) raise_status(p.ep.status, PSD_ERR_TIMEOUT);
 }
 
+// ------------------------------------------------------------ 2-SM form
+// The same product on CTA pairs (a cluster of two CTAs on two SMs): one
+// tcgen05.mma.cta_group::2 of M = 256 covers a 256 x N tile, rows 0-127 in the
+// leader's tensor memory and 128-255 in the peer's.  Each CTA stages its own
+// 128 rows of A and half of B (N/2 rows), so a stage holds 32 KB instead of
+// 48 KB and the ring six stages instead of four (the MMA warp has twice the
+// lookahead), and each SM loads half the B operand it used to.  The leader's
+// producer counts the bytes of both CTAs on its full barrier (the peer's TMA
+// signals it across the pair), its MMA warp issues for both, and its commits
+// arrive on the barriers of both CTAs; the peer's epilogue warps release an
+// accumulator through the leader's barrier.  Tiles: (m0, n0, block, width),
+// 256 x 256 blocks of the upper triangle, diagonal blocks in full (chunks
+// below the diagonal are computed but not written).  Epilogues: copy,
+// polynomial and scale with a 16-bit or FP16-pair output.
+constexpr int kStagesP = 6;
+constexpr int kBHalfBytes = kBM * kRowBytes16;          // 16 KB: 128 rows of B
+constexpr int kStageBytesP = kABytes16 + kBHalfBytes;  // 32 KB
+__host__ __device__ constexpr int smem_bytes_pair() {
+  return 1024 + kStagesP * kStageBytesP + 4 * kEpiWarpBytes + 8 * (2 * kStagesP + 5) + 16;
+}
+static_assert(smem_bytes_pair() <= 232448, "shared memory per CTA");
+// A wait that has given up leaves copies of this CTA in flight, which signal
+// the leader's barrier: they are given this long to land before the CTA exits.
+constexpr unsigned long long kPairDrainNs = 200000ull;
+
+template <int EPI, int OUTK>
+__global__ void __launch_bounds__(192, 1)
+    symgemm16_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          const GemmParams p, const int bf16_flag) {
+  static_assert(EPI != EPI_FINAL && OUTK != 1, "pair form: stage products with 16-bit or FP16-pair output");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* stages = smem;
+  uint8_t* epi_stg = smem + kStagesP * kStageBytesP;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_stg + 4 * kEpiWarpBytes);
+  // bars: full[S] | empty[S] | tfull[2] | tempty[2] | drain
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStagesP + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const bool bf16 = bf16_flag != 0;
+  const uint32_t rank = cluster_ctarank();
+  const bool leader = rank == 0;
+  const int cl = static_cast<int>(blockIdx.x >> 1), ncl = static_cast<int>(gridDim.x >> 1);
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + kStagesP + s); };
+  auto tfull_bar = [&](int a) { return smem_u32(bars + 2 * kStagesP + a); };
+  auto tempty_bar = [&](int a) { return smem_u32(bars + 2 * kStagesP + 2 + a); };
+  const uint32_t drain_bar = smem_u32(bars + 2 * kStagesP + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesP; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 8);  // the leader's: 4 epilogue warps of each CTA
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc_pair(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  cluster_sync_all();  // both CTAs' barriers initialised before any arrival crosses the pair
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t s = 0, ph = 0;
+      bool ok = true, issued = false;
+      for (int t = cl; ok && t < p.num_tiles; t += ncl) {
+        const int4 tc = p.tiles[t];
+        const BlockRec& bz = p.blocks[tc.z];
+        const int kbn = (bz.n + kBK16 - 1) / kBK16;
+        // this CTA's 128 rows of A and its N/2 rows of B
+        const int ya = static_cast<int>(bz.off + tc.x + 128 * static_cast<int>(rank));
+        const int yb = static_cast<int>(bz.off + bz.db + tc.y + (tc.w >> 1) * static_cast<int>(rank));
+        for (int kb = 0; kb < kbn; ++kb) {
+          if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          if (leader) mbar_arrive_expect_tx(full_bar(s), 2 * kStageBytesP);  // both CTAs' copies
+          const uint32_t dst = smem_u32(stages + s * kStageBytesP);
+          const uint32_t fb = mapa_shared(full_bar(s), 0);
+          tma_load_2d_pair(dst, &tmA, kb * kBK16, ya, fb);
+          tma_load_2d_pair(dst + kABytes16, &tmB, kb * kBK16, yb, fb);
+          issued = true;
+          if (++s == kStagesP) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok && issued) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < kPairDrainNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (leader) {
+      uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
+      bool ok = true;
+      for (int t = cl; ok && t < p.num_tiles; t += ncl) {
+        const int4 tc = p.tiles[t];
+        const int kbn = (p.blocks[tc.z].n + kBK16 - 1) / kBK16;
+        const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // M = 256, N = tile width
+        if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * kBN;
+        for (int kb = 0; kb < kbn; ++kb) {
+          if (!wait_bounded(full_bar(s), ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t a_addr = smem_u32(stages + s * kStageBytesP);
+            const uint32_t b_addr = a_addr + kABytes16;
+#pragma unroll
+            for (int k = 0; k < kRowBytes16 / 32; ++k)
+              mma_f16_pair(d_tmem, sw128_kmajor_desc(a_addr + 32 * k), sw128_kmajor_desc(b_addr + 32 * k), idesc,
+                           (kb | k) != 0 ? 1u : 0u);
+            mma_commit_pair(empty_bar(s), 3);  // frees the stage in both CTAs
+          }
+          __syncwarp();
+          if (++s == kStagesP) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit_pair(tfull_bar(acc), 3);
+        __syncwarp();
+        acc ^= 1u;
+        if (acc == 0) acc_ph ^= 1u;
+      }
+      if (!ok && lane == 0) {
+        mma_commit_pair(drain_bar, 1);  // the MMAs already issued, before tensor memory is released
+        const unsigned long long t0 = globaltimer_ns();
+        while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
+        }
+      }
+      __syncwarp();
+    }
+  } else {
+    const int ew = warp & 3;  // tensor-memory lane quarter (warps 2-5)
+    uint8_t* wbuf = epi_stg + (warp - 2) * kEpiWarpBytes;
+    uint32_t acc = 0, acc_ph = 0;
+    unsigned amax_bits = 0;
+    int amax_block = -1;
+    const bool track_launch = p.ep.absmax_blocks != 0 || p.ep.absmax != nullptr;
+    auto flush_amax = [&](int blk) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
+      if (lane == 0 && amax_bits) {
+        unsigned* dst = p.ep.absmax ? p.ep.absmax : &p.blocks[blk].st->absmax_bits;
+        atomicMax(dst, amax_bits);
+      }
+      amax_bits = 0;
+    };
+    const uint32_t tempty_leader[2] = {mapa_shared(tempty_bar(0), 0), mapa_shared(tempty_bar(1), 0)};
+    for (int t = cl; t < p.num_tiles; t += ncl) {
+      const int4 tc = p.tiles[t];
+      const BlockRec& br = p.blocks[tc.z];
+      const int n = br.n;
+      const int64_t off = br.off;
+      void* C = static_cast<uint8_t*>(p.ep.C) + (off + br.dc) * p.ep.ldc * 2;
+      void* C_lo = OUTK == 2 ? static_cast<uint8_t*>(p.ep.C_lo) + (off + br.dc) * p.ep.ldc * 2 : nullptr;
+      const uint16_t* Yb = EPI == EPI_POLY
+                               ? reinterpret_cast<const uint16_t*>(static_cast<const uint8_t*>(p.ep.Y) +
+                                                                   (off + br.dy) * p.ep.ldy * 2)
+                               : nullptr;
+      const bool track = track_launch && (p.ep.absmax_blocks != 2 || br.track != 0);
+      if (track_launch && amax_block != tc.z) {
+        if (amax_block >= 0) flush_amax(amax_block);
+        amax_block = tc.z;
+      }
+      const int r0 = tc.x + 128 * static_cast<int>(rank) + 32 * ew;
+      // chunks of this warp's 32 rows that lie on or above the diagonal and inside n
+      const int ch_begin = max(0, (r0 - tc.y) >> 5);
+      const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
+      uint4 ynext[4] = {};
+      if (EPI == EPI_POLY && ch_begin < ch_end) load_y_chunk(Yb, p.ep.ldy, n, r0, tc.y + 32 * ch_begin, lane, ynext);
+      if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (int ch = ch_begin; ch < ch_end; ++ch) {
+        const int c0 = tc.y + 32 * ch;
+        uint4 ycur[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ycur[k] = ynext[k];
+        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y_chunk(Yb, p.ep.ldy, n, r0, c0 + 32, lane, ynext);
+        uint32_t v[32];
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
+        epilogue_chunk16<EPI, false, OUTK>(p, br, bf16, n, C, C_lo, r0, c0, v, wbuf, ycur, lane, track,
+                                           amax_bits);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (leader)
+          mbar_arrive(tempty_bar(acc));
+        else
+          mbar_arrive_remote(tempty_leader[acc]);
+      }
+      acc ^= 1u;
+      if (acc == 0) acc_ph ^= 1u;
+    }
+    if (track_launch && amax_block >= 0) flush_amax(amax_block);
+  }
+
+  // every operand read, remote arrival and copy of the pair is complete
+  // before either CTA releases tensor memory or exits
+  tc_fence_before();
+  cluster_sync_all();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag) raise_status(p.ep.status, PSD_ERR_TIMEOUT);
+}
+
 using Kernel16 = void (*)(const CUtensorMap, const CUtensorMap, const GemmParams, const int);
 
 // Instances: 16-bit operands with 16-bit output (every epilogue); e4m3
@@ -739,6 +976,71 @@ std::vector<int4> make_tile_list(int64_t n, int block, int group) {
     }
   }
   return tiles;
+}
+
+// Tiles of the pair form: every 256 x 256 upper block (I <= J) as one 256-row
+// tile, in the same grouped raster; widths trimmed to the columns below n,
+// rounded up to 32 (N/2 rows of B per CTA; the extra columns read zero-filled
+// rows and are not written).
+std::vector<int4> make_tile_list_pair(int64_t n, int block, int group) {
+  std::vector<int4> tiles;
+  const int nb = static_cast<int>((n + kBN - 1) / kBN);
+  const int G = group > 0 ? group : 8;
+  for (int g0 = 0; g0 < nb; g0 += G)
+    for (int J = g0; J < nb; ++J) {
+      const int iend = std::min(g0 + G, J + 1);
+      for (int I = g0; I < iend; ++I)
+        tiles.push_back(make_int4(I * kBN, J * kBN, block, std::min(kBN, static_cast<int>((n - J * kBN + 31) / 32 * 32))));
+    }
+  return tiles;
+}
+
+cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                                const GemmParams& p, int grid, cudaStream_t stream, int out_dtype) {
+  if (p.num_tiles == 0) return cudaSuccess;
+  if (dtype != DT_F16 && dtype != DT_BF16) return cudaErrorNotSupported;
+  if (out_dtype < 0) out_dtype = dtype;
+  const int outk = out_dtype == DT_F16X2 ? 2 : 0;
+  if ((outk == 2 && dtype != DT_F16) || (outk == 0 && out_dtype != dtype)) return cudaErrorNotSupported;
+  Kernel16 k = nullptr;
+  if (outk == 0)
+    k = epi == EPI_COPY    ? symgemm16_pair_kernel<EPI_COPY, 0>
+        : epi == EPI_POLY  ? symgemm16_pair_kernel<EPI_POLY, 0>
+        : epi == EPI_SCALE ? symgemm16_pair_kernel<EPI_SCALE, 0>
+                           : nullptr;
+  else
+    k = epi == EPI_COPY ? symgemm16_pair_kernel<EPI_COPY, 2> : epi == EPI_POLY ? symgemm16_pair_kernel<EPI_POLY, 2> : nullptr;
+  if (!k) return cudaErrorNotSupported;
+  static std::mutex attr_mu;
+  static Kernel16 attr_done[8] = {};
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    bool set = false;
+    for (Kernel16 d : attr_done) set = set || d == k;
+    if (!set) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_pair());
+      if (e != cudaSuccess) return e;
+      for (Kernel16& d : attr_done)
+        if (!d) {
+          d = k;
+          break;
+        }
+    }
+  }
+  const int pairs = std::max(1, std::min(grid / 2, p.num_tiles));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = smem_bytes_pair();
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, tmA, tmB, p, out_dtype == DT_BF16 ? 1 : 0);
 }
 
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,

@@ -342,3 +342,44 @@ def test_grouped_instance_gives_the_same_bits(n, epi, out):
     assert torch.equal(c4.view(torch.int16), c8.view(torch.int16))
     if flag:  # the pair carries more than the single FP16 rounding: lo is not all zero
         assert torch.count_nonzero(c4[n:, :n]) > n
+
+
+@pytest.mark.parametrize("n", [16, 97, 255, 256, 300, 513, 1000])
+@pytest.mark.parametrize("epi,out", [(e, o) for o in ("fp16", "bf16", "fp16 pair") for e in (0, 1, 2)
+                                     if not (o == "fp16 pair" and e == 2)])
+def test_cta_pair_form_gives_the_same_bits(n, epi, out):
+    # The projection's 16-bit stage products run on pairs of SMs: one M = 256
+    # tensor-core product per 256 x 256 tile, A's rows split between the two
+    # SMs and B's rows split between their shared memories.  Per element it is
+    # the same dot product in the same K order as the one-SM form, so the two
+    # outputs must be bit-identical, also where a 256-row tile is ragged
+    # (n = 97, 255, 300, 513, 1000) or the pair owns a single tile (n = 16).
+    prec = "bf16" if out == "bf16" else "fp16"
+    ld = (n + 7) // 8 * 8
+    dev = torch.device("cuda")
+    A = sym16(n, ld, 50 + n, prec).to(dev)
+    B = sym16(n, ld, 51 + n, prec).to(dev)
+    Y = sym16(n, ld, 52 + n, prec).to(dev)
+    flag = b.EPI_F16_PAIR_OUT if out == "fp16 pair" else 0
+    params = {0: (), 1: (4.0611848147, -2.9698947955, 0.5492133813), 2: (1 / 1.01,)}[epi]
+    rows = 2 * n if flag else n
+    outs = []
+    for form in (0, b.EPI_CTA_PAIR):
+        C = torch.full((rows, ld), float("nan"), dtype=DT[prec], device=dev)
+        b.psd_symm_product(n, A, B if epi != 1 else Y, ld, C, 0, prec, epi | flag | form, params,
+                           Y if epi == 1 else None, ld if epi == 1 else 0)
+        torch.cuda.synchronize()
+        outs.append(C.cpu())
+    c1, c2 = outs
+    assert torch.isfinite(c1[:, :n]).all()
+    assert torch.equal(c1.view(torch.int16), c2.view(torch.int16))
+
+
+def test_cta_pair_form_rejects_what_it_does_not_run():
+    n, ld = 64, 64
+    dev = torch.device("cuda")
+    A = sym16(n, ld, 1, "fp16").to(dev)
+    C = torch.zeros((2 * n, ld), dtype=torch.float16, device=dev)
+    for epi in (b.EPI_CTA_PAIR | b.EPI_GROUPED, b.EPI_CTA_PAIR | 2 | b.EPI_F16_PAIR_OUT):
+        with pytest.raises(RuntimeError):
+            b.psd_symm_product(n, A, A, ld, C, 0, "fp16", epi, (1.0,))
