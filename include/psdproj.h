@@ -180,8 +180,8 @@ psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
  *   PSD_EPI_F16_PAIR_OUT (FP16, epi 0-1): write C as an FP16 hi/lo pair (hi
  *     at C, lo at C + n*ld elements), the Y and P outputs of the mixed
  *     precision;
- *   PSD_EPI_CTA_PAIR (epi 0-2, not with PSD_EPI_GROUPED): run the form the
- *     projection uses for its 16-bit stage products, on pairs of SMs (one
+ *   PSD_EPI_CTA_PAIR (FP16/BF16, epi 0-3, not with PSD_EPI_GROUPED): run the
+ *     form the projection uses for its 16-bit products, on pairs of SMs (one
  *     tensor-core product of M = 256 per 256 x 256 tile, each SM staging its
  *     128 rows of A and half of B) -- the same bits as the one-SM form. */
 #define PSD_EPI_GROUPED 0x100

@@ -129,6 +129,7 @@ struct Plan {
   int ntiles = 0;
   int4* d_tiles_pair = nullptr;  // 256-row tiles of the CTA-pair form of the 16-bit stage products
   int ntiles_pair = 0;
+  int ncompl = 0;  // complementarity shares the final product writes (4 per one-SM tile, 8 per pair tile)
   double* d_compl = nullptr;  // 4 per tile: shares of <out, X - out> from the final product
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
@@ -181,7 +182,8 @@ psd_status_t build_plan(Plan* p, void* user_ws, size_t user_bytes) {
   std::vector<int4> tiles_pair = make_tile_list_pair(n);
   p->ntiles_pair = static_cast<int>(tiles_pair.size());
   const size_t o_compl = o_tiles + round_up(sizeof(int4) * std::max<size_t>(tiles.size(), 1), 256);
-  const size_t o_pair = o_compl + round_up(sizeof(double) * 4 * std::max<size_t>(tiles.size(), 1), 256);
+  const size_t ncompl_max = std::max<size_t>(std::max(4 * tiles.size(), 8 * tiles_pair.size()), 1);
+  const size_t o_pair = o_compl + round_up(sizeof(double) * ncompl_max, 256);
   const size_t small = o_pair + sizeof(int4) * std::max<size_t>(tiles_pair.size(), 1);
   uint8_t* sm = nullptr;
   if (cudaMalloc(&sm, small) != cudaSuccess) {
@@ -244,7 +246,10 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
     g.ep.Y_lo = kind_is_pair(Y->kind) ? part_ptr(p, *Y, 1) : nullptr;
     g.ep.ldy = ldm;
   }
-  if (epi == EPI_FINAL) g.ep.cres = p->d_compl;
+  if (epi == EPI_FINAL) {
+    g.ep.cres = p->d_compl;
+    p->ncompl = 4 * p->ntiles;
+  }
   g.ep.in_scale = 1.f / (A.scale * B.scale);
   g.ep.y_scale = Y ? 1.f / Y->scale : 1.f;
   g.ep.out_scale = out ? out->scale : 1.f;
@@ -253,8 +258,9 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
   if (route == ROUTE_16) {
     const int dt = kind_dtype(A);
     const int odt = out ? kind_dtype(*out) : -1;
-    if (epi != EPI_FINAL && (dt == DT_F16 || dt == DT_BF16) && (odt == dt || (odt == DT_F16X2 && dt == DT_F16))) {
-      // stage products on CTA pairs: M = 256, half of B in each CTA (128-row boxes)
+    if ((dt == DT_F16 || dt == DT_BF16) &&
+        (epi == EPI_FINAL || odt == dt || (odt == DT_F16X2 && dt == DT_F16))) {
+      // 16-bit products on CTA pairs: M = 256, half of B in each CTA (128-row boxes)
       CUtensorMap ta, tb;
       if (!encode_tmap(&ta, dt, part_ptr(p, A, 0), n, ldm, 128) || !encode_tmap(&tb, dt, part_ptr(p, B, 0), n, ldm, 128))
         return cudaErrorInvalidValue;
@@ -262,7 +268,8 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
       g.num_tiles = p->ntiles_pair;
       g.tiles = p->d_tiles_pair;
       g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (16u << 24);  // M = 256; N per tile
-      return launch_symgemm_pair(dt, epi, ta, tb, g, grid, s, odt);
+      if (epi == EPI_FINAL) p->ncompl = 8 * p->ntiles_pair;
+      return launch_symgemm_pair(dt, epi, ta, tb, g, grid, s, epi == EPI_FINAL ? -1 : odt);
     }
     CUtensorMap ta, tb;
     if (!encode_tmap(&ta, dt, part_ptr(p, A, 0), n, ldm, 128) || !encode_tmap(&tb, dt, part_ptr(p, B, 0), n, ldm, 256))
@@ -298,7 +305,7 @@ struct PlanOps {
                    float sc, bool track) {
     return psd::gemm(p, epi, A, B, out, Y, a, b, c, sc, track ? &p->d_state->absmax_bits : nullptr, s);
   }
-  cudaError_t finish() { return enqueue_finalize(p->d_args, p->d_state, s, p->d_compl, 4 * p->ntiles); }
+  cudaError_t finish() { return enqueue_finalize(p->d_args, p->d_state, s, p->d_compl, p->ncompl); }
 };
 
 // Enqueue the whole projection (used for graph capture and for direct launch).
@@ -492,7 +499,8 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   const bool grouped = (flags & PSD_EPI_GROUPED) != 0, pair_out = (flags & PSD_EPI_F16_PAIR_OUT) != 0;
   const bool cta_pair = (flags & PSD_EPI_CTA_PAIR) != 0;
   if (flags & ~(PSD_EPI_GROUPED | PSD_EPI_F16_PAIR_OUT | PSD_EPI_CTA_PAIR)) return PSD_ERR_INVALID_ARG;
-  if ((grouped || pair_out || cta_pair) && (split || f8 || epi == 3)) return PSD_ERR_INVALID_ARG;
+  if ((grouped || pair_out) && (split || f8 || epi == 3)) return PSD_ERR_INVALID_ARG;
+  if (cta_pair && (split || f8)) return PSD_ERR_INVALID_ARG;
   if (grouped && cta_pair) return PSD_ERR_INVALID_ARG;
   if (pair_out && (precision != PSD_PREC_FP16 || epi == 2)) return PSD_ERR_INVALID_ARG;
   if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;

@@ -598,7 +598,10 @@ __global__ void __launch_bounds__(threads16(EW), 1)
 // accumulator through the leader's barrier.  Tiles: (m0, n0, block, width),
 // 256 x 256 blocks of the upper triangle, diagonal blocks in full (chunks
 // below the diagonal are computed but not written).  Epilogues: copy,
-// polynomial and scale with a 16-bit or FP16-pair output.
+// polynomial and scale with a 16-bit or FP16-pair output, and the final
+// product (FP32 output; the eight epilogue warps of a pair tile write the
+// complementarity shares of the two 128-row tiles of the one-SM form, in its
+// order: slots 8 t + 4 rank + warp).
 constexpr int kStagesP = 6;
 constexpr int kBHalfBytes = kBM * kRowBytes16;          // 16 KB: 128 rows of B
 constexpr int kStageBytesP = kABytes16 + kBHalfBytes;  // 32 KB
@@ -614,7 +617,7 @@ template <int EPI, int OUTK>
 __global__ void __launch_bounds__(192, 1)
     symgemm16_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                           const GemmParams p, const int bf16_flag) {
-  static_assert(EPI != EPI_FINAL && OUTK != 1, "pair form: stage products with 16-bit or FP16-pair output");
+  static_assert(OUTK != 1 && (EPI != EPI_FINAL || OUTK == 0), "pair form: 16-bit operands, no e4m3 output");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -785,6 +788,10 @@ __global__ void __launch_bounds__(192, 1)
       if (EPI == EPI_POLY && ch_begin < ch_end) load_y_chunk(Yb, p.ep.ldy, n, r0, tc.y + 32 * ch_begin, lane, ynext);
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
+      const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
+      double* cdst = EPI == EPI_FINAL && p.ep.cres ? p.ep.cres + 8 * t + 4 * static_cast<int>(rank) : nullptr;
+      ComplAcc cacc;
+      ComplAcc* cap = cdst ? &cacc : nullptr;
 #pragma unroll 1
       for (int ch = ch_begin; ch < ch_end; ++ch) {
         const int c0 = tc.y + 32 * ch;
@@ -794,8 +801,15 @@ __global__ void __launch_bounds__(192, 1)
         if (EPI == EPI_POLY && ch + 1 < ch_end) load_y_chunk(Yb, p.ep.ldy, n, r0, c0 + 32, lane, ynext);
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
-        epilogue_chunk16<EPI, false, OUTK>(p, br, bf16, n, C, C_lo, r0, c0, v, wbuf, ycur, lane, track,
-                                           amax_bits);
+        if (EPI == EPI_FINAL)
+          epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam, cap);
+        else
+          epilogue_chunk16<EPI, false, OUTK>(p, br, bf16, n, C, C_lo, r0, c0, v, wbuf, ycur, lane, track,
+                                             amax_bits);
+      }
+      if (EPI == EPI_FINAL && cdst) {
+        const double cs = compl_warp_sum(cacc);
+        if (lane == 0) cdst[ew] = cs;
       }
       tc_fence_before();
       __syncwarp();
@@ -808,7 +822,7 @@ __global__ void __launch_bounds__(192, 1)
       acc ^= 1u;
       if (acc == 0) acc_ph ^= 1u;
     }
-    if (track_launch && amax_block >= 0) flush_amax(amax_block);
+    if (EPI != EPI_FINAL && track_launch && amax_block >= 0) flush_amax(amax_block);
   }
 
   // every operand read, remote arrival and copy of the pair is complete
@@ -1007,6 +1021,7 @@ cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, cons
     k = epi == EPI_COPY    ? symgemm16_pair_kernel<EPI_COPY, 0>
         : epi == EPI_POLY  ? symgemm16_pair_kernel<EPI_POLY, 0>
         : epi == EPI_SCALE ? symgemm16_pair_kernel<EPI_SCALE, 0>
+        : epi == EPI_FINAL ? symgemm16_pair_kernel<EPI_FINAL, 0>
                            : nullptr;
   else
     k = epi == EPI_COPY ? symgemm16_pair_kernel<EPI_COPY, 2> : epi == EPI_POLY ? symgemm16_pair_kernel<EPI_POLY, 2> : nullptr;

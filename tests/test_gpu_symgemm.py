@@ -375,6 +375,28 @@ def test_cta_pair_form_gives_the_same_bits(n, epi, out):
     assert torch.equal(c1.view(torch.int16), c2.view(torch.int16))
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("n", [16, 97, 255, 300, 513, 1000])
+def test_cta_pair_form_final_product_gives_the_same_bits(n, prec):
+    # The final product out = (X + lam~ A B) / 2 in FP32, on pairs of SMs and
+    # on one: the same accumulator bits, so the same output, both triangles.
+    ld = (n + 7) // 8 * 8
+    dev = torch.device("cuda")
+    A = sym16(n, ld, 60 + n, prec).to(dev)
+    B = sym16(n, ld, 61 + n, prec).to(dev)
+    rng = np.random.default_rng(62 + n)
+    G = rng.standard_normal((n, n))
+    X = torch.from_numpy((0.5 * (G + G.T)).astype(np.float32)).to(dev)
+    outs = []
+    for form in (0, b.EPI_CTA_PAIR):
+        C = torch.full((n, n), float("nan"), dtype=torch.float32, device=dev)
+        b.psd_symm_product(n, A, B, ld, C, n, prec, 3 | form, (1.37,), X, n)
+        torch.cuda.synchronize()
+        outs.append(C.cpu())
+    assert torch.isfinite(outs[0]).all()
+    assert torch.equal(outs[0].view(torch.int32), outs[1].view(torch.int32))
+
+
 def test_cta_pair_form_rejects_what_it_does_not_run():
     n, ld = 64, 64
     dev = torch.device("cuda")
