@@ -623,9 +623,10 @@ def run_ours(args):
     barrier()
     e2e_ms = reduce_max(ev0.elapsed_time(ev1) / e2e_steps, dev) if e2e_steps else None
 
-    # dominant kernel: the symmetric tensor-core product of the chain, same kernel and shape
-    # (mixed: the FP16-pair split product of stages 1-3; fp16/bf16: the 16-bit product;
-    #  fp32: the TF32x3 split product), timed alone with CUDA events on the launching stream
+    # dominant kernel: the symmetric tensor-core product of the chain, same kernel, shape and
+    # form as in the projection (mixed: the FP16-pair split product of stages 1-3; fp16/bf16:
+    # the 16-bit product; both on SM pairs; fp32: the TF32x3 split product on one SM), timed
+    # alone with CUDA events on the launching stream
     ld = (n + 63) // 64 * 64
     kprec = {"mixed": "mixed", "fp32": "fp32", "bf16": "bf16"}.get(prec, "fp16")
     parts, et = {"mixed": (2, torch.float16), "fp32": (2, torch.float32),
@@ -634,12 +635,13 @@ def run_ours(args):
     if parts == 2:
         A[1].mul_(1.0 / 2048)  # lo part of a hi/lo pair
     C = torch.empty_like(A)
+    form = 0 if prec == "fp32" else b.EPI_CTA_PAIR
     for _ in range(3):
-        b.psd_symm_product(n, A, A, ld, C, 0, kprec, 0, stream=s)
+        b.psd_symm_product(n, A, A, ld, C, 0, kprec, form, stream=s)
     reps = 20 if parts == 1 else 8
     ev0.record(s)
     for _ in range(reps):
-        b.psd_symm_product(n, A, A, ld, C, 0, kprec, 0, stream=s)
+        b.psd_symm_product(n, A, A, ld, C, 0, kprec, form, stream=s)
     ev1.record(s)
     torch.cuda.synchronize(dev)
     gemm_ms = ev0.elapsed_time(ev1) / reps
@@ -696,8 +698,9 @@ def run_ours(args):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": roofline_traffic(prec, n),
                          "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                         "kernel": "%s symmetric product (%d tensor-core product%s per launch), timed alone: %.4f ms"
-                                   % (kprec, products, "s" if products > 1 else "", gemm_ms),
+                         "kernel": "%s symmetric product (%d tensor-core product%s per launch%s), timed alone: "
+                                   "%.4f ms" % (kprec, products, "s" if products > 1 else "",
+                                                "" if prec == "fp32" else ", SM pairs", gemm_ms),
                          "peak_source": "%s bf16 burst (MEASURED_PEAKS.json)%s"
                                         % (peak_src, ", x0.5 nominal tf32/bf16 ratio" if prec == "fp32" else ""),
                          "algorithmic_flops_per_launch": alg_flops},

@@ -180,8 +180,9 @@ psd_status_t psd_project_batched(int32_t count, const psd_block_desc_t *d_descs,
  *   PSD_EPI_F16_PAIR_OUT (FP16, epi 0-1): write C as an FP16 hi/lo pair (hi
  *     at C, lo at C + n*ld elements), the Y and P outputs of the mixed
  *     precision;
- *   PSD_EPI_CTA_PAIR (FP16/BF16, epi 0-3, not with PSD_EPI_GROUPED): run the
- *     form the projection uses for its 16-bit products, on pairs of SMs (one
+ *   PSD_EPI_CTA_PAIR (FP16/BF16 epi 0-3, MIXED epi 0-2, not with
+ *     PSD_EPI_GROUPED): run the form the projection uses for its 16-bit and
+ *     FP16-pair products, on pairs of SMs (one
  *     tensor-core product of M = 256 per 256 x 256 tile, each SM staging its
  *     128 rows of A and half of B) -- the same bits as the one-SM form. */
 #define PSD_EPI_GROUPED 0x100
@@ -314,8 +315,11 @@ psd_status_t psd_server_destroy(psd_server_t *server);
  * grouped product can be dealt to the persistent CTAs in several orders (6
  * candidates: blocks largest first or all tiles by estimated cost in
  * boustrophedon rounds, times a raster group of 4, 8 or 16 for a block's
- * tiles).  No candidate changes any tile's arithmetic: results are
- * bit-identical under every schedule.  When a plan is built (first call per
+ * tiles), and for FP16 / BF16 plans the products can run with another tile
+ * shape (candidate 6: 256 x 256 tiles on pairs of SMs, one M = 256
+ * tensor-core product per K step, each SM staging 128 rows of A and half of
+ * B).  No candidate changes any element's arithmetic: results are
+ * bit-identical under every schedule and shape.  When a plan is built (first call per
  * device, stream, precision and block orders) the library times one product
  * of the chain's first stage under each candidate (median of 3 after a
  * warm-up, on a private stream, synchronising the device) and keeps the
@@ -323,13 +327,28 @@ psd_status_t psd_server_destroy(psd_server_t *server);
  * size profile (the number of blocks per order bucket n in (2^(k-1), 2^k]), so
  * later plans with the same profile are not re-timed. */
 
-/* Forces schedule `index` (0..5) for plans built after the call; -1 restores
- * autotuning (the default).  Returns the previous setting.  Host-only. */
+/* Forces schedule `index` (0..5, or 6: the pair shape, FP16 / BF16 only) for
+ * plans built after the call; -1 restores autotuning (the default).  Returns
+ * the previous setting.  Host-only. */
 int32_t psd_batched_force_schedule(int32_t index);
 
-/* Schedule of the most recently built batched plan: *chosen (0..5),
- * *candidates (6) and, if ms is not NULL, the measured ms per candidate
- * (ms[6]; zeros when the schedule was forced or taken from the cache).
+/* Form of the products of plans built after the call: 1 = the chain form
+ * (FP16 and BF16, 128-row tiles: all 3T + 1 products of every block in ONE
+ * persistent cooperative launch; a block's next product starts as soon as all
+ * tiles of its previous product are written, counted per block and product
+ * and waited for with a bounded spin), 0 or -1 (the default) = one grouped
+ * launch per product.  The chain form measured slower on 512 blocks of orders
+ * 16-1024 (5.01 against 4.82 ms): its tiles are bound by the operand feed of
+ * their main loops, not by launch boundaries.  Both forms give bit-identical
+ * outputs; the complementarity residual of the report is summed from 8 shares
+ * per tile in the chain form and 4 otherwise (equal to within rounding).
+ * Returns the previous setting.  Host-only. */
+int32_t psd_batched_force_form(int32_t form);
+
+/* Schedule of the most recently built batched plan: *chosen (0..6),
+ * *candidates (7 for FP16 / BF16, else 6) and, if ms is not NULL, the
+ * measured ms per candidate (ms[*candidates]; zeros when the schedule was
+ * forced or taken from the cache).
  * PSD_ERR_INVALID_ARG before any plan was built.  Host-only. */
 psd_status_t psd_batched_last_tuning(int32_t *chosen, int32_t *candidates, float *ms);
 

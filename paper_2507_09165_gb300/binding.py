@@ -85,6 +85,7 @@ _SIGS = {
     "psd_server_destroy": ([_VP], _I32),
     "psd_project_deflate": ([_I64, _VP, _I64, _VP, _I64, _I32, _I32, _VP, _VP, _VP], _I32),
     "psd_batched_force_schedule": ([_I32], _I32),
+    "psd_batched_force_form": ([_I32], _I32),
     "psd_batched_last_tuning": ([ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)], _I32),
 }
 
@@ -157,6 +158,12 @@ def psd_project_deflate(n, X, ld, out, ld_out, precision="fp16", kmax=8, d_info=
 def psd_batched_force_schedule(index):
     """Force grouped-product schedule `index` (0..5) for batched plans built next; -1: autotune."""
     return int(lib().psd_batched_force_schedule(int(index)))
+
+
+def psd_batched_force_form(form):
+    """Product form of batched plans built next: 1 chain (one persistent launch), 0 one launch
+    per product, -1 default (chain where it applies)."""
+    return int(lib().psd_batched_force_form(int(form)))
 
 
 def psd_batched_last_tuning():

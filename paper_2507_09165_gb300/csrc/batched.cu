@@ -40,6 +40,11 @@ struct BatchPlan {
   int* d_status = nullptr;
   int4* d_tiles = nullptr;
   int ntiles = 0;
+  // 256 x 256 tiles on SM pairs (FP16 / BF16 plans), chosen by the autotuner
+  // when faster than every schedule of the 128-row tiles
+  int4* d_tiles_pair = nullptr;
+  int ntiles_pair = 0;
+  bool pair = false;
   int4* d_symv = nullptr;
   int nsymv = 0;
   int4* d_cast = nullptr;
@@ -50,6 +55,14 @@ struct BatchPlan {
   uint8_t* small = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
+  // The chain form (FP16 / BF16): every product of the chain in one persistent
+  // launch over the same tile list (launch_symgemm_chain).
+  bool chain = false;
+  ChainMaps cmaps{};
+  ChainProduct* d_prods = nullptr;  // in `small`
+  int nprod = 0;
+  int* d_done = nullptr;            // count x nprod tile counters, in `small`
+  Mat x0{};                         // the cast's output (the chain's X_0)
 };
 
 std::mutex g_bmu;
@@ -120,12 +133,28 @@ std::vector<int4> schedule_tiles(const std::vector<int>& sizes, int cand, int gr
   return out;
 }
 
+// Pair-form tiles: blocks largest first, each block's 256 x 256 tiles in its
+// grouped raster (make_tile_list_pair).
+std::vector<int4> pair_tiles(const std::vector<int>& sizes) {
+  std::vector<int> blocks(sizes.size());
+  for (size_t b = 0; b < sizes.size(); ++b) blocks[b] = static_cast<int>(b);
+  std::stable_sort(blocks.begin(), blocks.end(), [&](int x, int y) { return sizes[x] > sizes[y]; });
+  std::vector<int4> tiles;
+  for (int b : blocks) {
+    std::vector<int4> tl = make_tile_list_pair(sizes[b], b, 8);
+    tiles.insert(tiles.end(), tl.begin(), tl.end());
+  }
+  return tiles;
+}
+constexpr int kPairCandidate = kNumSchedules;  // autotune candidate index of the pair form
+
 struct TuneReport {
   int chosen = -1;
   int ncand = 0;
-  float ms[kNumSchedules] = {};
+  float ms[kNumSchedules + 1] = {};
 };
 int g_force_schedule = -1;                                  // for plans built next; -1: autotune
+int g_force_form = -1;  // for plans built next: -1 / 0 one launch per product, 1 chain form where it applies
 std::map<std::pair<int, std::vector<int>>, int> g_tuned;   // (precision, order buckets) -> schedule
 
 // Tuning key: the precision and the number of blocks per order bucket
@@ -180,6 +209,8 @@ psd_status_t build_bplan(BatchPlan* p) {
   p->R = off;
   // product tiles of all blocks in the default schedule (the autotuner may reorder them)
   std::vector<int4> tiles = schedule_tiles(p->sizes, 0, num_sms());
+  std::vector<int4> tiles_pair = pair_tiles(p->sizes);
+  p->ntiles_pair = static_cast<int>(tiles_pair.size());
   p->ntiles = static_cast<int>(tiles.size());
   p->nsymv = static_cast<int>(symv.size());
   p->ncast = static_cast<int>(cast.size());
@@ -219,10 +250,17 @@ psd_status_t build_bplan(BatchPlan* p) {
   const size_t o_symv = o_tiles + rup(sizeof(int4) * tiles.size(), 256);
   const size_t o_cast = o_symv + rup(sizeof(int4) * symv.size(), 256);
   const size_t o_cres = o_cast + rup(sizeof(int4) * cast.size(), 256);
-  const size_t o_cidx = o_cres + rup(sizeof(double) * 4 * std::max<size_t>(tiles.size(), 1), 256);
+  // final-product shares: 4 per tile position (one launch per product), 8 (chain form),
+  // 16 per pair tile
+  const size_t ncres = std::max<size_t>(std::max(8 * tiles.size(), 16 * tiles_pair.size()), 1);
+  const size_t o_cidx = o_cres + rup(sizeof(double) * ncres, 256);
   const size_t o_crange = o_cidx + rup(sizeof(int) * std::max<size_t>(tiles.size(), 1), 256);
   const size_t o_order = o_crange + rup(sizeof(int2) * count, 256);
-  const size_t smallb = o_order + rup(sizeof(int) * count, 256);
+  constexpr int kMaxProducts = 3 * kMaxStages + 1;
+  const size_t o_prods = o_order + rup(sizeof(int) * count, 256);
+  const size_t o_done = o_prods + rup(sizeof(ChainProduct) * kMaxProducts, 256);
+  const size_t o_tpair = o_done + rup(sizeof(int) * kMaxProducts * count, 256);
+  const size_t smallb = o_tpair + rup(sizeof(int4) * std::max<size_t>(tiles_pair.size(), 1), 256);
   if (cudaMalloc(&p->small, smallb) != cudaSuccess) {
     cudaGetLastError();
     p->small = nullptr;
@@ -240,6 +278,9 @@ psd_status_t build_bplan(BatchPlan* p) {
   p->d_cidx = reinterpret_cast<int*>(p->small + o_cidx);
   p->d_crange = reinterpret_cast<int2*>(p->small + o_crange);
   int* d_order = reinterpret_cast<int*>(p->small + o_order);
+  p->d_prods = reinterpret_cast<ChainProduct*>(p->small + o_prods);
+  p->d_done = reinterpret_cast<int*>(p->small + o_done);
+  p->d_tiles_pair = reinterpret_cast<int4*>(p->small + o_tpair);
   // per-block kernels take the blocks largest first (the longest CTAs start first)
   std::vector<int> order(count);
   for (int b = 0; b < count; ++b) order[b] = b;
@@ -251,7 +292,9 @@ psd_status_t build_bplan(BatchPlan* p) {
                 cudaSuccess &&
             cudaMemcpy(p->d_symv, symv.data(), sizeof(int4) * symv.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(p->d_cast, cast.data(), sizeof(int4) * cast.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) == cudaSuccess;
+            cudaMemcpy(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(p->d_tiles_pair, tiles_pair.data(), sizeof(int4) * tiles_pair.size(),
+                       cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) return PSD_ERR_CUDA;
   p->L.order = d_order;
   p->L.blk = p->d_bb;
@@ -262,6 +305,74 @@ psd_status_t build_bplan(BatchPlan* p) {
 
 void* bpart(const BatchPlan* p, const Mat& m, int part) {
   return p->slots + (static_cast<size_t>(m.slot) + static_cast<size_t>(part * kind_lo_step(m.kind))) * p->slot_size;
+}
+
+// The chain form: run_chain's sequence recorded without launching anything
+// (the cast's output and, per product, its epilogue, operands by tensor map,
+// output and coefficients).  Applies when every product is a 16-bit product
+// with a 16-bit output (FP16, BF16).
+struct ChainRecorder {
+  BatchPlan* p;
+  std::vector<ChainProduct> prods;
+  uint32_t encoded = 0;
+  bool ok = true;
+  Mat x0{};
+  int map_of(const Mat& m, int role) {  // role 0: A (128-row boxes), 1: B (256-row boxes)
+    if (m.slot < 0 || m.slot >= kChainMaxSlots || m.kind != MK_16) {
+      ok = false;
+      return 0;
+    }
+    const int idx = 2 * m.slot + role;
+    if (!(encoded & (1u << idx))) {
+      if (!encode_tmap_rows(&p->cmaps.m[idx], m.dt16, bpart(p, m, 0), p->ldm, p->R, p->ldm, role ? 256 : 128))
+        ok = false;
+      encoded |= 1u << idx;
+    }
+    return idx;
+  }
+  cudaError_t cast(const Mat& X0) {
+    x0 = X0;
+    return cudaSuccess;
+  }
+  cudaError_t gemm(int epi, const Mat& A, const Mat& B, const Mat* out, const Mat* Y, float a, float b, float c,
+                   float sc, bool track) {
+    if (gemm_route(A, B) != ROUTE_16 || A.kind != MK_16 || (out && out->kind != MK_16) || (Y && Y->kind != MK_16))
+      ok = false;
+    ChainProduct cp{};
+    cp.epi = epi;
+    cp.ma = map_of(A, 0);
+    cp.mb = map_of(B, 1);
+    cp.track = track ? 1 : 0;
+    cp.C = out ? bpart(p, *out, 0) : nullptr;
+    cp.Y = Y ? bpart(p, *Y, 0) : nullptr;
+    cp.a = a;
+    cp.b = b;
+    cp.c = c;
+    cp.s = sc;
+    prods.push_back(cp);
+    return cudaSuccess;
+  }
+  cudaError_t finish() { return cudaSuccess; }
+};
+
+// Decides the plan's form and, for the chain form, stores the product table.
+psd_status_t prepare_chain(BatchPlan* p) {
+  p->chain = false;
+  if (g_force_form != 1 || p->pair || (p->prec != PSD_PREC_FP16 && p->prec != PSD_PREC_BF16)) return PSD_OK;
+  ChainRecorder rec{p};
+  if (run_chain(p->prec, p->sched, p->nslots, dt16_for(p->prec), rec) != cudaSuccess || !rec.ok ||
+      rec.prods.empty() || rec.prods.size() > static_cast<size_t>(3 * kMaxStages + 1))
+    return PSD_OK;  // one launch per product
+  for (int b = 0; b < p->count; ++b)  // the counters' targets
+    if (static_cast<int>(make_tile_list(p->sizes[b], b, 8).size()) != tile_count_of_order(p->sizes[b]))
+      return PSD_OK;
+  if (cudaMemcpy(p->d_prods, rec.prods.data(), sizeof(ChainProduct) * rec.prods.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return PSD_ERR_CUDA;
+  p->nprod = static_cast<int>(rec.prods.size());
+  p->x0 = rec.x0;
+  p->chain = true;
+  return PSD_OK;
 }
 
 // One grouped product over every block's tiles (routes: chain.h gemm_route).
@@ -295,6 +406,17 @@ cudaError_t bgemm(BatchPlan* p, int epi, const Mat& A, const Mat& B, const Mat* 
   if (route == ROUTE_16) {
     const int dt = kind_dtype(A);
     CUtensorMap ta, tb;
+    if (p->pair && (dt == DT_F16 || dt == DT_BF16) && (epi == EPI_FINAL || kind_dtype(*out) == dt)) {
+      // 256 x 256 tiles on SM pairs: each CTA stages 128 rows of A and half of B
+      if (!encode_tmap_rows(&ta, dt, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
+          !encode_tmap_rows(&tb, dt, bpart(p, B, 0), cols, rows, p->ldm, 128))
+        return cudaErrorInvalidValue;
+      g.num_tiles = p->ntiles_pair;
+      g.tiles = p->d_tiles_pair;
+      const uint32_t fmt = dt == DT_BF16 ? 1u : 0u;
+      g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (16u << 24);  // M = 256; N per tile
+      return launch_symgemm_pair(dt, epi, ta, tb, g, grid, s, -1, /*many_small=*/true);
+    }
     if (!encode_tmap_rows(&ta, dt, bpart(p, A, 0), cols, rows, p->ldm, 128) ||
         !encode_tmap_rows(&tb, dt, bpart(p, B, 0), cols, rows, p->ldm, 256))
       return cudaErrorInvalidValue;
@@ -330,15 +452,36 @@ struct BatchOps {
     return bgemm(p, epi, A, B, out, Y, a, b, c, sc, track, s);
   }
   cudaError_t finish() {
-    return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, p->d_cres, p->d_cidx, p->d_crange, s);
+    return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, p->d_cres, p->d_cidx, p->d_crange, p->pair ? 16 : 4,
+                                  s);
   }
 };
 
 cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
   cudaError_t e;
   if ((e = enqueue_batch_norm_bound(p->L, p->count, p->d_symv, p->nsymv, s)) != cudaSuccess) return e;
+  if (!p->chain) {
+    BatchOps ops{p, s};
+    return run_chain(p->prec, p->sched, p->nslots, dt16_for(p->prec), ops);
+  }
   BatchOps ops{p, s};
-  return run_chain(p->prec, p->sched, p->nslots, dt16_for(p->prec), ops);
+  if ((e = ops.cast(p->x0)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(p->d_done, 0, sizeof(int) * p->nprod * p->count, s)) != cudaSuccess) return e;
+  GemmParams g{};
+  g.num_tiles = p->ntiles;
+  g.tiles = p->d_tiles;
+  g.blocks = p->d_rec;
+  g.ep.status = p->d_status;
+  g.ep.ldc = p->ldm;
+  g.ep.ldy = p->ldm;
+  g.ep.in_scale = g.ep.y_scale = g.ep.out_scale = 1.f;
+  g.ep.cres = p->d_cres;
+  const uint32_t fmt = dt16_for(p->prec) == DT_BF16 ? 1u : 0u;
+  g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);  // M = 128; N per tile
+  if ((e = launch_symgemm_chain(dt16_for(p->prec), p->cmaps, p->d_prods, p->nprod, g, p->d_done, num_sms(), s)) !=
+      cudaSuccess)
+    return e;
+  return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, p->d_cres, p->d_cidx, p->d_crange, 8, s);
 }
 
 // Picks the plan's product schedule: the forced one, the one tuned earlier for
@@ -348,12 +491,14 @@ cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
 psd_status_t tune_bplan(BatchPlan* p) {
   const int grid = std::max(1, std::min(num_sms(), p->ntiles));
   const auto key = tune_key(p);
+  // the pair form: FP16 / BF16 plans (every product a 16-bit product), not with the chain form
+  const bool pair_ok = (p->prec == PSD_PREC_FP16 || p->prec == PSD_PREC_BF16) && g_force_form != 1;
   TuneReport rep;
-  rep.ncand = kNumSchedules;
+  rep.ncand = kNumSchedules + (pair_ok ? 1 : 0);
   int chosen = 0;
-  if (g_force_schedule >= 0 && g_force_schedule < kNumSchedules) {
+  if (g_force_schedule >= 0 && g_force_schedule < rep.ncand) {
     chosen = g_force_schedule;
-  } else if (g_tuned.count(key)) {
+  } else if (g_tuned.count(key) && g_tuned[key] < rep.ncand) {
     chosen = g_tuned[key];
   } else {
     cudaStream_t ts;
@@ -371,10 +516,13 @@ psd_status_t tune_bplan(BatchPlan* p) {
     Y.dt16 = A.dt16;
     float best = 0.f;
     bool ok = true;
-    for (int c = 0; c < kNumSchedules && ok; ++c) {
-      const std::vector<int4> t = schedule_tiles(p->sizes, c, grid);
-      ok = cudaMemcpyAsync(p->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice, ts) ==
-           cudaSuccess;
+    for (int c = 0; c < rep.ncand && ok; ++c) {
+      p->pair = c == kPairCandidate;
+      if (!p->pair) {
+        const std::vector<int4> t = schedule_tiles(p->sizes, c, grid);
+        ok = cudaMemcpyAsync(p->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice, ts) ==
+             cudaSuccess;
+      }
       float ms[3] = {};
       for (int r = -1; r < 3 && ok; ++r) {
         cudaEventRecord(e0, ts);
@@ -396,17 +544,21 @@ psd_status_t tune_bplan(BatchPlan* p) {
     if (!ok) return PSD_ERR_CUDA;
     g_tuned[key] = chosen;
   }
-  const std::vector<int4> t = schedule_tiles(p->sizes, chosen, grid);
+  p->pair = chosen == kPairCandidate;
+  const std::vector<int4> t = schedule_tiles(p->sizes, p->pair ? 0 : chosen, grid);
   if (cudaMemcpy(p->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return PSD_ERR_CUDA;
-  // each block's final-product shares, in the block's own tile order (schedule-independent sums)
+  // each block's final-product shares, in the block's own tile order (schedule-independent
+  // sums), positions in the tile list the final product runs over
+  const std::vector<int4> tf = p->pair ? pair_tiles(p->sizes) : t;
   std::map<std::tuple<int, int, int>, int> pos;
-  for (int i = 0; i < static_cast<int>(t.size()); ++i) pos[std::make_tuple(t[i].z, t[i].x, t[i].y)] = i;
+  for (int i = 0; i < static_cast<int>(tf.size()); ++i) pos[std::make_tuple(tf[i].z, tf[i].x, tf[i].y)] = i;
   std::vector<int> cidx;
   std::vector<int2> crange(p->count);
   for (int b = 0; b < p->count; ++b) {
     crange[b].x = static_cast<int>(cidx.size());
-    for (const int4& c : make_tile_list(p->sizes[b], b, 8)) cidx.push_back(pos.at(std::make_tuple(b, c.x, c.y)));
+    const std::vector<int4> own = p->pair ? make_tile_list_pair(p->sizes[b], b, 8) : make_tile_list(p->sizes[b], b, 8);
+    for (const int4& c : own) cidx.push_back(pos.at(std::make_tuple(b, c.x, c.y)));
     crange[b].y = static_cast<int>(cidx.size()) - crange[b].x;
   }
   if (cudaMemcpy(p->d_cidx, cidx.data(), sizeof(int) * cidx.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -453,7 +605,14 @@ using namespace psd;
 extern "C" int32_t psd_batched_force_schedule(int32_t index) {
   std::lock_guard<std::mutex> lk(g_bmu);
   const int prev = g_force_schedule;
-  g_force_schedule = (index >= 0 && index < kNumSchedules) ? index : -1;
+  g_force_schedule = (index >= 0 && index <= kPairCandidate) ? index : -1;
+  return prev;
+}
+
+extern "C" int32_t psd_batched_force_form(int32_t form) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  const int prev = g_force_form;
+  g_force_form = (form == 0 || form == 1) ? form : -1;
   return prev;
 }
 
@@ -500,7 +659,7 @@ extern "C" psd_status_t psd_project_batched(int32_t count, const psd_block_desc_
     sizes[b] = static_cast<int>(d.n);
   }
   std::lock_guard<std::mutex> lk(g_bmu);
-  auto key = std::make_tuple(dev, s, static_cast<int>(precision), sizes);
+  auto key = std::make_tuple(dev, s, 4 * static_cast<int>(precision) + g_force_form + 1, sizes);
   BatchPlan* p = nullptr;
   auto it = g_bplans.find(key);
   if (it != g_bplans.end()) {
@@ -512,6 +671,7 @@ extern "C" psd_status_t psd_project_batched(int32_t count, const psd_block_desc_
     p->sizes = sizes;
     psd_status_t st = build_bplan(p);
     if (st == PSD_OK) st = tune_bplan(p);
+    if (st == PSD_OK) st = prepare_chain(p);
     if (st != PSD_OK) {
       free_bplan(p);
       return st;

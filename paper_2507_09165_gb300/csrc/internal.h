@@ -202,16 +202,52 @@ cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUt
 // The same product on CTA pairs (tcgen05.mma.cta_group::2, M = 256): tiles
 // from make_tile_list_pair, tmB with 128-row boxes (each CTA loads half of
 // B), p.idesc with M = 256; 16-bit operands; EPI_COPY / EPI_POLY / EPI_SCALE
-// with a 16-bit (out_dtype = dtype or -1) or FP16-pair output.
+// with a 16-bit (out_dtype = dtype or -1) or FP16-pair output, and EPI_FINAL
+// (cres: 8 shares per tile; 16 with many_small).  many_small: 8 epilogue warps
+// per CTA and a 5-stage ring (16-bit outputs and EPI_FINAL).
 std::vector<int4> make_tile_list_pair(int64_t n, int block = 0, int group = 8);
 cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                                const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1);
+                                const GemmParams& p, int grid, cudaStream_t stream, int out_dtype = -1,
+                                bool many_small = false);
+// The whole chain of 16-bit products of a block-diagonal cone in ONE
+// persistent launch (symgemm.cu): products 0 .. nprod - 1 (prods, device
+// memory) over the tile list p.tiles, every CTA taking its tiles of product 0,
+// then of product 1, ...  A tile of product k of block b starts loading once
+// all tiles of product k - 1 of block b are written: done[b nprod + k - 1]
+// counts them (zeroed before the launch), waited on with a bounded spin.  The
+// launch is cooperative (all CTAs resident), which with the product-major
+// order rules out a wait that never ends.  Each product names its operands
+// by tensor map (maps: for slot s, 2 s with 128-row boxes for A and 2 s + 1
+// with 256-row boxes for B); EPI_FINAL writes 8 shares per tile position to
+// p.ep.cres (8 epilogue warps).
+constexpr int kChainMaxSlots = 6;
+struct ChainMaps {
+  CUtensorMap m[2 * kChainMaxSlots];
+};
+struct ChainProduct {
+  int epi;          // EPI_COPY / POLY / SCALE / FINAL
+  int ma, mb;       // tensor maps of A and B
+  int track;        // atomic max of |output| per block (absmax_bits)
+  void* C;          // 16-bit output slot (stacked rows, ld = p.ep.ldc)
+  const void* Y;    // EPI_POLY operand slot
+  float a, b, c, s;
+};
+// Tiles of make_tile_list(n) (any group).
+__host__ __device__ inline int tile_count_of_order(int n) {
+  const int nb = (n + 255) / 256;
+  return nb * (nb + 1) - ((n - (nb - 1) * 256) <= 128 ? 1 : 0);
+}
+cudaError_t launch_symgemm_chain(int dtype, const ChainMaps& maps, const ChainProduct* prods, int nprod,
+                                 const GemmParams& p, int* done, int grid, cudaStream_t stream);
 // split-operand product (symgemm_x3.cu); tm = {A_hi, A_lo, B_hi, B_lo};
 // out: 0 = split pair, 1 = single FP16, (EPI_FINAL) FP32 to the caller's output.
 // Split-operand products: et = DT_TF32X3 (TF32 pairs) or DT_F16X2 (FP16
 // pairs); b_single: A is an FP16 pair and B one FP16 matrix.
+// pair: FP16 pairs on SM pairs (M = 256; tiles from make_tile_list_pair; every
+// tensor map with 128-row boxes), EPI_COPY / POLY / SCALE with a pair output,
+// or a single B with EPI_SCALE and an FP16 output.
 cudaError_t launch_symgemm_x3(int et, bool b_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
-                              int grid, cudaStream_t stream);
+                              int grid, cudaStream_t stream, bool pair = false);
 int num_sms();
 
 // --- batched projection of a block-diagonal cone (batched_kernels.cu) ---
@@ -252,8 +288,9 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
                                      cudaStream_t stream);
 cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* blk, const DevState* st,
                                const int4* items, int nitems, cudaStream_t stream);
+// shares: final-product shares per tile position in cres (4, or 8 from the chain form).
 cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, const double* cres,
-                                   const int* cidx, const int2* crange, cudaStream_t stream);
+                                   const int* cidx, const int2* crange, int shares, cudaStream_t stream);
 bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t cols, int64_t rows, int64_t ld,
                       int box_rows, int row_bytes = kRowBytes16);
 

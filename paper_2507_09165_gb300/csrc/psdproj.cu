@@ -285,13 +285,21 @@ cudaError_t gemm(Plan* p, int epi, const Mat& A, const Mat& B, const Mat* out, c
   const int dt = kind_dtype(PA);
   CUtensorMap tm[4];
   const int rb = x3_row_bytes(b1);
+  const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
+  // FP16-pair stage products on CTA pairs (M = 256, half of B in each CTA)
+  const bool pair = dt == DT_F16X2 && epi != EPI_FINAL &&
+                    (b1 ? (epi == EPI_SCALE && out_mode == 1) : out_mode == 0);
+  const int brows = pair ? 128 : 256;
   if (!encode_tmap(&tm[0], dt, part_ptr(p, PA, 0), n, ldm, 128, rb) ||
       !encode_tmap(&tm[1], dt, part_ptr(p, PA, 1), n, ldm, 128, rb) ||
-      !encode_tmap(&tm[2], dt, part_ptr(p, PB, 0), n, ldm, 256, rb) ||
-      !encode_tmap(&tm[3], dt, part_ptr(p, PB, b1 ? 0 : 1), n, ldm, 256, rb))
+      !encode_tmap(&tm[2], dt, part_ptr(p, PB, 0), n, ldm, brows, rb) ||
+      !encode_tmap(&tm[3], dt, part_ptr(p, PB, b1 ? 0 : 1), n, ldm, brows, rb))
     return cudaErrorInvalidValue;
-  const int out_mode = epi == EPI_FINAL ? 2 : (kind_is_pair(out->kind) ? 0 : 1);
-  return launch_symgemm_x3(dt, b1, epi, out_mode, tm, g, grid, s);
+  if (pair) {
+    g.num_tiles = p->ntiles_pair;
+    g.tiles = p->d_tiles_pair;
+  }
+  return launch_symgemm_x3(dt, b1, epi, out_mode, tm, g, grid, s, pair);
 }
 
 struct PlanOps {
@@ -500,7 +508,7 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   const bool cta_pair = (flags & PSD_EPI_CTA_PAIR) != 0;
   if (flags & ~(PSD_EPI_GROUPED | PSD_EPI_F16_PAIR_OUT | PSD_EPI_CTA_PAIR)) return PSD_ERR_INVALID_ARG;
   if ((grouped || pair_out) && (split || f8 || epi == 3)) return PSD_ERR_INVALID_ARG;
-  if (cta_pair && (split || f8)) return PSD_ERR_INVALID_ARG;
+  if (cta_pair && (f8 || precision == PSD_PREC_FP32)) return PSD_ERR_INVALID_ARG;
   if (grouped && cta_pair) return PSD_ERR_INVALID_ARG;
   if (pair_out && (precision != PSD_PREC_FP16 || epi == 2)) return PSD_ERR_INVALID_ARG;
   if (epi < 0 || epi > 3) return PSD_ERR_INVALID_ARG;
@@ -587,7 +595,7 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   }
   if (enqueue_set_block(ps.d_block, br, s) != cudaSuccess) return PSD_ERR_CUDA;
   cudaError_t e;
-  if (cta_pair) {
+  if (cta_pair && !split) {
     CUtensorMap ta, tb;
     if (!encode_tmap(&ta, dtype, A, n, ld, 128) || !encode_tmap(&tb, dtype, B, n, ld, 128)) return PSD_ERR_CUDA;
     const uint32_t fmt = dtype == DT_BF16 ? 1u : 0u;
@@ -604,10 +612,11 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
     const uint8_t* a8 = static_cast<const uint8_t*>(A);
     const uint8_t* b8 = static_cast<const uint8_t*>(B);
     const int rb = x3_row_bytes(false);
+    const int brows = cta_pair ? 128 : 256;
     if (!encode_tmap(&tm[0], dtype, a8, n, ld, 128, rb) || !encode_tmap(&tm[1], dtype, a8 + pair, n, ld, 128, rb) ||
-        !encode_tmap(&tm[2], dtype, b8, n, ld, 256, rb) || !encode_tmap(&tm[3], dtype, b8 + pair, n, ld, 256, rb))
+        !encode_tmap(&tm[2], dtype, b8, n, ld, brows, rb) || !encode_tmap(&tm[3], dtype, b8 + pair, n, ld, brows, rb))
       return PSD_ERR_CUDA;
-    e = launch_symgemm_x3(dtype, false, epi, epi == 3 ? 2 : 0, tm, g, num_sms(), s);
+    e = launch_symgemm_x3(dtype, false, epi, epi == 3 ? 2 : 0, tm, g, num_sms(), s, cta_pair);
   }
   return e == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
 }

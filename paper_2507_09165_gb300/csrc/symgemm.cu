@@ -599,31 +599,39 @@ __global__ void __launch_bounds__(threads16(EW), 1)
 // 256 x 256 blocks of the upper triangle, diagonal blocks in full (chunks
 // below the diagonal are computed but not written).  Epilogues: copy,
 // polynomial and scale with a 16-bit or FP16-pair output, and the final
-// product (FP32 output; the eight epilogue warps of a pair tile write the
-// complementarity shares of the two 128-row tiles of the one-SM form, in its
-// order: slots 8 t + 4 rank + warp).
-constexpr int kStagesP = 6;
+// product (FP32 output; with 4 epilogue warps per CTA, the eight of a pair
+// tile write the complementarity shares of the two 128-row tiles of the
+// one-SM form, in its order: slots 8 t + 4 rank + warp quarter).
+// EW epilogue warps per CTA: 4 with a 6-stage ring (single matrices, long
+// K), or 8 with a 5-stage ring (the blocks of a block-diagonal cone: K <=
+// 1024, where one warp per 32-lane quarter no longer drains a tile within
+// the next tile's main loop); with 8, a quarter's two warps take alternate
+// 32-column chunks and FINAL writes 16 shares per pair tile (2 EW t + EW rank
+// + warp).
 constexpr int kBHalfBytes = kBM * kRowBytes16;          // 16 KB: 128 rows of B
 constexpr int kStageBytesP = kABytes16 + kBHalfBytes;  // 32 KB
-__host__ __device__ constexpr int smem_bytes_pair() {
-  return 1024 + kStagesP * kStageBytesP + 4 * kEpiWarpBytes + 8 * (2 * kStagesP + 5) + 16;
+__host__ __device__ constexpr int stages_pair(int ew) { return ew == 4 ? 6 : 5; }
+__host__ __device__ constexpr int smem_bytes_pair(int ew = 4) {
+  return 1024 + stages_pair(ew) * kStageBytesP + ew * kEpiWarpBytes + 8 * (2 * stages_pair(ew) + 5) + 16;
 }
-static_assert(smem_bytes_pair() <= 232448, "shared memory per CTA");
+static_assert(smem_bytes_pair(4) <= 232448 && smem_bytes_pair(8) <= 232448, "shared memory per CTA");
 // A wait that has given up leaves copies of this CTA in flight, which signal
 // the leader's barrier: they are given this long to land before the CTA exits.
 constexpr unsigned long long kPairDrainNs = 200000ull;
 
-template <int EPI, int OUTK>
-__global__ void __launch_bounds__(192, 1)
+template <int EPI, int OUTK, int EW = 4>
+__global__ void __launch_bounds__(threads16(EW), 1)
     symgemm16_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                           const GemmParams p, const int bf16_flag) {
   static_assert(OUTK != 1 && (EPI != EPI_FINAL || OUTK == 0), "pair form: 16-bit operands, no e4m3 output");
+  static_assert(EW == 4 || EW == 8, "4 or 8 epilogue warps");
+  constexpr int kStagesP = stages_pair(EW);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* stages = smem;
   uint8_t* epi_stg = smem + kStagesP * kStageBytesP;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_stg + 4 * kEpiWarpBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_stg + EW * kEpiWarpBytes);
   // bars: full[S] | empty[S] | tfull[2] | tempty[2] | drain
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStagesP + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
@@ -647,7 +655,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 8);  // the leader's: 4 epilogue warps of each CTA
+      mbar_init(tempty_bar(a), 2 * EW);  // the leader's: the epilogue warps of both CTAs
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -748,8 +756,11 @@ __global__ void __launch_bounds__(192, 1)
       __syncwarp();
     }
   } else {
-    const int ew = warp & 3;  // tensor-memory lane quarter (warps 2-5)
-    uint8_t* wbuf = epi_stg + (warp - 2) * kEpiWarpBytes;
+    const int ew = warp & 3;         // tensor-memory lane quarter
+    const int ewi = warp - 2;        // epilogue warp 0 .. EW - 1
+    constexpr int kChStep = EW / 4;  // chunks of a quarter, dealt to its EW / 4 warps
+    const int ch_first = ewi / 4;
+    uint8_t* wbuf = epi_stg + ewi * kEpiWarpBytes;
     uint32_t acc = 0, acc_ph = 0;
     unsigned amax_bits = 0;
     int amax_block = -1;
@@ -785,20 +796,24 @@ __global__ void __launch_bounds__(192, 1)
       const int ch_begin = max(0, (r0 - tc.y) >> 5);
       const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
       uint4 ynext[4] = {};
-      if (EPI == EPI_POLY && ch_begin < ch_end) load_y_chunk(Yb, p.ep.ldy, n, r0, tc.y + 32 * ch_begin, lane, ynext);
+      if (EPI == EPI_POLY && ch_begin + ch_first < ch_end)
+        load_y_chunk(Yb, p.ep.ldy, n, r0, tc.y + 32 * (ch_begin + ch_first), lane, ynext);
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
-      double* cdst = EPI == EPI_FINAL && p.ep.cres ? p.ep.cres + 8 * t + 4 * static_cast<int>(rank) : nullptr;
+      double* cdst = EPI == EPI_FINAL && p.ep.cres
+                         ? p.ep.cres + 2 * EW * static_cast<int64_t>(t) + EW * static_cast<int>(rank)
+                         : nullptr;
       ComplAcc cacc;
       ComplAcc* cap = cdst ? &cacc : nullptr;
 #pragma unroll 1
-      for (int ch = ch_begin; ch < ch_end; ++ch) {
+      for (int ch = ch_begin + ch_first; ch < ch_end; ch += kChStep) {
         const int c0 = tc.y + 32 * ch;
         uint4 ycur[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) ycur[k] = ynext[k];
-        if (EPI == EPI_POLY && ch + 1 < ch_end) load_y_chunk(Yb, p.ep.ldy, n, r0, c0 + 32, lane, ynext);
+        if (EPI == EPI_POLY && ch + kChStep < ch_end)
+          load_y_chunk(Yb, p.ep.ldy, n, r0, c0 + 32 * kChStep, lane, ynext);
         uint32_t v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
         if (EPI == EPI_FINAL)
@@ -809,7 +824,7 @@ __global__ void __launch_bounds__(192, 1)
       }
       if (EPI == EPI_FINAL && cdst) {
         const double cs = compl_warp_sum(cacc);
-        if (lane == 0) cdst[ew] = cs;
+        if (lane == 0) cdst[EW == 4 ? ew : ewi] = cs;
       }
       tc_fence_before();
       __syncwarp();
@@ -832,6 +847,285 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc_pair(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag) raise_status(p.ep.status, PSD_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------ chain form
+// All 16-bit products of a block-diagonal cone's chain in one persistent
+// launch (launch_symgemm_chain).  Roles, ring and per-tile arithmetic are
+// those of symgemm16_kernel with 8 epilogue warps, so every output is
+// bit-identical to one launch per product; what changes is that a CTA goes
+// on to its tiles of the next product without waiting for the whole grid:
+// a block's next product starts as soon as that block's previous product is
+// written, so small blocks run ahead while large blocks' tiles are in flight,
+// and no launch boundary leaves SMs idle behind the slowest tile.
+
+// Spins until *ctr >= target; false (and *abort raised) after kWaitLimitNs.
+__device__ __forceinline__ bool wait_count(const int* ctr, int target, volatile int* abort) {
+  if (ld_acquire_gpu(ctr) >= target) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
+    if (ld_acquire_gpu(ctr) >= target) return true;
+    if (*abort) return false;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      *abort = 1;
+      return false;
+    }
+    __nanosleep(64);
+  }
+}
+
+template <int EW>
+__global__ void __launch_bounds__(threads16(EW), 1)
+    symgemm16_chain_kernel(const __grid_constant__ ChainMaps maps, const ChainProduct* __restrict__ prods,
+                           const int nprod, const GemmParams p, int* done, const int bf16_flag) {
+  constexpr int kStages16 = stages16(EW);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* stages = smem;
+  uint8_t* epi_stg = smem + kStages16 * kStageBytes16;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages16 * kStageBytes16 + EW * kEpiWarpBytes);
+  // bars: full[S] | empty[S] | tfull[2] | tempty[2] | drain
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kStages16 + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const bool bf16 = bf16_flag != 0;
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + kStages16 + s); };
+  auto tfull_bar = [&](int a) { return smem_u32(bars + 2 * kStages16 + a); };
+  auto tempty_bar = [&](int a) { return smem_u32(bars + 2 * kStages16 + 2 + a); };
+  const uint32_t drain_bar = smem_u32(bars + 2 * kStages16 + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages16; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), EW);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    for (int k = 0; k < nprod; ++k) {
+      tma_prefetch_desc(&maps.m[prods[k].ma]);
+      tma_prefetch_desc(&maps.m[prods[k].mb]);
+    }
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int last_parity[kStages16];
+      for (int s = 0; s < kStages16; ++s) last_parity[s] = -1;
+      uint32_t s = 0, ph = 0;
+      bool ok = true;
+      for (int k = 0; ok && k < nprod; ++k) {
+        const CUtensorMap* tmA = &maps.m[prods[k].ma];
+        const CUtensorMap* tmB = &maps.m[prods[k].mb];
+        for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+          const int4 tc = p.tiles[t];
+          const BlockRec& bz = p.blocks[tc.z];
+          const int kbn = (bz.n + kBK16 - 1) / kBK16;
+          const int ya = static_cast<int>(bz.off + tc.x), yb = static_cast<int>(bz.off + bz.db + tc.y);
+          if (k > 0) {  // the block's previous product is written (by any CTA)
+            if (!wait_count(done + static_cast<int64_t>(tc.z) * nprod + k - 1, tile_count_of_order(bz.n),
+                            abort_flag)) {
+              ok = false;
+              break;
+            }
+            fence_proxy_async_global();
+          }
+          for (int kb = 0; kb < kbn; ++kb) {
+            if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(full_bar(s), kStageBytes16);
+            const uint32_t a_dst = smem_u32(stages + s * kStageBytes16);
+            tma_load_2d(a_dst, tmA, kb * kBK16, ya, full_bar(s));
+            tma_load_2d(a_dst + kABytes16, tmB, kb * kBK16, yb, full_bar(s));
+            last_parity[s] = static_cast<int>(ph);
+            if (++s == kStages16) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        for (int q = 0; q < kStages16; ++q)
+          if (last_parity[q] >= 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(full_bar(q), static_cast<uint32_t>(last_parity[q])) &&
+                   globaltimer_ns() - t0 < kWaitLimitNs) {
+            }
+          }
+      }
+    }
+  } else if (warp == 1) {
+    uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
+    bool ok = true;
+    for (int k = 0; ok && k < nprod; ++k) {
+      for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+        const int4 tc = p.tiles[t];
+        const int kbn = (p.blocks[tc.z].n + kBK16 - 1) / kBK16;
+        const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);
+        if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * kBN;
+        for (int kb = 0; kb < kbn; ++kb) {
+          if (!wait_bounded(full_bar(s), ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t a_addr = smem_u32(stages + s * kStageBytes16);
+            const uint32_t b_addr = a_addr + kABytes16;
+#pragma unroll
+            for (int q = 0; q < kRowBytes16 / 32; ++q)
+              mma_f16(d_tmem, sw128_kmajor_desc(a_addr + 32 * q), sw128_kmajor_desc(b_addr + 32 * q), idesc,
+                      (kb | q) != 0 ? 1u : 0u);
+            mma_commit(empty_bar(s));
+          }
+          __syncwarp();
+          if (++s == kStages16) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit(tfull_bar(acc));
+        __syncwarp();
+        acc ^= 1u;
+        if (acc == 0) acc_ph ^= 1u;
+      }
+    }
+    if (!ok && lane == 0) {
+      mma_commit(drain_bar);
+      const unsigned long long t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+    __syncwarp();
+  } else {
+    const int ew = warp & 3;         // tensor-memory lane quarter
+    const int ewi = warp - 2;        // epilogue warp 0 .. EW - 1
+    constexpr int kChStep = EW / 4;  // chunks of a quarter, dealt to its EW / 4 warps
+    const int ch_first = ewi / 4;
+    uint8_t* wbuf = epi_stg + ewi * kEpiWarpBytes;
+    uint32_t acc = 0, acc_ph = 0;
+    unsigned amax_bits = 0;
+    int amax_block = -1;
+    auto flush_amax = [&](int blk) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax_bits = max(amax_bits, __shfl_xor_sync(0xffffffffu, amax_bits, o));
+      if (lane == 0 && amax_bits) atomicMax(&p.blocks[blk].st->absmax_bits, amax_bits);
+      amax_bits = 0;
+    };
+    bool ok = true;
+    for (int k = 0; ok && k < nprod; ++k) {
+      const ChainProduct cp = prods[k];
+      GemmParams q = p;  // the product's coefficients for the shared epilogue code
+      q.ep.a = cp.a;
+      q.ep.b = cp.b;
+      q.ep.c = cp.c;
+      q.ep.s = cp.s;
+      const bool track = cp.track != 0;
+      for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+        const int4 tc = p.tiles[t];
+        const BlockRec& br = p.blocks[tc.z];
+        const int n = br.n;
+        const int64_t off = br.off;
+        void* C = cp.epi == EPI_FINAL ? nullptr : static_cast<uint8_t*>(cp.C) + (off + br.dc) * p.ep.ldc * 2;
+        const uint16_t* Yb = cp.epi == EPI_POLY
+                                 ? reinterpret_cast<const uint16_t*>(static_cast<const uint8_t*>(cp.Y) +
+                                                                     (off + br.dy) * p.ep.ldy * 2)
+                                 : nullptr;
+        if (track && amax_block != tc.z) {
+          if (amax_block >= 0) flush_amax(amax_block);
+          amax_block = tc.z;
+        }
+        const int r0 = tc.x + 32 * ew;
+        const int ch_begin = max(0, (r0 - tc.y) >> 5);
+        const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
+        uint4 ynext[4] = {};
+        if (cp.epi == EPI_POLY && ch_begin + ch_first < ch_end)
+          load_y_chunk(Yb, p.ep.ldy, n, r0, tc.y + 32 * (ch_begin + ch_first), lane, ynext);
+        if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const float lam = cp.epi == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
+        double* cdst = cp.epi == EPI_FINAL && p.ep.cres ? p.ep.cres + 8 * static_cast<int64_t>(t) + ewi : nullptr;
+        ComplAcc cacc;
+        ComplAcc* cap = cdst ? &cacc : nullptr;
+#pragma unroll 1
+        for (int ch = ch_begin + ch_first; ch < ch_end; ch += kChStep) {
+          const int c0 = tc.y + 32 * ch;
+          uint4 ycur[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) ycur[i] = ynext[i];
+          if (cp.epi == EPI_POLY && ch + kChStep < ch_end)
+            load_y_chunk(Yb, p.ep.ldy, n, r0, c0 + 32 * kChStep, lane, ynext);
+          uint32_t v[32];
+          tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * ew) << 16) + acc * kBN + 32 * ch, v);
+          if (cp.epi == EPI_COPY)
+            epilogue_chunk16<EPI_COPY, false, 0>(q, br, bf16, n, C, nullptr, r0, c0, v, wbuf, ycur, lane, track,
+                                                 amax_bits);
+          else if (cp.epi == EPI_POLY)
+            epilogue_chunk16<EPI_POLY, false, 0>(q, br, bf16, n, C, nullptr, r0, c0, v, wbuf, ycur, lane, track,
+                                                 amax_bits);
+          else if (cp.epi == EPI_SCALE)
+            epilogue_chunk16<EPI_SCALE, false, 0>(q, br, bf16, n, C, nullptr, r0, c0, v, wbuf, ycur, lane, track,
+                                                  amax_bits);
+          else
+            epilogue_chunk_final(br, r0, c0, v, wbuf, lane, lam, cap);
+        }
+        if (cdst) {
+          const double cs = compl_warp_sum(cacc);
+          if (lane == 0) *cdst = cs;
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        acc ^= 1u;
+        if (acc == 0) acc_ph ^= 1u;
+        if (k + 1 < nprod) {
+          // publish the tile: every epilogue warp's stores, then one increment
+          __threadfence();
+          fence_proxy_async_global();
+          asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+          if (ewi == 0 && lane == 0) red_release_add_gpu(done + static_cast<int64_t>(tc.z) * nprod + k, 1);
+        }
+      }
+      if (track && amax_block >= 0) flush_amax(amax_block);
+      amax_block = -1;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
   }
   if (threadIdx.x == 0 && *abort_flag) raise_status(p.ep.status, PSD_ERR_TIMEOUT);
 }
@@ -1010,7 +1304,7 @@ std::vector<int4> make_tile_list_pair(int64_t n, int block, int group) {
 }
 
 cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                                const GemmParams& p, int grid, cudaStream_t stream, int out_dtype) {
+                                const GemmParams& p, int grid, cudaStream_t stream, int out_dtype, bool many_small) {
   if (p.num_tiles == 0) return cudaSuccess;
   if (dtype != DT_F16 && dtype != DT_BF16) return cudaErrorNotSupported;
   if (out_dtype < 0) out_dtype = dtype;
@@ -1025,15 +1319,22 @@ cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, cons
                            : nullptr;
   else
     k = epi == EPI_COPY ? symgemm16_pair_kernel<EPI_COPY, 2> : epi == EPI_POLY ? symgemm16_pair_kernel<EPI_POLY, 2> : nullptr;
+  const int ew = many_small && outk == 0 ? 8 : 4;
+  if (ew == 8)
+    k = epi == EPI_COPY    ? symgemm16_pair_kernel<EPI_COPY, 0, 8>
+        : epi == EPI_POLY  ? symgemm16_pair_kernel<EPI_POLY, 0, 8>
+        : epi == EPI_SCALE ? symgemm16_pair_kernel<EPI_SCALE, 0, 8>
+        : epi == EPI_FINAL ? symgemm16_pair_kernel<EPI_FINAL, 0, 8>
+                           : nullptr;
   if (!k) return cudaErrorNotSupported;
   static std::mutex attr_mu;
-  static Kernel16 attr_done[8] = {};
+  static Kernel16 attr_done[16] = {};
   {
     std::lock_guard<std::mutex> lk(attr_mu);
     bool set = false;
     for (Kernel16 d : attr_done) set = set || d == k;
     if (!set) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_pair());
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_pair(ew));
       if (e != cudaSuccess) return e;
       for (Kernel16& d : attr_done)
         if (!d) {
@@ -1045,8 +1346,8 @@ cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, cons
   const int pairs = std::max(1, std::min(grid / 2, p.num_tiles));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(2 * pairs);
-  cfg.blockDim = dim3(192);
-  cfg.dynamicSmemBytes = smem_bytes_pair();
+  cfg.blockDim = dim3(threads16(ew));
+  cfg.dynamicSmemBytes = smem_bytes_pair(ew);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1056,6 +1357,33 @@ cudaError_t launch_symgemm_pair(int dtype, int epi, const CUtensorMap& tmA, cons
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k, tmA, tmB, p, out_dtype == DT_BF16 ? 1 : 0);
+}
+
+cudaError_t launch_symgemm_chain(int dtype, const ChainMaps& maps, const ChainProduct* prods, int nprod,
+                                 const GemmParams& p, int* done, int grid, cudaStream_t stream) {
+  if (p.num_tiles == 0 || nprod <= 0) return cudaSuccess;
+  if (dtype != DT_F16 && dtype != DT_BF16) return cudaErrorNotSupported;
+  constexpr int kEW = 8;
+  auto k = symgemm16_chain_kernel<kEW>;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes16(kEW));
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  // one CTA per SM (its shared memory allows no second), all resident: the
+  // cooperative launch fails rather than leave a CTA waiting for an SM
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(std::max(1, std::min(grid, p.num_tiles)));
+  cfg.blockDim = dim3(threads16(kEW));
+  cfg.dynamicSmemBytes = smem_bytes16(kEW);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, maps, prods, nprod, p, done, dtype == DT_BF16 ? 1 : 0);
 }
 
 cudaError_t launch_symgemm(int dtype, int epi, const CUtensorMap& tmA, const CUtensorMap& tmB,

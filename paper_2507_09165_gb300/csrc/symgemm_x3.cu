@@ -49,19 +49,25 @@ constexpr int kPromoteK = 128;  // K elements per promoted chunk (TF32 pairs)
 // the MMAs read the fourth: three times the lookahead of 2 stages of 128-byte
 // rows in the same space); with a single B, 3 stages of 64 KB (A_hi | A_lo |
 // B) of kRowBytesX3Single-byte rows (or 6 of 32 KB).
-template <bool B1>
+// PAIR (FP16 pairs): the product on SM pairs (tcgen05.mma.cta_group::2,
+// M = 256, 256 x 256 tiles): each CTA stages its 128 rows of A_hi and A_lo and
+// half of B's rows, so a stage holds 32 KB (pair B) or 48 KB (single B) and
+// the ring 6 or 4 stages.
+template <bool B1, bool PAIR = false>
 struct X3Cfg {
   static constexpr int kRowBytes = B1 ? kRowBytesX3Single : 64;
   static constexpr bool kSW64 = kRowBytes == 64;
   static constexpr int kABytes = kBM * kRowBytes;
-  static constexpr int kBBytes = kBN * kRowBytes;
-  static constexpr int kStages = (B1 ? 3 : 2) * (128 / kRowBytes);
+  static constexpr int kBBytes = (PAIR ? kBM : kBN) * kRowBytes;
+  static constexpr int kStages = PAIR ? (B1 ? 4 : 6) : (B1 ? 3 : 2) * (128 / kRowBytes);
   static constexpr int kStageBytes = B1 ? 2 * kABytes + kBBytes : 2 * kABytes + 2 * kBBytes;
   static constexpr int smem() {
     return 1024 + kStages * kStageBytes + 4 * kEpiWarpBytes + 8 * (2 * kStages + 5) + 16;
   }
 };
-static_assert(X3Cfg<false>::smem() <= 232448 && X3Cfg<true>::smem() <= 232448, "shared memory per CTA");
+static_assert(X3Cfg<false>::smem() <= 232448 && X3Cfg<true>::smem() <= 232448 &&
+                  X3Cfg<false, true>::smem() <= 232448 && X3Cfg<true, true>::smem() <= 232448,
+              "shared memory per CTA");
 
 __device__ __forceinline__ float tf32_rn(float v) {
   if (!isfinite(v)) return v;
@@ -324,16 +330,21 @@ __device__ __forceinline__ void epilogue_chunk_x3(const GemmParams& p, const Blo
   }
 }
 
-template <int ET, int EPI, int OUT, bool B1>
+// A wait that has given up in the pair form leaves copies of this CTA in
+// flight, which signal the leader's barrier: they are given this long to land.
+constexpr unsigned long long kPairDrainNs = 200000ull;
+
+template <int ET, int EPI, int OUT, bool B1, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, 1)
     symgemm_x3_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                       const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                       const GemmParams p) {
-  constexpr int kStages = X3Cfg<B1>::kStages;
-  constexpr int kStageBytes = X3Cfg<B1>::kStageBytes;
-  constexpr int kABytes = X3Cfg<B1>::kABytes;
-  constexpr int kBBytes = X3Cfg<B1>::kBBytes;
-  constexpr bool kSW64 = X3Cfg<B1>::kSW64;
+  static_assert(!PAIR || (ET == DT_F16X2 && EPI != EPI_FINAL), "pair form: FP16 pairs, stage products");
+  constexpr int kStages = X3Cfg<B1, PAIR>::kStages;
+  constexpr int kStageBytes = X3Cfg<B1, PAIR>::kStageBytes;
+  constexpr int kABytes = X3Cfg<B1, PAIR>::kABytes;
+  constexpr int kBBytes = X3Cfg<B1, PAIR>::kBBytes;
+  constexpr bool kSW64 = X3Cfg<B1, PAIR>::kSW64;
   auto desc = [](uint32_t a) { return kSW64 ? sw64_kmajor_desc(a) : sw128_kmajor_desc(a); };
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -346,6 +357,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // pair form: CTA rank in its cluster of two; tiles are dealt to clusters
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
+  const int cl = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int ncl = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + kStages + s); };
   auto tfull_bar = [&](int a) { return smem_u32(bars + 2 * kStages + a); };
@@ -359,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 4);
+      mbar_init(tempty_bar(a), PAIR ? 8 : 4);  // pair: the leader's, 4 epilogue warps of each CTA
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -370,11 +386,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!B1) tma_prefetch_desc(&tmBl);
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(smem_u32(tmem_holder), kTmemCols);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if (PAIR)
+    cluster_sync_all();  // both CTAs' barriers initialised before any arrival crosses the pair
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
   constexpr bool TF32 = ET == DT_TF32X3;
@@ -388,22 +412,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
       uint32_t s = 0, ph = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+      for (int t = cl; ok && t < p.num_tiles; t += ncl) {
         const int4 tc = p.tiles[t];
         const BlockRec& bz = p.blocks[tc.z];
         const int kbn = (bz.n + kKElems - 1) / kKElems;
-        const int ya = static_cast<int>(bz.off + tc.x), yb = static_cast<int>(bz.off + bz.db + tc.y);
+        // pair form: this CTA's 128 rows of A and its N/2 rows of B
+        const int ya = static_cast<int>(bz.off + tc.x + 128 * static_cast<int>(rank));
+        const int yb = static_cast<int>(bz.off + bz.db + tc.y + (tc.w >> 1) * static_cast<int>(rank));
         for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(full_bar(s), kStageBytes);
           const uint32_t base = smem_u32(stages + s * kStageBytes);
-          tma_load_2d(base, &tmAh, kb * kKElems, ya, full_bar(s));
-          tma_load_2d(base + kABytes, &tmAl, kb * kKElems, ya, full_bar(s));
-          tma_load_2d(base + 2 * kABytes, &tmBh, kb * kKElems, yb, full_bar(s));
-          if (!B1) tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, yb, full_bar(s));
+          if (PAIR) {
+            if (leader) mbar_arrive_expect_tx(full_bar(s), 2 * kStageBytes);  // both CTAs' copies
+            const uint32_t fb = mapa_shared(full_bar(s), 0);
+            tma_load_2d_pair(base, &tmAh, kb * kKElems, ya, fb);
+            tma_load_2d_pair(base + kABytes, &tmAl, kb * kKElems, ya, fb);
+            tma_load_2d_pair(base + 2 * kABytes, &tmBh, kb * kKElems, yb, fb);
+            if (!B1) tma_load_2d_pair(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, yb, fb);
+          } else {
+            mbar_arrive_expect_tx(full_bar(s), kStageBytes);
+            tma_load_2d(base, &tmAh, kb * kKElems, ya, full_bar(s));
+            tma_load_2d(base + kABytes, &tmAl, kb * kKElems, ya, full_bar(s));
+            tma_load_2d(base + 2 * kABytes, &tmBh, kb * kKElems, yb, full_bar(s));
+            if (!B1) tma_load_2d(base + 2 * kABytes + kBBytes, &tmBl, kb * kKElems, yb, full_bar(s));
+          }
           last_parity[s] = static_cast<int>(ph);
           if (++s == kStages) {
             s = 0;
@@ -411,7 +446,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      if (!ok) {
+      if (!ok && PAIR) {
+        // the copies in flight signal the leader's barrier: give them time to land
+        bool any = false;
+        for (int q = 0; q < kStages; ++q) any = any || last_parity[q] >= 0;
+        const unsigned long long t0 = globaltimer_ns();
+        while (any && globaltimer_ns() - t0 < kPairDrainNs) {
+        }
+      } else if (!ok) {
         for (int q = 0; q < kStages; ++q)
           if (last_parity[q] >= 0) {
             const unsigned long long t0 = globaltimer_ns();
@@ -427,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t s = 0, ph = 0, cph = 0;
     bool ok = true;
     constexpr int kChunkBlocks = kPromoteK / kKElems;
-    for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+    for (int t = cl; ok && t < p.num_tiles; t += ncl) {
       const int4 tc = p.tiles[t];
       const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
       const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
@@ -476,10 +518,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     __syncwarp();
-  } else if (warp == 1) {
+  } else if (warp == 1 && (!PAIR || leader)) {  // pair form: the leader issues for both CTAs
     uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
     bool ok = true;
-    for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
+    for (int t = cl; ok && t < p.num_tiles; t += ncl) {
       const int4 tc = p.tiles[t];
       const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
       const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
@@ -506,13 +548,20 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_tf32(d_tmem, desc(ah + off), desc(bh + off), idesc, first);
               mma_tf32(d_tmem, desc(ah + off), desc(bl + off), idesc, 1u);
               mma_tf32(d_tmem, desc(al + off), desc(bh + off), idesc, 1u);
+            } else if (PAIR) {
+              mma_f16_pair(d_tmem, desc(ah + off), desc(bh + off), idesc, first);
+              if (!B1) mma_f16_pair(d_tmem, desc(ah + off), desc(bl + off), idesc, 1u);
+              mma_f16_pair(d_tmem, desc(al + off), desc(bh + off), idesc, 1u);
             } else {
               mma_f16(d_tmem, desc(ah + off), desc(bh + off), idesc, first);
               if (!B1) mma_f16(d_tmem, desc(ah + off), desc(bl + off), idesc, 1u);
               mma_f16(d_tmem, desc(al + off), desc(bh + off), idesc, 1u);
             }
           }
-          mma_commit(empty_bar(s));
+          if (PAIR)
+            mma_commit_pair(empty_bar(s), 3);  // frees the stage in both CTAs
+          else
+            mma_commit(empty_bar(s));
         }
         __syncwarp();
         if (++s == kStages) {
@@ -521,18 +570,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) break;
-      if (lane == 0) mma_commit(tfull_bar(acc));
+      if (lane == 0) {
+        if (PAIR)
+          mma_commit_pair(tfull_bar(acc), 3);
+        else
+          mma_commit(tfull_bar(acc));
+      }
       __syncwarp();
       acc ^= 1u;
       if (acc == 0) acc_ph ^= 1u;
     }
     if (!ok && lane == 0) {
-      mma_commit(drain_bar);
+      // the MMAs already issued, before tensor memory is released
+      if (PAIR)
+        mma_commit_pair(drain_bar, 1);
+      else
+        mma_commit(drain_bar);
       const unsigned long long t0 = globaltimer_ns();
       while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
       }
     }
     __syncwarp();
+  } else if (warp == 1) {
+    // pair form, peer CTA: the leader's MMA warp issues for both
   } else {
     const int ew = warp & 3;
     float* S = reinterpret_cast<float*>(epi + ew * kEpiWarpBytes);
@@ -550,7 +610,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       amax_bits = 0;
     };
-    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x) {
+    // pair form: the peer releases an accumulator through the leader's barrier
+    const uint32_t tempty_leader[2] = {PAIR ? mapa_shared(tempty_bar(0), 0) : 0u,
+                                       PAIR ? mapa_shared(tempty_bar(1), 0) : 0u};
+    for (int t = cl; t < p.num_tiles; t += ncl) {
       const int4 tc = p.tiles[t];
       const BlockRec& br = p.blocks[tc.z];
       const int n = br.n;
@@ -560,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         amax_block = tc.z;
       }
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
-      const int r0 = tc.x + 32 * ew;
+      const int r0 = tc.x + 128 * static_cast<int>(rank) + 32 * ew;
       const int ch_begin = max(0, (r0 - tc.y) >> 5);
       const int ch_end = r0 < n ? min((tc.w + 31) >> 5, (n - tc.y + 31) >> 5) : ch_begin;
       const uint32_t lanes = static_cast<uint32_t>(32 * ew) << 16;
@@ -622,7 +685,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        if (lane == 0) {
+          if (!PAIR || leader)
+            mbar_arrive(tempty_bar(acc));
+          else
+            mbar_arrive_remote(tempty_leader[acc]);
+        }
         acc ^= 1u;
         if (acc == 0) acc_ph ^= 1u;
       }
@@ -630,11 +698,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (track_launch && amax_block >= 0) flush_amax(amax_block);
   }
 
+  // pair form: every operand read, remote arrival and copy of the pair is
+  // complete before either CTA releases tensor memory or exits
   tc_fence_before();
-  __syncthreads();
+  if (PAIR)
+    cluster_sync_all();
+  else
+    __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, kTmemCols);
+    if (PAIR)
+      tmem_dealloc_pair(tmem_base, kTmemCols);
+    else
+      tmem_dealloc(tmem_base, kTmemCols);
   }
   if (threadIdx.x == 0 && *abort_flag && p.ep.status) atomicCAS(p.ep.status, 0, PSD_ERR_TIMEOUT);
 }
@@ -645,6 +721,15 @@ using KernelX3 = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMa
 // Instances: TF32 pairs (the FP32 path: pair outputs, the FP32 final output);
 // FP16 pairs (pair or FP16 outputs); FP16 pair A with a single FP16 B (P X of
 // the mixed precision's pair stages, FP16 output).
+KernelX3 pick_pair(bool b1, int epi, int out) {
+  if (b1) return (epi == EPI_SCALE && out == 1) ? symgemm_x3_kernel<DT_F16X2, EPI_SCALE, 1, true, true> : nullptr;
+  if (out != 0) return nullptr;
+  if (epi == EPI_COPY) return symgemm_x3_kernel<DT_F16X2, EPI_COPY, 0, false, true>;
+  if (epi == EPI_POLY) return symgemm_x3_kernel<DT_F16X2, EPI_POLY, 0, false, true>;
+  if (epi == EPI_SCALE) return symgemm_x3_kernel<DT_F16X2, EPI_SCALE, 0, false, true>;
+  return nullptr;
+}
+
 KernelX3 pick(int et, bool b1, int epi, int out) {
   if (et == DT_TF32X3) {
     if (b1) return nullptr;
@@ -671,11 +756,13 @@ KernelX3 pick(int et, bool b1, int epi, int out) {
 // et: DT_TF32X3 or DT_F16X2; b_single: B is one FP16 matrix (tm[3] unused).
 // tm: A_hi, A_lo, B_hi, B_lo.  out: 0 = split pair, 1 = FP16 (EPI_FINAL: 2, FP32 to the block's out).
 cudaError_t launch_symgemm_x3(int et, bool b_single, int epi, int out, const CUtensorMap* tm, const GemmParams& p,
-                              int grid, cudaStream_t stream) {
+                              int grid, cudaStream_t stream, bool pair) {
   if (p.num_tiles == 0) return cudaSuccess;
-  KernelX3 k = pick(et, b_single, epi, out);
+  if (pair && et != DT_F16X2) return cudaErrorNotSupported;
+  KernelX3 k = pair ? pick_pair(b_single, epi, out) : pick(et, b_single, epi, out);
   if (!k) return cudaErrorNotSupported;
-  const int smem = b_single ? X3Cfg<true>::smem() : X3Cfg<false>::smem();
+  const int smem = pair ? (b_single ? X3Cfg<true, true>::smem() : X3Cfg<false, true>::smem())
+                        : (b_single ? X3Cfg<true>::smem() : X3Cfg<false>::smem());
   static std::mutex done_mu;  // launches come from callers' threads and the request server's
   static KernelX3 done[32];
   static int ndone = 0;
@@ -691,10 +778,26 @@ cudaError_t launch_symgemm_x3(int et, bool b_single, int epi, int out, const CUt
   }
   GemmParams q = p;
   const uint32_t fmt = et == DT_TF32X3 ? 2u : 0u;  // kind::tf32, or kind::f16 with FP16 operands
-  q.idesc = make_idesc(fmt, kBM, 0);  // N comes from each tile
-  const int g = std::max(1, std::min(grid, p.num_tiles));
-  k<<<g, kThreads, smem, stream>>>(tm[0], tm[1], tm[2], tm[3], q);
-  return cudaGetLastError();
+  q.idesc = make_idesc(fmt, pair ? 2 * kBM : kBM, 0);  // N comes from each tile
+  if (!pair) {
+    const int g = std::max(1, std::min(grid, p.num_tiles));
+    k<<<g, kThreads, smem, stream>>>(tm[0], tm[1], tm[2], tm[3], q);
+    return cudaGetLastError();
+  }
+  const int pairs = std::max(1, std::min(grid / 2, p.num_tiles));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, tm[0], tm[1], tm[2], tm[3], q);
 }
 
 }  // namespace psd

@@ -405,3 +405,31 @@ def test_cta_pair_form_rejects_what_it_does_not_run():
     for epi in (b.EPI_CTA_PAIR | b.EPI_GROUPED, b.EPI_CTA_PAIR | 2 | b.EPI_F16_PAIR_OUT):
         with pytest.raises(RuntimeError):
             b.psd_symm_product(n, A, A, ld, C, 0, "fp16", epi, (1.0,))
+
+
+@pytest.mark.parametrize("n", [16, 97, 255, 300, 513, 1000])
+@pytest.mark.parametrize("epi", [0, 1, 2])
+def test_cta_pair_form_of_the_split_product_gives_the_same_bits(n, epi):
+    # The mixed precision's products of FP16 pairs (A_hi B_hi + A_hi B_lo +
+    # A_lo B_hi) on SM pairs and on one SM: the same three tensor products in
+    # the same K order per element, so the same output pair, bit for bit.
+    ld = (n + 7) // 8 * 8
+    rng = np.random.default_rng(70 + n)
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    A = split_pair(0.5 * (G + G.T), "mixed", n, ld)
+    G = rng.standard_normal((n, n)) / np.sqrt(n)
+    B = split_pair(0.5 * (G + G.T), "mixed", n, ld)
+    dev = torch.device("cuda")
+    Ad, Bd = A.to(dev), B.to(dev)
+    params = {0: (), 1: (1.5, -0.7, 0.3), 2: (1.0 / 1.01,)}[epi]
+    outs = []
+    for form in (0, b.EPI_CTA_PAIR):
+        Cd = torch.full_like(Ad, float("nan"))
+        if epi == 1:
+            b.psd_symm_product(n, Ad, Ad, ld, Cd, 0, "mixed", 1 | form, params=params, aux=Ad, ld_aux=ld)
+        else:
+            b.psd_symm_product(n, Ad, Bd, ld, Cd, 0, "mixed", epi | form, params=params)
+        torch.cuda.synchronize()
+        outs.append(Cd.cpu())
+    assert torch.isfinite(outs[0][:, :, :n]).all()
+    assert torch.equal(outs[0].view(torch.int16), outs[1].view(torch.int16))
