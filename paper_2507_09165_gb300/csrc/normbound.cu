@@ -423,23 +423,33 @@ __device__ __forceinline__ void ph_fro(const NBCtx& c) {
   if (threadIdx.x == 0) c.st->fro = sqrt(f);
 }
 
+// The chunk-reducing phases take two chunks per CTA at once, one per half
+// of the CTA (warps 0-3 and 4-7): a chunk pair index cp covers chunks 2 cp and
+// 2 cp + 1.  With one chunk per CTA, orders just above 32 x the CTA count
+// (n = 10,000: 313 chunks, 304 CTAs) left a few CTAs a second chunk and the
+// whole phase waiting for them.
+__device__ __forceinline__ int chunk_of_half(int cp) { return 2 * cp + static_cast<int>(threadIdx.x >> 7); }
+__device__ __forceinline__ bool half_lead_warp() { return (threadIdx.x & 127) < 32; }
+
 // y_e = sum_{bj >= b(e)} P1[bj][e] + sum_{bi <= b(e)} P2[bi][e] for the 32
-// elements e of chunk `ch` (kNT threads): warp w adds the blocks congruent to
-// w mod 8 in double-float, then warp 0 combines the 8 warp sums in a fixed
-// order.  Returns y_e (FP64) in warp 0; other warps return 0.
+// elements e of chunk `ch`, by the 4 warps of this thread's half of the CTA:
+// warp h (0-3 in the half) adds the blocks congruent to h mod 4 in
+// double-float, then the half's first warp combines the 4 warp sums in a fixed
+// order.  Returns y_e (FP64) in that warp; other warps return 0.  Both halves
+// call it together (CTA barriers).
 __device__ __forceinline__ double reduce_partials(const NBCtx& c, int ch, NBShared& sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, hw = w & 3;
   const int e = ch * 32 + lane;
   F2 a{0.f, 0.f}, d{0.f, 0.f};
   if (e < c.n) {
     const int b = e / kSymvTile;
 #pragma unroll 4
-    for (int bj = b + w; bj < c.nb; bj += 8) {
+    for (int bj = b + hw; bj < c.nb; bj += 4) {
       const float2 t = __ldcg(c.P1 + static_cast<int64_t>(bj) * c.npad + e);
       a = f2_add(a, F2{t.x, t.y});
     }
 #pragma unroll 4
-    for (int bi = w; bi <= b; bi += 8) {
+    for (int bi = hw; bi <= b; bi += 4) {
       const float2 t = __ldcg(c.P2 + static_cast<int64_t>(bi) * c.npad + e);
       d = f2_add(d, F2{t.x, t.y});
     }
@@ -448,21 +458,22 @@ __device__ __forceinline__ double reduce_partials(const NBCtx& c, int ch, NBShar
   sh.u.part[w][lane] = make_float2(t.h, t.l);
   __syncthreads();
   double y = 0.0;
-  if (w == 0) {
-    F2 acc{sh.u.part[0][lane].x, sh.u.part[0][lane].y};
+  if (hw == 0) {
+    F2 acc{sh.u.part[w][lane].x, sh.u.part[w][lane].y};
 #pragma unroll
-    for (int q = 1; q < kNT / 32; ++q) acc = f2_add(acc, F2{sh.u.part[q][lane].x, sh.u.part[q][lane].y});
+    for (int q = 1; q < 4; ++q) acc = f2_add(acc, F2{sh.u.part[w + q][lane].x, sh.u.part[w + q][lane].y});
     y = f2_to_d(acc);
   }
   __syncthreads();
   return y;
 }
 
-// u = X v (first product of X (X v)); split u for the second product.
-__device__ __forceinline__ void ph_reduce_split(const NBCtx& c, int ch, double* u, NBShared& sh) {
+// u = X v (first product of X (X v)); split u for the second product.  Chunk pair cp.
+__device__ __forceinline__ void ph_reduce_split(const NBCtx& c, int cp, double* u, NBShared& sh) {
+  const int ch = chunk_of_half(cp);
   const double y = reduce_partials(c, ch, sh);
   const int e = ch * 32 + (threadIdx.x & 31);
-  if (threadIdx.x < 32 && e < c.n) {
+  if (half_lead_warp() && e < c.n) {
     u[e] = y;
     split_d(y, c.vh[e], c.vl[e]);
   }
@@ -510,11 +521,12 @@ __device__ __forceinline__ void chunk_sums(const float2* part, int nch, uint32_t
 }
 
 // w = X u (the second product, reduced); partial dots q_k . w (k <= j) of the
-// chunk into slot k of dots.
-__device__ __forceinline__ void ph_reduce_dots(const NBCtx& c, int ch, int j, NBShared& sh) {
+// chunk into slot k of dots.  Chunk pair cp.
+__device__ __forceinline__ void ph_reduce_dots(const NBCtx& c, int cp, int j, NBShared& sh) {
+  const int ch = chunk_of_half(cp);
   const double y = reduce_partials(c, ch, sh);
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+  if (!half_lead_warp() || ch >= c.npart) return;
+  const int lane = threadIdx.x & 31;
   const int e = ch * 32 + lane;
   if (e < c.n) c.w[e] = y;
   double v[32];
@@ -695,10 +707,11 @@ __device__ __forceinline__ void ph_ritz_norm(const NBCtx& c, int vb, double inv)
 }
 
 // r = X (X q) - sigma q, partial ||r||^2 of the chunk into norms2[ch].
-__device__ __forceinline__ void ph_resid(const NBCtx& c, int ch, NBShared& sh) {
+__device__ __forceinline__ void ph_resid(const NBCtx& c, int cp, NBShared& sh) {
+  const int ch = chunk_of_half(cp);
   const double y = reduce_partials(c, ch, sh);
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+  if (!half_lead_warp() || ch >= c.npart) return;
+  const int lane = threadIdx.x & 31;
   const int e = ch * 32 + lane;
   double r = 0.0;
   if (e < c.n) r = y - __ldcg(&c.st->sigma) * __ldcg(c.q + e);
@@ -871,6 +884,7 @@ __global__ void __launch_bounds__(kNT, 2) nb_persistent_kernel(NBCtx c, unsigned
   GridBarrier gb{sync, 0u};
   int* status = &c.st->status;
   const int G = gridDim.x, b0 = blockIdx.x;
+  const int npair = (c.npart + 1) / 2;  // chunk pairs of the reducing phases
   const float* X = c.args->X;
   const int64_t ld = c.args->ld;
 #define NB_SYNC()                           \
@@ -891,11 +905,11 @@ __global__ void __launch_bounds__(kNT, 2) nb_persistent_kernel(NBCtx c, unsigned
     NB_SYNC();
     if (j == 0 && b0 == 0 && threadIdx.x < 32) ph_fro(c);
     double* u = c.zsave ? c.zsave + j * c.npad : c.u;
-    for (int ch = b0; ch < c.npart; ch += G) ph_reduce_split(c, ch, u, sh);
+    for (int cp = b0; cp < npair; cp += G) ph_reduce_split(c, cp, u, sh);
     NB_SYNC();
     ph_symv_run<false>(c, X, ld, b0, G, (pass++ & 1) != 0, sh);
     NB_SYNC();
-    for (int ch = b0; ch < c.npart; ch += G) ph_reduce_dots(c, ch, j, sh);
+    for (int cp = b0; cp < npair; cp += G) ph_reduce_dots(c, cp, j, sh);
     NB_SYNC();
     ph_orth1(c, b0, G, j, sh);
     NB_SYNC();
@@ -915,11 +929,11 @@ __global__ void __launch_bounds__(kNT, 2) nb_persistent_kernel(NBCtx c, unsigned
   NB_SYNC();
   ph_symv_run<false>(c, X, ld, b0, G, (pass++ & 1) != 0, sh);
   NB_SYNC();
-  for (int ch = b0; ch < c.npart; ch += G) ph_reduce_split(c, ch, c.u, sh);
+  for (int cp = b0; cp < npair; cp += G) ph_reduce_split(c, cp, c.u, sh);
   NB_SYNC();
   ph_symv_run<false>(c, X, ld, b0, G, (pass++ & 1) != 0, sh);
   NB_SYNC();
-  for (int ch = b0; ch < c.npart; ch += G) ph_resid(c, ch, sh);
+  for (int cp = b0; cp < npair; cp += G) ph_resid(c, cp, sh);
   NB_SYNC();
   if (b0 == 0 && threadIdx.x < 32) ph_final(c);
 #undef NB_SYNC
@@ -1195,7 +1209,7 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
       return cudaLaunchKernelEx(&cfg, nb_persistent_kernel, c, L.sync);
     }
   }
-  const int vb = c.nv, rb = c.npart;
+  const int vb = c.nv, rb = c.npart, pb = (c.npart + 1) / 2;  // pb: chunk pairs
   nb_init_kernel<<<vb, kNT, 0, s>>>(c);
   nb_norm0_kernel<<<vb, kNT, 0, s>>>(c);
   int pass = 0;  // products over X so far: odd ones traverse the tiles backwards
@@ -1207,9 +1221,9 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
       nb_symv_kernel<false><<<c.ntiles, kNT, 0, s>>>(c, 1, pass++ & 1);
     }
     double* u = L.zsave ? L.zsave + j * L.npad : L.u;
-    nb_reduce_split_kernel<<<rb, kNT, 0, s>>>(c, u, 1);
+    nb_reduce_split_kernel<<<pb, kNT, 0, s>>>(c, u, 1);
     nb_symv_kernel<false><<<c.ntiles, kNT, 0, s>>>(c, 1, pass++ & 1);
-    nb_reduce_dots_kernel<<<rb, kNT, 0, s>>>(c, j);
+    nb_reduce_dots_kernel<<<pb, kNT, 0, s>>>(c, j);
     nb_orth1_kernel<<<rb, kNT, 0, s>>>(c, j);
     nb_orth2_kernel<<<rb, kNT, 0, s>>>(c, j);
   }
@@ -1219,9 +1233,9 @@ cudaError_t enqueue_norm_bound(const LanczosBufs& L, const DevArgs* args, DevSta
   // (after a breakdown the remaining steps' products do no work, so these two
   // may not continue the alternation; results do not depend on the direction)
   nb_symv_kernel<false><<<c.ntiles, kNT, 0, s>>>(c, 0, pass++ & 1);
-  nb_reduce_split_kernel<<<rb, kNT, 0, s>>>(c, L.u, 0);
+  nb_reduce_split_kernel<<<pb, kNT, 0, s>>>(c, L.u, 0);
   nb_symv_kernel<false><<<c.ntiles, kNT, 0, s>>>(c, 0, pass++ & 1);
-  nb_resid_kernel<<<rb, kNT, 0, s>>>(c);
+  nb_resid_kernel<<<pb, kNT, 0, s>>>(c);
   nb_final_kernel<<<1, 32, 0, s>>>(c);
   return cudaGetLastError();
 }
