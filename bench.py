@@ -30,10 +30,10 @@ METRIC = "ms per n=10k PSD projection at rel err ≤1e-3 vs FP32 path; tensor-pi
 # one ncu capture of the bench's own roofline launch, n = 10,000), valid only while the kernel's
 # sources are the ones captured (sha256 over the files below); null otherwise.
 ROOFLINE_TRAFFIC = {
-    "mixed": {"bytes": 1897260800 + 381659392,
+    "mixed": {"bytes": 2008449536 + 381596416,
               "sources": ("paper_2507_09165_gb300/csrc/symgemm_x3.cu", "paper_2507_09165_gb300/csrc/ptx.cuh"),
-              "sha256": "723920b5d3f1d5b77ab97207224becb831b8fb7f33eb1093294139542cc9d1b9",
-              "profile": "profiles/symgemm_x3_f16pairs_traffic_n10000.md"},
+              "sha256": "63951a9dab827377fb3173a25468fd59c40cead16ca40e1546fee691f1cf7d7e",
+              "profile": "profiles/symgemm_x3_pair_traffic_n10000.md"},
 }
 
 # Tensor-pipe utilisation of one whole projection (sm__pipe_tensor_cycles_active, percent of
@@ -42,9 +42,12 @@ ROOFLINE_TRAFFIC = {
 # small single-kernel captures (n = 8192); over all launches and over the product launches.
 # Valid only while the library's sources are the ones captured (sha256 over every csrc file).
 TENSOR_PIPE = {
-    "mixed": {"projection_pct": 68.47, "products_pct": 77.52,
-              "sha256": "2cbbda358c20a8ef1520e10294be3af5d5b83eabf9827472d43508716b1345fa",
-              "profile": "profiles/tensor_pipe_mixed_n10000.md"},
+    "mixed": {"projection_pct": 77.63, "products_pct": 88.27,
+              "sha256": "5e6b7ad99e808c0d71794d25c96052fe9c70a6c8693623133c5adcf9c8eaf938",
+              "profile": "profiles/tensor_pipe_n10000.md"},
+    "fp16": {"projection_pct": 71.21, "products_pct": 84.29,
+             "sha256": "5e6b7ad99e808c0d71794d25c96052fe9c70a6c8693623133c5adcf9c8eaf938",
+             "profile": "profiles/tensor_pipe_n10000.md"},
 }
 
 def tensor_pipe(prec, n):
@@ -453,8 +456,9 @@ def batched_leg(dev, prec="fp16", reps=5):
                         % (sum(sizes), max(sizes)),
             "precision": prec, "ms": ms, "ms_all": ts, "blocks_per_s": len(sizes) / (ms * 1e-3),
             "schedule": {"chosen": chosen, "product_ms_per_candidate": cand_ms,
-                         "what": "autotuned order of the grouped products' tiles (6 result-invariant candidates, "
-                                 "one first-stage product timed per candidate at plan build)"},
+                         "what": "autotuned order of the grouped products' tiles (6 result-invariant candidates) "
+                                 "and, FP16/BF16, their shape (candidate 6: 256 x 256 tiles on SM pairs); "
+                                 "one first-stage product timed per candidate at plan build"},
             "tflops_22n3": flops / (ms * 1e-3) / 1e12}
 
 
