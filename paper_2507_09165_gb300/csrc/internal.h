@@ -161,6 +161,51 @@ struct GemmParams {
   EpiParams ep;
 };
 
+// A tile and the fields of its block that the producer and MMA roles need.
+struct TileMeta {
+  int4 tc;
+  int n;
+  int64_t off, db;
+};
+// The tiles t0, t0 + stride, ... of a persistent role, with their metadata read
+// ahead: the tile record two tiles on and the block record of the next tile are
+// loaded while the current tile runs (prefetch() before working on cur()).
+// Read on demand, the tile record and then its block's record (a dependent
+// load) put two global-memory latencies between one tile's last K-step and the
+// next tile's first, which tiles with short K loops (a block-diagonal cone's
+// blocks) feel at every boundary.
+class TileStream {
+ public:
+  __device__ __forceinline__ TileStream(const GemmParams& p, int t0, int stride)
+      : tiles_(p.tiles), blocks_(p.blocks), num_(p.num_tiles), t_(t0), stride_(stride) {
+    if (t_ < num_) cur_ = meta(tiles_[t_]);
+    if (t_ + stride_ < num_) tc1_ = tiles_[t_ + stride_];
+  }
+  __device__ __forceinline__ bool valid() const { return t_ < num_; }
+  __device__ __forceinline__ int index() const { return t_; }
+  __device__ __forceinline__ const TileMeta& cur() const { return cur_; }
+  __device__ __forceinline__ void prefetch() {
+    if (t_ + 2 * stride_ < num_) tc2_ = tiles_[t_ + 2 * stride_];
+    if (t_ + stride_ < num_) nxt_ = meta(tc1_);
+  }
+  __device__ __forceinline__ void advance() {
+    t_ += stride_;
+    cur_ = nxt_;
+    tc1_ = tc2_;
+  }
+
+ private:
+  __device__ __forceinline__ TileMeta meta(const int4& tc) const {
+    const BlockRec& b = blocks_[tc.z];
+    return TileMeta{tc, b.n, b.off, b.db};
+  }
+  const int4* tiles_;
+  const BlockRec* blocks_;
+  int num_, t_, stride_;
+  TileMeta cur_{}, nxt_{};
+  int4 tc1_{}, tc2_{};
+};
+
 // Upper-triangle tiles of one order-n matrix: 256 x 256 blocks (I <= J) split
 // into two 128-row tiles; the lower-right tile of a diagonal block starts at
 // its diagonal (128 columns); tile widths are trimmed at n (multiples of 16).

@@ -408,12 +408,12 @@ __global__ void __launch_bounds__(threads16(EW), 1)
       for (int s = 0; s < kStages16; ++s) last_parity[s] = -1;
       uint32_t s = 0, ph = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
-        const int4 tc = p.tiles[t];
-        const BlockRec& bz = p.blocks[tc.z];
+      for (TileStream ts(p, blockIdx.x, gridDim.x); ok && ts.valid(); ts.advance()) {
+        ts.prefetch();
+        const TileMeta& m = ts.cur();
         constexpr int kBK = IN8 ? kBK8 : kBK16;
-        const int kbn = (bz.n + kBK - 1) / kBK;
-        const int ya = static_cast<int>(bz.off + tc.x), yb = static_cast<int>(bz.off + bz.db + tc.y);
+        const int kbn = (m.n + kBK - 1) / kBK;
+        const int ya = static_cast<int>(m.off + m.tc.x), yb = static_cast<int>(m.off + m.db + m.tc.y);
         for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
@@ -444,10 +444,11 @@ __global__ void __launch_bounds__(threads16(EW), 1)
   } else if (warp == 1) {
     uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
     bool ok = true;
-    for (int t = blockIdx.x; ok && t < p.num_tiles; t += gridDim.x) {
-      const int4 tc = p.tiles[t];
+    for (TileStream ts(p, blockIdx.x, gridDim.x); ok && ts.valid(); ts.advance()) {
+      ts.prefetch();
+      const int4 tc = ts.cur().tc;
       constexpr int kBK = IN8 ? kBK8 : kBK16;
-      const int kbn = (p.blocks[tc.z].n + kBK - 1) / kBK;
+      const int kbn = (ts.cur().n + kBK - 1) / kBK;
       const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
       if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
         ok = false;
@@ -676,13 +677,14 @@ __global__ void __launch_bounds__(threads16(EW), 1)
     if (lane == 0) {
       uint32_t s = 0, ph = 0;
       bool ok = true, issued = false;
-      for (int t = cl; ok && t < p.num_tiles; t += ncl) {
-        const int4 tc = p.tiles[t];
-        const BlockRec& bz = p.blocks[tc.z];
-        const int kbn = (bz.n + kBK16 - 1) / kBK16;
+      for (TileStream ts(p, cl, ncl); ok && ts.valid(); ts.advance()) {
+        ts.prefetch();
+        const TileMeta& m = ts.cur();
+        const int4 tc = m.tc;
+        const int kbn = (m.n + kBK16 - 1) / kBK16;
         // this CTA's 128 rows of A and its N/2 rows of B
-        const int ya = static_cast<int>(bz.off + tc.x + 128 * static_cast<int>(rank));
-        const int yb = static_cast<int>(bz.off + bz.db + tc.y + (tc.w >> 1) * static_cast<int>(rank));
+        const int ya = static_cast<int>(m.off + tc.x + 128 * static_cast<int>(rank));
+        const int yb = static_cast<int>(m.off + m.db + tc.y + (tc.w >> 1) * static_cast<int>(rank));
         for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
@@ -710,9 +712,10 @@ __global__ void __launch_bounds__(threads16(EW), 1)
     if (leader) {
       uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
       bool ok = true;
-      for (int t = cl; ok && t < p.num_tiles; t += ncl) {
-        const int4 tc = p.tiles[t];
-        const int kbn = (p.blocks[tc.z].n + kBK16 - 1) / kBK16;
+      for (TileStream ts(p, cl, ncl); ok && ts.valid(); ts.advance()) {
+        ts.prefetch();
+        const int4 tc = ts.cur().tc;
+        const int kbn = (ts.cur().n + kBK16 - 1) / kBK16;
         const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // M = 256, N = tile width
         if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
           ok = false;

@@ -412,13 +412,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
       uint32_t s = 0, ph = 0;
       bool ok = true;
-      for (int t = cl; ok && t < p.num_tiles; t += ncl) {
-        const int4 tc = p.tiles[t];
-        const BlockRec& bz = p.blocks[tc.z];
-        const int kbn = (bz.n + kKElems - 1) / kKElems;
+      for (TileStream ts(p, cl, ncl); ok && ts.valid(); ts.advance()) {
+        ts.prefetch();
+        const TileMeta& m = ts.cur();
+        const int4 tc = m.tc;
+        const int kbn = (m.n + kKElems - 1) / kKElems;
         // pair form: this CTA's 128 rows of A and its N/2 rows of B
-        const int ya = static_cast<int>(bz.off + tc.x + 128 * static_cast<int>(rank));
-        const int yb = static_cast<int>(bz.off + bz.db + tc.y + (tc.w >> 1) * static_cast<int>(rank));
+        const int ya = static_cast<int>(m.off + tc.x + 128 * static_cast<int>(rank));
+        const int yb = static_cast<int>(m.off + m.db + tc.y + (tc.w >> 1) * static_cast<int>(rank));
         for (int kb = 0; kb < kbn; ++kb) {
           if (!wait_bounded(empty_bar(s), ph ^ 1u, abort_flag)) {
             ok = false;
@@ -469,9 +470,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t s = 0, ph = 0, cph = 0;
     bool ok = true;
     constexpr int kChunkBlocks = kPromoteK / kKElems;
-    for (int t = cl; ok && t < p.num_tiles; t += ncl) {
-      const int4 tc = p.tiles[t];
-      const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
+    for (TileStream ts(p, cl, ncl); ok && ts.valid(); ts.advance()) {
+      ts.prefetch();
+      const int4 tc = ts.cur().tc;
+      const int kbn = (ts.cur().n + kKElems - 1) / kKElems;
       const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
       for (int kc = 0; ok && kc < kbn; kc += kChunkBlocks) {
         if (!wait_bounded(tempty_bar(0), cph ^ 1u, abort_flag)) {
@@ -521,9 +523,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1 && (!PAIR || leader)) {  // pair form: the leader issues for both CTAs
     uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
     bool ok = true;
-    for (int t = cl; ok && t < p.num_tiles; t += ncl) {
-      const int4 tc = p.tiles[t];
-      const int kbn = (p.blocks[tc.z].n + kKElems - 1) / kKElems;
+    for (TileStream ts(p, cl, ncl); ok && ts.valid(); ts.advance()) {
+      ts.prefetch();
+      const int4 tc = ts.cur().tc;
+      const int kbn = (ts.cur().n + kKElems - 1) / kKElems;
       const uint32_t idesc = p.idesc | (static_cast<uint32_t>(tc.w >> 3) << 17);  // N = tile width
       if (!wait_bounded(tempty_bar(acc), acc_ph ^ 1u, abort_flag)) {
         ok = false;
