@@ -387,6 +387,24 @@ psd_status_t psd_project_deflate(int64_t n, const float *X, int64_t ld, float *o
                                  psd_precision_t precision, int32_t kmax, psd_info_t *d_info,
                                  int32_t *d_kused, psd_stream_t stream);
 
+/* ---- Host-side fault injection (tests) ----------------------------------- */
+/* No counterpart in the paper.  Sets a knob of the norm bound's kernels on the
+ * current device for calls made after this one (captured graphs included):
+ *   PSD_DEBUG_BOUND_SCALE (value > 0, default 1): lam~ is multiplied by value;
+ *     below 1 the filter sees a spectrum beyond its basin and the report must
+ *     show the overshoot (PSD_ERR_BOUND, or PSD_ERR_NONFINITE when the chain
+ *     diverges);
+ *   PSD_DEBUG_BARRIER_LIMIT_NS (value >= 0, default 4e9): how long a grid
+ *     barrier of the persistent norm bound waits before it gives up; 0 makes
+ *     every barrier that is not already complete give up at once, so the bound
+ *     and a projection built on it report PSD_ERR_TIMEOUT (the kernel's CTAs
+ *     leave at their next barrier; nothing hangs or faults).
+ * PSD_ERR_INVALID_ARG for an unknown knob or a value out of range,
+ * PSD_ERR_CUDA if the copy to the device failed.  Synchronous. */
+#define PSD_DEBUG_BOUND_SCALE 1
+#define PSD_DEBUG_BARRIER_LIMIT_NS 2
+psd_status_t psd_debug_set(int32_t knob, double value);
+
 /* ---- Host-only queries (no GPU needed) ----------------------------------- */
 const char *psd_status_string(psd_status_t status);
 /* Copies the library's schedule for `precision`: *T stages, coef[3*t + {0,1,2}]

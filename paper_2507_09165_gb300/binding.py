@@ -86,6 +86,7 @@ _SIGS = {
     "psd_project_deflate": ([_I64, _VP, _I64, _VP, _I64, _I32, _I32, _VP, _VP, _VP], _I32),
     "psd_batched_force_schedule": ([_I32], _I32),
     "psd_batched_force_form": ([_I32], _I32),
+    "psd_debug_set": ([_I32, ctypes.c_double], _I32),
     "psd_batched_last_tuning": ([ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)], _I32),
 }
 
@@ -164,6 +165,16 @@ def psd_batched_force_form(form):
     """Product form of batched plans built next: 1 chain (one persistent launch), 0 one launch
     per product, -1 default (chain where it applies)."""
     return int(lib().psd_batched_force_form(int(form)))
+
+
+DEBUG_BOUND_SCALE = 1         # PSD_DEBUG_BOUND_SCALE
+DEBUG_BARRIER_LIMIT_NS = 2    # PSD_DEBUG_BARRIER_LIMIT_NS
+
+
+def psd_debug_set(knob, value):
+    """Host-side fault injection into the norm bound (test hook): knob 1 = factor on lam~,
+    knob 2 = grid-barrier wait limit in ns."""
+    _check(lib().psd_debug_set(int(knob), float(value)), "psd_debug_set")
 
 
 def psd_batched_last_tuning():

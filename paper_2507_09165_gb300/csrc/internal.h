@@ -340,6 +340,9 @@ bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t col
                       int box_rows, int row_bytes = kRowBytes16);
 
 // --- norm bound and cast (normbound.cu) ---
+// Host-side fault injection (psd_debug_set): knob 1 = factor on lam~, knob 2 =
+// grid-barrier wait limit in ns; current device.
+cudaError_t set_norm_bound_debug(int knob, double value);
 struct LanczosBufs {
   int64_t n, npad;
   int nb;                // 128-blocks

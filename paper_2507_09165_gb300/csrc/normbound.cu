@@ -36,6 +36,15 @@ namespace psd {
 namespace {
 
 constexpr uint64_t kSeed = 0x243F6A8885A308D3ull;  // Lanczos start vector seed
+
+// Host-side fault injection (psd_debug_set): a factor applied to lam~ (1.0:
+// none; a factor below 1 drives the chain past the composite's basin and
+// exercises the overshoot report) and the limit of the grid barriers' waits
+// (0: every barrier that is not already complete gives up at once and the
+// bound returns PSD_ERR_TIMEOUT).  Read by the kernels at run time, so
+// captured graphs see the current values.
+__device__ double g_debug_bound_scale = 1.0;
+__device__ unsigned long long g_debug_barrier_limit_ns = kWaitLimitNs;
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 
 // ------------------------------------------------------- double-float helpers
@@ -746,6 +755,7 @@ __device__ __forceinline__ void ph_final(const NBCtx& c) {
   double lam = sqrt(fmax(sigma + r, 0.0));
   lam = fmax(lam, fro / sqrt(static_cast<double>(c.n)));
   lam = fmax(lam, md);
+  lam *= g_debug_bound_scale;  // 1.0 unless a test injects a bound that is too small
   st->resid = r;
   st->maxdiag = md;
   const bool finite = isfinite(fro2) && isfinite(lam) && isfinite(sigma);
@@ -853,13 +863,19 @@ struct GridBarrier {
       __threadfence();
       atomicAdd(sync, 1u);
       int ok = 1;
+      const unsigned long long limit = g_debug_barrier_limit_ns;
       const unsigned long long t0 = globaltimer_ns();
       while (ld_acquire_u32(sync) < target) {
         if (ld_acquire_u32(sync + 1) != 0u) {
+          // another CTA gave up; record it too: the first phase resets the
+          // status word in CTA 0, which may run after that CTA's record, and
+          // every CTA (CTA 0 included) leaves through a barrier after its own
+          // first phase
+          atomicCAS(status, 0, PSD_ERR_TIMEOUT);
           ok = 0;
           break;
         }
-        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        if (globaltimer_ns() - t0 >= limit) {  // >=: a zero limit gives up on the first poll
           atomicExch(sync + 1, 1u);
           atomicCAS(status, 0, PSD_ERR_TIMEOUT);
           ok = 0;
@@ -1092,6 +1108,15 @@ __global__ void __launch_bounds__(kComplSumThreads)
 }
 
 }  // namespace
+
+cudaError_t set_norm_bound_debug(int knob, double value) {
+  if (knob == 1) return cudaMemcpyToSymbol(g_debug_bound_scale, &value, sizeof(double));
+  if (knob == 2) {
+    const unsigned long long ns = static_cast<unsigned long long>(value);
+    return cudaMemcpyToSymbol(g_debug_barrier_limit_ns, &ns, sizeof(ns));
+  }
+  return cudaErrorInvalidValue;
+}
 
 size_t lanczos_bytes(int64_t n) {
   const int64_t npad = (n + 255) / 256 * 256;

@@ -621,6 +621,19 @@ psd_status_t psd_symm_product(int64_t n, const void* A, const void* B, int64_t l
   return e == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
 }
 
+psd_status_t psd_debug_set(int32_t knob, double value) {
+  if (knob == PSD_DEBUG_BOUND_SCALE) {
+    if (!(value > 0.0) || !std::isfinite(value)) return PSD_ERR_INVALID_ARG;
+  } else if (knob == PSD_DEBUG_BARRIER_LIMIT_NS) {
+    if (!(value >= 0.0) || !(value <= 6.0e10)) return PSD_ERR_INVALID_ARG;  // at most a minute
+  } else {
+    return PSD_ERR_INVALID_ARG;
+  }
+  psd_status_t st = check_device();
+  if (st != PSD_OK) return st;
+  return set_norm_bound_debug(knob, value) == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
+}
+
 const char* psd_status_string(psd_status_t status) {
   switch (status) {
     case PSD_OK: return "ok";
