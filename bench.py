@@ -30,9 +30,9 @@ METRIC = "ms per n=10k PSD projection at rel err ≤1e-3 vs FP32 path; tensor-pi
 # one ncu capture of the bench's own roofline launch, n = 10,000), valid only while the kernel's
 # sources are the ones captured (sha256 over the files below); null otherwise.
 ROOFLINE_TRAFFIC = {
-    "mixed": {"bytes": 2008449536 + 381596416,
+    "mixed": {"bytes": 2234340608 + 381945600,
               "sources": ("paper_2507_09165_gb300/csrc/symgemm_x3.cu", "paper_2507_09165_gb300/csrc/ptx.cuh"),
-              "sha256": "63951a9dab827377fb3173a25468fd59c40cead16ca40e1546fee691f1cf7d7e",
+              "sha256": "4df80dbaa3b2fbc1dcc36d6d68e3344d1b60ed30f4da79b31f7d584e8cd7a311",
               "profile": "profiles/symgemm_x3_pair_traffic_n10000.md"},
 }
 
@@ -42,11 +42,11 @@ ROOFLINE_TRAFFIC = {
 # small single-kernel captures (n = 8192); over all launches and over the product launches.
 # Valid only while the library's sources are the ones captured (sha256 over every csrc file).
 TENSOR_PIPE = {
-    "mixed": {"projection_pct": 77.63, "products_pct": 88.27,
-              "sha256": "5e6b7ad99e808c0d71794d25c96052fe9c70a6c8693623133c5adcf9c8eaf938",
+    "mixed": {"projection_pct": 77.04, "products_pct": 87.45,
+              "sha256": "97ed6da017ba2f3c5f3e2d00c52c8fe13e23a69e230a66352602909e14421a01",
               "profile": "profiles/tensor_pipe_n10000.md"},
-    "fp16": {"projection_pct": 71.21, "products_pct": 84.29,
-             "sha256": "5e6b7ad99e808c0d71794d25c96052fe9c70a6c8693623133c5adcf9c8eaf938",
+    "fp16": {"projection_pct": 70.63, "products_pct": 83.44,
+             "sha256": "97ed6da017ba2f3c5f3e2d00c52c8fe13e23a69e230a66352602909e14421a01",
              "profile": "profiles/tensor_pipe_n10000.md"},
 }
 
