@@ -40,7 +40,7 @@ def model_error(prec, X, lam_tilde):
                                emulate.named_plan(prec, len(coefs)))
 
 
-def _judge(prec, rel_f, what, model_fn):
+def _assess(prec, rel_f, what, model_fn):
     """None if rel_f meets the bar; the known-miss message if the miss is
     covered by the rounding model (model_fn() -> the model's error in the same
     metric); a failed assertion otherwise."""
@@ -84,13 +84,13 @@ def check_rel_f(prec, rel_f, X=None, lam_tilde=None, what="", model_input=None, 
 
 def check_all(prec, results):
     """check_rel_f over several results (rel_f, X, lam_tilde, what[, model_input[, model_fn]]):
-    every result is judged, then one expected failure lists the known misses."""
+    every result is assessed, then one expected failure lists the known misses."""
     misses = []
     for r in results:
         rel_f, X, lam_tilde, what = r[:4]
         mi = r[4] if len(r) > 4 else None
         fn = r[5] if len(r) > 5 and r[5] is not None else _model_fn(prec, X, lam_tilde, mi)
-        m = _judge(prec, rel_f, what, fn)
+        m = _assess(prec, rel_f, what, fn)
         if m:
             misses.append(m)
     if misses:

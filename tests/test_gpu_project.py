@@ -272,7 +272,7 @@ def test_rank_one_closed_form(prec):
         # eigenvalue: the error is measured relative to |s|
         err = np.linalg.norm(o - F) / abs(s)
 
-        def model(X=X, F=F, s=s, lt=info["lambda_bound"]):  # bound now: judged after the loop
+        def model(X=X, F=F, s=s, lt=info["lambda_bound"]):  # bound now: assessed after the loop
             out_m, _, _ = emulate.chain_rounded(X.astype(np.float64), lt, coefs, scales, emulate.named_plan(prec))
             return np.linalg.norm(out_m - F) / abs(s)
         results.append((err, None, None, "rank one, s = %g" % s, None, model if prec != "fp32" else None))
