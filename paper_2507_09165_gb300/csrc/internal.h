@@ -75,9 +75,10 @@ struct BlockRec {
   // relative to `off` (the A operand's first row).  Zero when every operand of
   // the block sits at the same rows of its own buffer.
   int64_t db, dc, dy;
-  // EPI_FINAL with EpiParams::cres unset: if set, warp w of the tile at launch
-  // position t writes its share of <out, X - out> to cres[4 (t + cres_shift) + w]
-  // (a served request: its tiles' positions in its own tile list).
+  // EPI_FINAL with EpiParams::cres unset: if set, the shares of <out, X - out>
+  // of the tile at launch position t go to cres at the tile's position in the
+  // request's own tile list, t + cres_shift (a served request; 4 per 128-row
+  // tile, 8 per tile on SM pairs: 4 (2 (t + cres_shift) + rank) + warp).
   double* cres;
   int64_t cres_shift;
 };

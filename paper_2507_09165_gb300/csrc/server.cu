@@ -76,8 +76,9 @@ struct Request {
   int g = 0;         // product of the stage in progress: 0 Y, 1 P, 2 X_t, 3 final
   int k = 0;         // tiles of that product done
   int ntiles = 0;    // bound on the tile count (admission)
-  std::vector<int4> tl;  // tile list of order n
-  double* cres = nullptr;  // shares of <out, X - out>, 4 per tile of tl (arena rows after the matrices)
+  std::vector<int4> tl;  // tile list of order n: 256 x 256 tiles on SM pairs (make_tile_list_pair)
+  double* cres = nullptr;  // shares of <out, X - out>, 8 per tile of tl in the one-SM order (arena rows
+                           // after the matrices)
   Clock::time_point t_submit;
   double latency_ms = 0.0;
   psd_info_t info{};
@@ -128,7 +129,8 @@ int64_t tiles_of(int64_t n) {
 }
 
 // Arena rows of a request of order n: its four matrices, then its shares of
-// <out, X - out> (4 doubles per tile) in whole rows of ldm 16-bit elements.
+// <out, X - out> (8 doubles per 256 x 256 tile, 4 per 128-row half: tiles_of(n)
+// halves) in whole rows of ldm 16-bit elements.
 int64_t rows_of(int64_t ldm, int64_t n) {
   const int64_t share_bytes = 4 * static_cast<int64_t>(sizeof(double)) * tiles_of(n);
   return 4 * n + (share_bytes + 2 * ldm - 1) / (2 * ldm);
@@ -154,7 +156,7 @@ struct psd_server {
   uint8_t* h_stage[psd::kRing] = {};
   size_t stage_bytes = 0;
   uint16_t* arena = nullptr;
-  CUtensorMap tmA[2], tmB[2];  // [0] FP16, [1] BF16 views of the arena
+  CUtensorMap tmA[2], tmB[2];  // [0] FP16, [1] BF16 views of the arena (128-row boxes: the pair form)
   // streams and events
   cudaStream_t main = nullptr;
   cudaStream_t lane[psd::kLanes] = {};
@@ -366,11 +368,11 @@ cudaError_t step_gemm(psd_server* s, int dti, int epi, const BlockRec* d_blocks,
   g.ep.per_block_coef = 1;
   g.ep.absmax_blocks = epi == EPI_SCALE ? 2 : 0;
   const uint32_t fmt = dti == 1 ? 1u : 0u;
-  g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (8u << 24);
-  const int grid = std::min(num_sms(), ntiles);
+  g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (16u << 24);  // M = 256: tiles on SM pairs
   ++launches;
-  // (4 epilogue warps: served steps mix large requests, whose main loops want the 4-stage ring)
-  return launch_symgemm(dti == 1 ? DT_BF16 : DT_F16, epi, s->tmA[dti], s->tmB[dti], g, grid, s->main);
+  // SM pairs with 4 epilogue warps per CTA: served steps mix large requests,
+  // whose long main loops want the 6-stage ring
+  return launch_symgemm_pair(dti == 1 ? DT_BF16 : DT_F16, epi, s->tmA[dti], s->tmB[dti], g, num_sms(), s->main);
 }
 
 // Builds and enqueues one scheduler step over `run`.  A step is one grouped
@@ -460,7 +462,7 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
   for (int i : order) {
     Request* r = run[i];
     const int nt = static_cast<int>(r->tl.size());
-    const int64_t cost = (r->n + 63) / 64;  // K-blocks of 64 per tile
+    const int64_t cost = 2 * ((r->n + 63) / 64);  // K-blocks of 64 per 256-row tile (two 128-row tiles)
     Cursor c{r->stage, r->g, r->k, false};
     bool any = false;
     for (;;) {
@@ -516,7 +518,7 @@ bool enqueue_step(psd_server* s, const std::vector<Request*>& run, int& launches
   int nf = 0;
   for (int i = 0; i < nrun; ++i)
     if (next[i].done) {
-      hfin[nf++] = FinRec{run[i]->slot, 4 * static_cast<int>(run[i]->tl.size()), run[i]->cres};
+      hfin[nf++] = FinRec{run[i]->slot, 8 * static_cast<int>(run[i]->tl.size()), run[i]->cres};
       fin_ids.push_back(run[i]->id);
     }
   {
@@ -804,7 +806,7 @@ extern "C" psd_status_t psd_server_create(size_t hbm_budget_bytes, int32_t devic
     ok = cudaEventCreateWithFlags(&s->prep_ev[k], cudaEventDisableTiming) == cudaSuccess;
   for (int d = 0; ok && d < 2; ++d)
     ok = encode_tmap_rows(&s->tmA[d], d ? DT_BF16 : DT_F16, s->arena, s->ldm, rows, s->ldm, 128) &&
-         encode_tmap_rows(&s->tmB[d], d ? DT_BF16 : DT_F16, s->arena, s->ldm, rows, s->ldm, 256);
+         encode_tmap_rows(&s->tmB[d], d ? DT_BF16 : DT_F16, s->arena, s->ldm, rows, s->ldm, 128);
   ok = ok && cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -841,7 +843,7 @@ extern "C" psd_status_t psd_server_submit(psd_server_t* s, int64_t n, const floa
   r->dt = precision == PSD_PREC_BF16 ? DT_BF16 : DT_F16;
   r->ready = reinterpret_cast<cudaEvent_t>(ready);
   r->ntiles = static_cast<int>(tiles_of(n));
-  if (n > 0) r->tl = make_tile_list(n, 0);
+  if (n > 0) r->tl = make_tile_list_pair(n, 0);
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);

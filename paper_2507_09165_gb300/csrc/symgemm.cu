@@ -804,8 +804,12 @@ __global__ void __launch_bounds__(threads16(EW), 1)
       if (!wait_bounded(tfull_bar(acc), acc_ph, abort_flag)) break;
       tc_fence_after();
       const float lam = EPI == EPI_FINAL ? static_cast<float>(br.st->lambda) : 0.f;
-      double* cdst = EPI == EPI_FINAL && p.ep.cres
-                         ? p.ep.cres + 2 * EW * static_cast<int64_t>(t) + EW * static_cast<int>(rank)
+      // shares at the launch position t, or (a served request) at its tile's
+      // position in the request's own list, t + cres_shift
+      double* cdst = nullptr;
+      if (EPI == EPI_FINAL)
+        cdst = p.ep.cres ? p.ep.cres + 2 * EW * static_cast<int64_t>(t) + EW * static_cast<int>(rank)
+               : br.cres ? br.cres + 2 * EW * (static_cast<int64_t>(t) + br.cres_shift) + EW * static_cast<int>(rank)
                          : nullptr;
       ComplAcc cacc;
       ComplAcc* cap = cdst ? &cacc : nullptr;
