@@ -30,7 +30,7 @@ METRIC = "ms per n=10k PSD projection at rel err ≤1e-3 vs FP32 path; tensor-pi
 # one ncu capture of the bench's own roofline launch, n = 10,000), valid only while the kernel's
 # sources are the ones captured (sha256 over the files below); null otherwise.
 ROOFLINE_TRAFFIC = {
-    "mixed": {"bytes": 2234340608 + 381945600,
+    "mixed": {"bytes": 2117522688 + 381887744,
               "sources": ("paper_2507_09165_gb300/csrc/symgemm_x3.cu", "paper_2507_09165_gb300/csrc/ptx.cuh"),
               "sha256": "4df80dbaa3b2fbc1dcc36d6d68e3344d1b60ed30f4da79b31f7d584e8cd7a311",
               "profile": "profiles/symgemm_x3_pair_traffic_n10000.md"},
@@ -42,11 +42,11 @@ ROOFLINE_TRAFFIC = {
 # small single-kernel captures (n = 8192); over all launches and over the product launches.
 # Valid only while the library's sources are the ones captured (sha256 over every csrc file).
 TENSOR_PIPE = {
-    "mixed": {"projection_pct": 77.04, "products_pct": 87.45,
-              "sha256": "97ed6da017ba2f3c5f3e2d00c52c8fe13e23a69e230a66352602909e14421a01",
+    "mixed": {"projection_pct": 77.15, "products_pct": 87.68,
+              "sha256": "bccd2c11e7f7b09d013ac892c0f0fc951f2c6cea296fb7df91ea48dfe1d53de1",
               "profile": "profiles/tensor_pipe_n10000.md"},
-    "fp16": {"projection_pct": 70.63, "products_pct": 83.44,
-             "sha256": "97ed6da017ba2f3c5f3e2d00c52c8fe13e23a69e230a66352602909e14421a01",
+    "fp16": {"projection_pct": 70.98, "products_pct": 83.82,
+             "sha256": "bccd2c11e7f7b09d013ac892c0f0fc951f2c6cea296fb7df91ea48dfe1d53de1",
              "profile": "profiles/tensor_pipe_n10000.md"},
 }
 
