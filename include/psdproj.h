@@ -345,6 +345,21 @@ int32_t psd_batched_force_schedule(int32_t index);
  * Returns the previous setting.  Host-only. */
 int32_t psd_batched_force_form(int32_t form);
 
+/* Form of the batched norm bound of plans built after the call: 1 = ONE
+ * launch of resident CTAs that claim work items (a block's start vector,
+ * mat-vec tiles, reductions, Lanczos steps, Ritz vector, bound) from a fixed
+ * list in order and wait, bounded, only for the block's own earlier items,
+ * counted per block, so that the Lanczos steps of large blocks overlap the
+ * mat-vec tiles of the others; 0 or -1 (the default) = one grouped launch per
+ * phase (about 125 launches, every block of a phase before any block of the
+ * next).  The one-launch form measured slower on 512 blocks of orders 16-1024
+ * (5.1-5.3 against 4.8-5.0 ms per call): its Lanczos steps, sharing SMs with
+ * streaming mat-vec tiles, wait longer on their vector loads than the overlap
+ * saves.  Both forms run the same arithmetic per block in the same order:
+ * outputs and reports are bit-identical.  Returns the previous setting.
+ * Host-only. */
+int32_t psd_batched_force_bound(int32_t form);
+
 /* Schedule of the most recently built batched plan: *chosen (0..6),
  * *candidates (7 for FP16 / BF16, else 6) and, if ms is not NULL, the
  * measured ms per candidate (ms[*candidates]; zeros when the schedule was
@@ -395,10 +410,12 @@ psd_status_t psd_project_deflate(int64_t n, const float *X, int64_t ld, float *o
  *     show the overshoot (PSD_ERR_BOUND, or PSD_ERR_NONFINITE when the chain
  *     diverges);
  *   PSD_DEBUG_BARRIER_LIMIT_NS (value >= 0, default 4e9): how long a grid
- *     barrier of the persistent norm bound waits before it gives up; 0 makes
- *     every barrier that is not already complete give up at once, so the bound
- *     and a projection built on it report PSD_ERR_TIMEOUT (the kernel's CTAs
- *     leave at their next barrier; nothing hangs or faults).
+ *     barrier of the persistent norm bound, or a dependency wait of the
+ *     batched one-launch bound (psd_batched_force_bound), waits before it
+ *     gives up; 0 makes every wait that is not already satisfied give up at
+ *     once, so the bound and a projection built on it report PSD_ERR_TIMEOUT
+ *     (every block of a batch; the kernel's CTAs leave at their next wait;
+ *     nothing hangs or faults).
  * PSD_ERR_INVALID_ARG for an unknown knob or a value out of range,
  * PSD_ERR_CUDA if the copy to the device failed.  Synchronous. */
 #define PSD_DEBUG_BOUND_SCALE 1

@@ -86,6 +86,7 @@ _SIGS = {
     "psd_project_deflate": ([_I64, _VP, _I64, _VP, _I64, _I32, _I32, _VP, _VP, _VP], _I32),
     "psd_batched_force_schedule": ([_I32], _I32),
     "psd_batched_force_form": ([_I32], _I32),
+    "psd_batched_force_bound": ([_I32], _I32),
     "psd_debug_set": ([_I32, ctypes.c_double], _I32),
     "psd_batched_last_tuning": ([ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)], _I32),
 }
@@ -165,6 +166,12 @@ def psd_batched_force_form(form):
     """Product form of batched plans built next: 1 chain (one persistent launch), 0 one launch
     per product, -1 default (chain where it applies)."""
     return int(lib().psd_batched_force_form(int(form)))
+
+
+def psd_batched_force_bound(form):
+    """Norm-bound form of batched plans built next: 1 one launch over a work-item list with
+    per-block counters, 0 or -1 (default) one grouped launch per phase."""
+    return int(lib().psd_batched_force_bound(int(form)))
 
 
 DEBUG_BOUND_SCALE = 1         # PSD_DEBUG_BOUND_SCALE

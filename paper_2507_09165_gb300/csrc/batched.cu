@@ -63,6 +63,12 @@ struct BatchPlan {
   int nprod = 0;
   int* d_done = nullptr;            // count x nprod tile counters, in `small`
   Mat x0{};                         // the cast's output (the chain's X_0)
+  // The norm bound as one launch over a work-item list (the default), or as
+  // grouped launches (psd_batched_force_bound(0)).
+  bool flow = false;
+  int4* d_flow = nullptr;           // in `small`
+  int nflow = 0;
+  unsigned* d_flowctl = nullptr;    // 2 + count words, in `small`
 };
 
 std::mutex g_bmu;
@@ -155,6 +161,7 @@ struct TuneReport {
 };
 int g_force_schedule = -1;                                  // for plans built next; -1: autotune
 int g_force_form = -1;  // for plans built next: -1 / 0 one launch per product, 1 chain form where it applies
+int g_force_bound = -1;  // for plans built next: -1 / 0 grouped launches, 1 the bound in one launch
 std::map<std::pair<int, std::vector<int>>, int> g_tuned;   // (precision, order buckets) -> schedule
 
 // Tuning key: the precision and the number of blocks per order bucket
@@ -170,6 +177,50 @@ std::pair<int, std::vector<int>> tune_key(const BatchPlan* p) {
   return std::make_pair(static_cast<int>(p->prec), hist);
 }
 TuneReport g_last_tune;
+
+// Work items of the one-launch bound in their global order (the order in which
+// CTAs claim them).  Per block: start vector; per Lanczos step j its mat-vec
+// tiles, reduction, mat-vec tiles and step; the Ritz vector; the residual's
+// tiles, reduction and tiles; the bound.  item.w counts the block's items in
+// earlier phases: the new item starts when the block's counter reaches it.
+// Within a phase the single-item kinds take the blocks largest first (the
+// longest items start first) and the mat-vecs smallest first, so that a large
+// block's tiles are claimed last, when its step (claimed first in the phase
+// before) is most likely done.
+constexpr int kFlowTiles = 4;
+std::vector<int4> build_flow(const std::vector<int>& sizes, const std::vector<BatchBlock>& bb,
+                             const std::vector<int>& big_first) {
+  const int count = static_cast<int>(sizes.size());
+  std::vector<int> big_last(big_first.rbegin(), big_first.rend());
+  std::vector<int4> flow;
+  std::vector<int> done(count, 0);
+  auto single = [&](int op) {
+    for (int b : big_first) flow.push_back(make_int4(op, b, 0, done[b]));
+    for (int b = 0; b < count; ++b) done[b] += 1;
+  };
+  // mat-vec items: up to kFlowTiles consecutive tiles of a block each
+  auto products = [&](int op) {
+    for (int b : big_last)
+      for (int t = 0; t < bb[b].ntiles; t += kFlowTiles) {
+        const int k = std::min(kFlowTiles, bb[b].ntiles - t);
+        flow.push_back(make_int4(op | (k << 20), b, static_cast<int>(bb[b].toff) + t, done[b]));
+      }
+    for (int b = 0; b < count; ++b) done[b] += (bb[b].ntiles + kFlowTiles - 1) / kFlowTiles;
+  };
+  single(FK_INIT);
+  for (int j = 0; j < kMaxSteps; ++j) {
+    products(FK_MV | (j << 8) | (j == 0 ? FF_STATS : FF_SKIP));
+    single(FK_RED | (j << 8) | (j == 0 ? FF_FRO : 0));
+    products(FK_MV | (j << 8) | FF_SKIP);
+    single(FK_STEP | (j << 8));
+  }
+  single(FK_RITZ);
+  products(FK_MV);
+  single(FK_RED | FF_RITZ);
+  products(FK_MV);
+  single(FK_BOUND);
+  return flow;
+}
 
 psd_status_t build_bplan(BatchPlan* p) {
   if (!get_schedule(p->prec, p->sched)) return PSD_ERR_INVALID_ARG;
@@ -260,7 +311,16 @@ psd_status_t build_bplan(BatchPlan* p) {
   const size_t o_prods = o_order + rup(sizeof(int) * count, 256);
   const size_t o_done = o_prods + rup(sizeof(ChainProduct) * kMaxProducts, 256);
   const size_t o_tpair = o_done + rup(sizeof(int) * kMaxProducts * count, 256);
-  const size_t smallb = o_tpair + rup(sizeof(int4) * std::max<size_t>(tiles_pair.size(), 1), 256);
+  // per-block kernels take the blocks largest first (the longest CTAs start first)
+  std::vector<int> order(count);
+  for (int b = 0; b < count; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p->sizes[x] > p->sizes[y]; });
+  p->flow = g_force_bound == 1;
+  const std::vector<int4> flow = p->flow ? build_flow(p->sizes, bb, order) : std::vector<int4>();
+  p->nflow = static_cast<int>(flow.size());
+  const size_t o_flow = o_tpair + rup(sizeof(int4) * std::max<size_t>(tiles_pair.size(), 1), 256);
+  const size_t o_flowctl = o_flow + rup(sizeof(int4) * std::max<size_t>(flow.size(), 1), 256);
+  const size_t smallb = o_flowctl + rup(sizeof(unsigned) * (2 + count), 256);
   if (cudaMalloc(&p->small, smallb) != cudaSuccess) {
     cudaGetLastError();
     p->small = nullptr;
@@ -281,10 +341,8 @@ psd_status_t build_bplan(BatchPlan* p) {
   p->d_prods = reinterpret_cast<ChainProduct*>(p->small + o_prods);
   p->d_done = reinterpret_cast<int*>(p->small + o_done);
   p->d_tiles_pair = reinterpret_cast<int4*>(p->small + o_tpair);
-  // per-block kernels take the blocks largest first (the longest CTAs start first)
-  std::vector<int> order(count);
-  for (int b = 0; b < count; ++b) order[b] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p->sizes[x] > p->sizes[y]; });
+  p->d_flow = reinterpret_cast<int4*>(p->small + o_flow);
+  p->d_flowctl = reinterpret_cast<unsigned*>(p->small + o_flowctl);
   for (int b = 0; b < count; ++b) rec[b].st = p->d_st + b;
   bool ok = cudaMemcpy(p->d_rec, rec.data(), sizeof(BlockRec) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(p->d_bb, bb.data(), sizeof(BatchBlock) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -294,7 +352,9 @@ psd_status_t build_bplan(BatchPlan* p) {
             cudaMemcpy(p->d_cast, cast.data(), sizeof(int4) * cast.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(p->d_tiles_pair, tiles_pair.data(), sizeof(int4) * tiles_pair.size(),
-                       cudaMemcpyHostToDevice) == cudaSuccess;
+                       cudaMemcpyHostToDevice) == cudaSuccess &&
+            (flow.empty() ||
+             cudaMemcpy(p->d_flow, flow.data(), sizeof(int4) * flow.size(), cudaMemcpyHostToDevice) == cudaSuccess);
   if (!ok) return PSD_ERR_CUDA;
   p->L.order = d_order;
   p->L.blk = p->d_bb;
@@ -453,13 +513,16 @@ struct BatchOps {
   }
   cudaError_t finish() {
     return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, p->d_cres, p->d_cidx, p->d_crange, p->pair ? 16 : 4,
+                                  p->flow ? p->d_flowctl + 1 : nullptr,
                                   s);
   }
 };
 
 cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
   cudaError_t e;
-  if ((e = enqueue_batch_norm_bound(p->L, p->count, p->d_symv, p->nsymv, s)) != cudaSuccess) return e;
+  e = p->flow ? enqueue_batch_norm_bound_flow(p->L, p->d_symv, p->nsymv, p->d_flow, p->nflow, p->d_flowctl, p->count, s)
+              : enqueue_batch_norm_bound(p->L, p->count, p->d_symv, p->nsymv, s);
+  if (e != cudaSuccess) return e;
   if (!p->chain) {
     BatchOps ops{p, s};
     return run_chain(p->prec, p->sched, p->nslots, dt16_for(p->prec), ops);
@@ -481,7 +544,8 @@ cudaError_t enqueue_batch(BatchPlan* p, cudaStream_t s) {
   if ((e = launch_symgemm_chain(dt16_for(p->prec), p->cmaps, p->d_prods, p->nprod, g, p->d_done, num_sms(), s)) !=
       cudaSuccess)
     return e;
-  return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, p->d_cres, p->d_cidx, p->d_crange, 8, s);
+  return enqueue_batch_finalize(p->d_bb, p->d_st, p->count, p->d_cres, p->d_cidx, p->d_crange, 8,
+                                p->flow ? p->d_flowctl + 1 : nullptr, s);
 }
 
 // Picks the plan's product schedule: the forced one, the one tuned earlier for
@@ -616,6 +680,13 @@ extern "C" int32_t psd_batched_force_form(int32_t form) {
   return prev;
 }
 
+extern "C" int32_t psd_batched_force_bound(int32_t form) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  const int prev = g_force_bound;
+  g_force_bound = (form == 0 || form == 1) ? form : -1;
+  return prev;
+}
+
 extern "C" psd_status_t psd_batched_last_tuning(int32_t* chosen, int32_t* candidates, float* ms) {
   std::lock_guard<std::mutex> lk(g_bmu);
   if (g_last_tune.chosen < 0) return PSD_ERR_INVALID_ARG;
@@ -659,7 +730,8 @@ extern "C" psd_status_t psd_project_batched(int32_t count, const psd_block_desc_
     sizes[b] = static_cast<int>(d.n);
   }
   std::lock_guard<std::mutex> lk(g_bmu);
-  auto key = std::make_tuple(dev, s, 4 * static_cast<int>(precision) + g_force_form + 1, sizes);
+  auto key = std::make_tuple(dev, s, 4 * static_cast<int>(precision) + g_force_form + 1 + 64 * (g_force_bound == 1),
+                             sizes);
   BatchPlan* p = nullptr;
   auto it = g_bplans.find(key);
   if (it != g_bplans.end()) {

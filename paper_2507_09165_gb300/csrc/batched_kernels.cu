@@ -15,9 +15,11 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
+#include "ptx.cuh"
 #include "tridiag.cuh"
 
 namespace psd {
@@ -28,6 +30,7 @@ constexpr uint64_t kSeed = 0x243F6A8885A308D3ull;  // Lanczos start vector seed
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr int kBT = 256;  // threads of a per-block CTA
 constexpr int kEPT = kMaxBatchOrder / kBT;  // elements per thread
+constexpr int kQChunk = 7;  // Lanczos vectors loaded at once in the Ritz vector's sum (21 = 3 x 7)
 
 struct F2 {
   float h, l;
@@ -68,8 +71,18 @@ __device__ __forceinline__ F2 df_from_d(double v) {
   const float h = __double2float_rn(v);
   return F2{h, __double2float_rn(v - static_cast<double>(h))};
 }
+// Loads of data written during the bound.  CG (the one-launch form, where
+// other CTAs write it while the kernel runs): through L2 (ld.global.cg).
+// Otherwise (grouped launches: written by earlier kernels) a plain load, which
+// may hit L1 when a thread reads the same element again.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+template <bool CG>
 __device__ __forceinline__ F2 ld_f2(const float2* p) {
-  const float2 t = *p;
+  const float2 t = ldv<CG>(p);
   return F2{t.x, t.y};
 }
 __device__ __forceinline__ void st_f2(float2* p, F2 a) { *p = make_float2(a.h, a.l); }
@@ -136,44 +149,78 @@ __device__ __forceinline__ BView view_of(const BatchLanczos& L, const BatchBlock
 __device__ __forceinline__ BView view(const BatchLanczos& L, int b) { return view_of(L, L.blk[b]); }
 
 // ------------------------------------------------------------ grouped mat-vec
-// One 128 x 128 upper tile of block `blk`: same arithmetic as the single-matrix
-// kernel (see normbound.cu), partial sums into the block's P1 / P2.
-template <bool STATS, bool DIAG>
-__device__ __forceinline__ void bsymv_tile(const float* __restrict__ T, int n, int bi, int bj,
-                                           const float* __restrict__ vh, float2* __restrict__ P1,
-                                           float2* __restrict__ P2, double* __restrict__ tile_fro,
-                                           int tile_slot, unsigned* maxdiag, float2 (*red)[kSymvTile],
-                                           double* fro_sh) {
-  const int i0 = bi * kSymvTile, j0 = bj * kSymvTile;
+// One 128 x 128 upper tile (bi, bj) of a block: same arithmetic as the
+// single-matrix kernel (see normbound.cu), partial sums into the block's
+// P1 / P2.  In four pieces so that a loop over tiles can have the next tile's
+// loads in flight while the previous one is reduced.
+
+// The thread's 64 elements of the packed tile: column c of the tile at
+// T + 128 c, zeros outside n x n (the zeros are not read: small blocks fill a
+// few rows of their tile); on a diagonal tile, an 8 x 8 piece wholly below the
+// diagonal (tr > tcol) is masked to zero below and not read either (18% of the
+// bytes of 512 blocks of orders 16-1024).
+// A 16-byte load of packed X with an L2 evict-first policy (the one-launch
+// form, STREAM): there the mat-vec tiles stream while other CTAs run Lanczos
+// steps, whose reads of the Lanczos vectors the tiles would otherwise push out
+// of L2 (measured: the steps' dot products 25-30% faster).  The grouped
+// launches keep the default policy: consecutive products read the tiles in
+// opposite orders and find part of them in L2.
+__device__ __forceinline__ float4 ld_stream4(const float* p) {
+  float4 r;
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+      "ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], pol;\n\t}"
+      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+      : "l"(p));
+  return r;
+}
+
+template <bool STREAM>
+__device__ __forceinline__ void btile_load_x(const float* __restrict__ T, int n, int bi, int bj,
+                                             float (&x)[8][8]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tr = lane & 15, tcol = 2 * warp + (lane >> 4);
-  const int ib = i0 + 8 * tr;
-  const int jb = j0 + 8 * tcol;
-  float vi[8], vj[8], x[8][8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    vi[k] = (ib + k < n) ? __ldg(vh + ib + k) : 0.f;
-    vj[k] = (jb + k < n) ? __ldg(vh + jb + k) : 0.f;
-  }
-  // the packed tile: column c of the tile at T + 128 c, zeros outside n x n
-  // (the zeros are not read: small blocks fill a few rows of their tile); on
-  // a diagonal tile, an 8 x 8 piece wholly below the diagonal (tr > tcol) is
-  // masked to zero below and not read either (18% of the bytes of 512 blocks
-  // of orders 16-1024)
-  const bool piece = !DIAG || tr <= tcol;
+  const int ib = bi * kSymvTile + 8 * tr;
+  const int jb = bj * kSymvTile + 8 * tcol;
+  const bool piece = bi != bj || tr <= tcol;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float* col = T + (8 * tcol + c) * kSymvTile + 8 * tr;
     const bool live = jb + c < n && ib < n && piece;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 a4 = live ? __ldg(reinterpret_cast<const float4*>(col)) : z;
-    const float4 b4 = live && ib + 4 < n ? __ldg(reinterpret_cast<const float4*>(col + 4)) : z;
+    const float4 a4 = !live ? z : STREAM ? ld_stream4(col) : __ldg(reinterpret_cast<const float4*>(col));
+    const float4 b4 = !(live && ib + 4 < n) ? z
+                      : STREAM              ? ld_stream4(col + 4)
+                                            : __ldg(reinterpret_cast<const float4*>(col + 4));
     x[c][0] = a4.x; x[c][1] = a4.y; x[c][2] = a4.z; x[c][3] = a4.w;
     x[c][4] = b4.x; x[c][5] = b4.y; x[c][6] = b4.z; x[c][7] = b4.w;
   }
-  float rsum[8], csum[8];
-  float fro = 0.f;
-  unsigned mdiag = 0;
+}
+
+// The thread's slices of the mat-vec input (rows and columns).
+template <bool CG>
+__device__ __forceinline__ void btile_load_v(const float* vh, int n, int bi, int bj, float (&vi)[8],
+                                             float (&vj)[8]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ib = bi * kSymvTile + 8 * (lane & 15);
+  const int jb = bj * kSymvTile + 8 * (2 * warp + (lane >> 4));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    vi[k] = (ib + k < n) ? (CG ? __ldcg(vh + ib + k) : __ldg(vh + ib + k)) : 0.f;
+    vj[k] = (jb + k < n) ? (CG ? __ldcg(vh + jb + k) : __ldg(vh + jb + k)) : 0.f;
+  }
+}
+
+// Per-thread row and column dot products of the 8 x 8 piece (8-term FP32 FMA runs).
+template <bool STATS, bool DIAG>
+__device__ __forceinline__ void btile_fma(int n, int bi, int bj, const float (&vi)[8], const float (&vj)[8],
+                                          const float (&x)[8][8], float (&rsum)[8], float (&csum)[8], float& fro,
+                                          unsigned& mdiag) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ib = bi * kSymvTile + 8 * (lane & 15);
+  const int jb = bj * kSymvTile + 8 * (2 * warp + (lane >> 4));
+  fro = 0.f;
+  mdiag = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) rsum[k] = 0.f;
 #pragma unroll
@@ -193,6 +240,21 @@ __device__ __forceinline__ void bsymv_tile(const float* __restrict__ T, int n, i
       if (STATS) fro = fmaf(xr, xc + xr, fro);
     }
   }
+}
+
+// Combines the threads' sums in a fixed order (double-float) into the tile's
+// row partials P1[bj][rows] and column partials P2[bi][columns]; STATS: the
+// tile's share of ||X||_F^2 and max |X_ii|.  `red` is read after its barrier:
+// a loop over tiles needs another barrier before the next tile writes it.
+template <bool STATS>
+__device__ __forceinline__ void btile_reduce(int n, int bi, int bj, const float (&rsum)[8], const float (&csum)[8],
+                                             float fro, unsigned mdiag, float2* __restrict__ P1,
+                                             float2* __restrict__ P2, double* __restrict__ tile_fro, int tile_slot,
+                                             unsigned* maxdiag, float2 (*red)[kSymvTile], double* fro_sh) {
+  const int i0 = bi * kSymvTile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tr = lane & 15;
+  const int jb = bj * kSymvTile + 8 * (2 * warp + (lane >> 4));
   F2 cs[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -243,6 +305,21 @@ __device__ __forceinline__ void bsymv_tile(const float* __restrict__ T, int n, i
   }
 }
 
+template <bool STATS, bool DIAG>
+__device__ __forceinline__ void bsymv_tile(const float* __restrict__ T, int n, int bi, int bj,
+                                           const float* __restrict__ vh, float2* __restrict__ P1,
+                                           float2* __restrict__ P2, double* __restrict__ tile_fro,
+                                           int tile_slot, unsigned* maxdiag, float2 (*red)[kSymvTile],
+                                           double* fro_sh) {
+  float vi[8], vj[8], x[8][8];
+  btile_load_v<false>(vh, n, bi, bj, vi, vj);
+  btile_load_x<false>(T, n, bi, bj, x);
+  float rsum[8], csum[8], fro;
+  unsigned mdiag;
+  btile_fma<STATS, DIAG>(n, bi, bj, vi, vj, x, rsum, csum, fro, mdiag);
+  btile_reduce<STATS>(n, bi, bj, rsum, csum, fro, mdiag, P1, P2, tile_fro, tile_slot, maxdiag, red, fro_sh);
+}
+
 // Copies the 128 x 128 upper tiles of every block out of the caller's
 // matrices into L.xt, one contiguous 64 KB tile per mat-vec work item (column
 // c of the tile at 128 c; zeros outside the block and below the diagonal of a
@@ -272,10 +349,8 @@ __global__ void __launch_bounds__(256) bpack_kernel(BatchLanczos L, const int4* 
 // exceed L2).  The item -> partial slot mapping does not change: results are
 // identical.
 template <bool STATS>
-__global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int4* __restrict__ items, int reverse) {
-  __shared__ float2 red[8][kSymvTile];
-  __shared__ double fro_sh[8];
-  const int idx = reverse ? static_cast<int>(gridDim.x) - 1 - static_cast<int>(blockIdx.x) : static_cast<int>(blockIdx.x);
+__device__ __forceinline__ void ph_bsymv(const BatchLanczos& L, const int4* __restrict__ items, int idx, bool skip,
+                                         float2 (*red)[kSymvTile], double* fro_sh) {
   const int4 it = items[idx];
   const int b = it.x;
   // the block record and the done flag are independent loads: issue both
@@ -284,7 +359,7 @@ __global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int
   const int done = L.st[b].done;
   const BView v = view_of(L, bb);
   const float* T = L.xt + static_cast<int64_t>(idx) * kSymvTile * kSymvTile;
-  if (done && !STATS && L.skip_done) return;
+  if (done && !STATS && skip) return;
   if (it.y == it.z)
     bsymv_tile<STATS, true>(T, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
                             &L.st[b].maxdiag_bits, red, fro_sh);
@@ -293,18 +368,27 @@ __global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int
                              &L.st[b].maxdiag_bits, red, fro_sh);
 }
 
+template <bool STATS>
+__global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int4* __restrict__ items, int reverse) {
+  __shared__ float2 red[8][kSymvTile];
+  __shared__ double fro_sh[8];
+  const int idx = reverse ? static_cast<int>(gridDim.x) - 1 - static_cast<int>(blockIdx.x) : static_cast<int>(blockIdx.x);
+  ph_bsymv<STATS>(L, items, idx, L.skip_done != 0, red, fro_sh);
+}
+
 // y_e of block b from its partial sums (fixed order, double-float, normalised), e < n:
 // P1 of the tiles bj = b(e) .. nb - 1, then P2 of bi = 0 .. b(e).  All (at most
 // 2 kMaxBatchOrder / 128) loads are issued before the additions.
 constexpr int kMaxTileBlocks = kMaxBatchOrder / kSymvTile;
+template <bool CG>
 __device__ __forceinline__ F2 bred(const BView& v, int e) {
   const int bk = e / kSymvTile;
   float2 p1[kMaxTileBlocks], p2[kMaxTileBlocks];
 #pragma unroll
   for (int i = 0; i < kMaxTileBlocks; ++i) {
     const int bj = bk + i, bi = i;
-    p1[i] = bj < v.nb ? v.P1[static_cast<int64_t>(bj) * v.n + e] : make_float2(0.f, 0.f);
-    p2[i] = bi <= bk ? v.P2[static_cast<int64_t>(bi) * v.n + e] : make_float2(0.f, 0.f);
+    p1[i] = bj < v.nb ? ldv<CG>(v.P1 + static_cast<int64_t>(bj) * v.n + e) : make_float2(0.f, 0.f);
+    p2[i] = bi <= bk ? ldv<CG>(v.P2 + static_cast<int64_t>(bi) * v.n + e) : make_float2(0.f, 0.f);
   }
   F2 a{0.f, 0.f};
 #pragma unroll
@@ -316,12 +400,24 @@ __device__ __forceinline__ F2 bred(const BView& v, int e) {
   return fast_two_sum(a.h, a.l);
 }
 
+// Lanczos vectors c0 .. c0 + kQChunk - 1 (those below `cnt`) at the thread's
+// elements: every load issued before any is used (zeros elsewhere).
+template <bool CG>
+__device__ __forceinline__ void load_q_chunk(const BView& v, int c0, int cnt, F2 (&qk)[kEPT][kQChunk]) {
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) {
+    const int e = threadIdx.x + k * kBT;
+#pragma unroll
+    for (int i = 0; i < kQChunk; ++i)
+      qk[k][i] = (e < v.n && c0 + i < cnt) ? ld_f2<CG>(v.Q + static_cast<int64_t>(c0 + i) * v.n + e) : F2{0.f, 0.f};
+  }
+}
+
 // ------------------------------------------------------------ per-block CTAs
 // Start vector (SplitMix64, normalised), state reset, split for the first product.
-__global__ void __launch_bounds__(kBT) binit_kernel(BatchLanczos L) {
+__device__ __forceinline__ void ph_binit(const BatchLanczos& L, int b) {
   __shared__ F2 sh[kBT / 32];
   __shared__ double inv_sh;
-  const int b = L.order[blockIdx.x];
   const BView v = view(L, b);
   F2 loc[kEPT];
   F2 s{0.f, 0.f};
@@ -362,23 +458,24 @@ __global__ void __launch_bounds__(kBT) binit_kernel(BatchLanczos L) {
 }
 
 // ||X_b||_F from the block's tile sums (after the first product).
-__global__ void bfro_kernel(BatchLanczos L) {
-  const int b = L.order[blockIdx.x];
+// (lanes 0-31 of the CTA)
+template <bool CG>
+__device__ __forceinline__ void ph_bfro(const BatchLanczos& L, int b) {
   const BatchBlock& bb = L.blk[b];
   double f = 0.0;
-  for (int t = threadIdx.x; t < bb.ntiles; t += 32) f += L.tile_fro[bb.toff + t];
+  for (int t = threadIdx.x; t < bb.ntiles; t += 32) f += ldv<CG>(L.tile_fro + bb.toff + t);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
   if (threadIdx.x == 0) L.st[b].fro = sqrt(f);
 }
 
 // u = X v: reduce, store, split for the second product.  MODE 1: Ritz pass (no done check).
-__global__ void __launch_bounds__(kBT) breduce_kernel(BatchLanczos L, int mode) {
-  const int b = L.order[blockIdx.x];
-  if (mode == 0 && L.st[b].done) return;
+template <bool CG>
+__device__ __forceinline__ void ph_breduce(const BatchLanczos& L, int b, int mode) {
+  if (mode == 0 && ldv<CG>(&L.st[b].done)) return;
   const BView v = view(L, b);
   for (int e = threadIdx.x; e < v.n; e += kBT) {
-    const F2 y = bred(v, e);
+    const F2 y = bred<CG>(v, e);
     v.u[e] = f2_to_d(y);
     v.vh[e] = y.h;
     v.vl[e] = y.l;
@@ -434,21 +531,21 @@ __device__ __forceinline__ void cta_multi_sum(const F2 (&v)[kMaxSteps + 1], int 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
+template <bool CG>
+__device__ __forceinline__ void ph_bstep(const BatchLanczos& L, int b, int j) {
   __shared__ F2 sh[kBT / 32][32];
   __shared__ F2 h[32];
   __shared__ F2 shs[kBT / 32];
   __shared__ double beta_sh[2];
-  const int b = L.order[blockIdx.x];
   DevState* st = &L.st[b];
-  if (st->done) return;
+  if (ldv<CG>(&st->done)) return;
   const BView v = view(L, b);
   const bool any = (threadIdx.x & ~31) < v.n;  // the warp owns an element
   F2 w[kEPT];
 #pragma unroll
   for (int k = 0; k < kEPT; ++k) {
     const int e = threadIdx.x + k * kBT;
-    w[k] = e < v.n ? bred(v, e) : F2{0.f, 0.f};
+    w[k] = e < v.n ? bred<CG>(v, e) : F2{0.f, 0.f};
   }
   for (int pass = 0; pass < 2; ++pass) {
     F2 d[kMaxSteps + 1];
@@ -460,7 +557,7 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
       if (e < v.n) {
 #pragma unroll
         for (int kk = 0; kk <= kMaxSteps; ++kk)
-          if (kk <= j) d[kk] = df_add(d[kk], df_mul(ld_f2(v.Q + static_cast<int64_t>(kk) * v.n + e), w[k]));
+          if (kk <= j) d[kk] = df_add(d[kk], df_mul(ld_f2<CG>(v.Q + static_cast<int64_t>(kk) * v.n + e), w[k]));
       }
     }
     cta_multi_sum(d, j, any, sh, h);
@@ -470,7 +567,7 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
       const int e = threadIdx.x + k * kBT;
       if (e < v.n)
         for (int kk = 0; kk <= j; ++kk)
-          w[k] = df_add(w[k], df_neg(df_mul(h[kk], ld_f2(v.Q + static_cast<int64_t>(kk) * v.n + e))));
+          w[k] = df_add(w[k], df_neg(df_mul(h[kk], ld_f2<CG>(v.Q + static_cast<int64_t>(kk) * v.n + e))));
     }
     __syncthreads();  // h is rewritten by the next pass
   }
@@ -487,7 +584,7 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
   }
   __syncthreads();
   const double beta = beta_sh[0];
-  const double fro = st->fro;
+  const double fro = ldv<CG>(&st->fro);
   const bool brk = !(beta > kBreakdown * fro * fro);
   if (brk || j == kMaxSteps - 1) {
     if (threadIdx.x == 0) {
@@ -517,17 +614,23 @@ __global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
 // Largest Ritz pair of each block's tridiagonal (one warp per block):
 // multisection on the Sturm count, inverse iteration with partial pivoting,
 // then q = Q_m y, normalised, split.
-__global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
+template <bool CG>
+__device__ __forceinline__ void ph_britz(const BatchLanczos& L, int b) {
   __shared__ double y[kMaxSteps];
   __shared__ float a32[kMaxSteps], b32[kMaxSteps];
   __shared__ F2 sh[kBT / 32];
   __shared__ F2 yf[kMaxSteps];
   __shared__ double inv_sh;
-  const int b = L.order[blockIdx.x];
+  __shared__ double ab[2][kMaxSteps];
   DevState* st = &L.st[b];
-  const int m = st->m;
+  const int m = ldv<CG>(&st->m);
   if (threadIdx.x < 32) {
-    const double sigma = tridiag_top_eig(st->alpha, st->beta, m, y, a32, b32);
+    if (threadIdx.x < kMaxSteps) {
+      ab[0][threadIdx.x] = ldv<CG>(st->alpha + threadIdx.x);
+      ab[1][threadIdx.x] = ldv<CG>(st->beta + threadIdx.x);
+    }
+    __syncwarp();
+    const double sigma = tridiag_top_eig(ab[0], ab[1], m, y, a32, b32);
     if (threadIdx.x == 0) {
       st->sigma = sigma;
       for (int k = 0; k < kMaxSteps; ++k) st->y[k] = y[k];
@@ -537,16 +640,27 @@ __global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
   __syncthreads();
   const BView v = view(L, b);
   F2 qv[kEPT];
+#pragma unroll
+  for (int k = 0; k < kEPT; ++k) qv[k] = F2{0.f, 0.f};
+  // qv = sum_k y_k q_k in order k = 0 .. m - 1
+#pragma unroll
+  for (int c0 = 0; c0 < kMaxSteps; c0 += kQChunk) {
+    if (c0 < m) {
+      F2 qk[kEPT][kQChunk];
+      load_q_chunk<CG>(v, c0, m, qk);
+#pragma unroll
+      for (int k = 0; k < kEPT; ++k) {
+        if (threadIdx.x + k * kBT < v.n) {
+#pragma unroll
+          for (int i = 0; i < kQChunk; ++i)
+            if (c0 + i < m) qv[k] = df_add(qv[k], df_mul(yf[c0 + i], qk[k][i]));
+        }
+      }
+    }
+  }
   F2 s{0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < kEPT; ++k) {
-    const int e = threadIdx.x + k * kBT;
-    F2 t{0.f, 0.f};
-    if (e < v.n)
-      for (int kk = 0; kk < m; ++kk) t = df_add(t, df_mul(yf[kk], ld_f2(v.Q + static_cast<int64_t>(kk) * v.n + e)));
-    qv[k] = t;
-    s = df_add(s, df_mul(t, t));
-  }
+  for (int k = 0; k < kEPT; ++k) s = df_add(s, df_mul(qv[k], qv[k]));
   const F2 nrm2 = cta_sum_df(s, sh);
   if (threadIdx.x == 0) {
     const double n2 = f2_to_d(nrm2);
@@ -567,22 +681,22 @@ __global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) {
 }
 
 // r = ||X (X q) - sigma q||, lam~ = max(sqrt(sigma + r), ||X||_F / sqrt n, max |X_ii|), report.
-__global__ void __launch_bounds__(kBT) bbound_kernel(BatchLanczos L) {
+template <bool CG>
+__device__ __forceinline__ void ph_bbound(const BatchLanczos& L, int b) {
   __shared__ double sh[kBT / 32];
-  const int b = L.order[blockIdx.x];
   DevState* st = &L.st[b];
   const BView v = view(L, b);
+  const double sigma = ldv<CG>(&st->sigma);
   double s = 0.0;
   for (int e = threadIdx.x; e < v.n; e += kBT) {
-    const double r = f2_to_d(bred(v, e)) - st->sigma * v.q[e];
+    const double r = f2_to_d(bred<CG>(v, e)) - sigma * ldv<CG>(v.q + e);
     s += r * r;
   }
   const double r2 = cta_sum(s, sh);
   if (threadIdx.x != 0) return;
   const double r = sqrt(r2);
-  const double fro = st->fro;
-  const double md = static_cast<double>(__uint_as_float(st->maxdiag_bits));
-  const double sigma = st->sigma;
+  const double fro = ldv<CG>(&st->fro);
+  const double md = static_cast<double>(__uint_as_float(ldv<CG>(&st->maxdiag_bits)));
   double lam = sqrt(fmax(sigma + r, 0.0));
   lam = fmax(lam, fro / sqrt(static_cast<double>(v.n)));
   lam = fmax(lam, md);
@@ -601,9 +715,175 @@ __global__ void __launch_bounds__(kBT) bbound_kernel(BatchLanczos L) {
     info->lanczos_resid = r;
     info->fro_X = fro;
     info->max_diag = md;
-    info->lanczos_steps = st->m;
-    info->status = st->status;
+    info->lanczos_steps = ldv<CG>(&st->m);
+    info->status = ldv<CG>(&st->status);
     info->compl_resid = __longlong_as_double(0x7ff8000000000000ll);  // set by the last step
+  }
+}
+
+// One CTA per block (block order[blockIdx.x]) for the grouped launches.
+__global__ void __launch_bounds__(kBT) binit_kernel(BatchLanczos L) { ph_binit(L, L.order[blockIdx.x]); }
+__global__ void bfro_kernel(BatchLanczos L) { ph_bfro<false>(L, L.order[blockIdx.x]); }
+__global__ void __launch_bounds__(kBT) breduce_kernel(BatchLanczos L, int mode) {
+  ph_breduce<false>(L, L.order[blockIdx.x], mode);
+}
+__global__ void __launch_bounds__(kBT) bstep_kernel(BatchLanczos L, int j) {
+  ph_bstep<false>(L, L.order[blockIdx.x], j);
+}
+__global__ void __launch_bounds__(kBT) britz_kernel(BatchLanczos L) { ph_britz<false>(L, L.order[blockIdx.x]); }
+__global__ void __launch_bounds__(kBT) bbound_kernel(BatchLanczos L) { ph_bbound<false>(L, L.order[blockIdx.x]); }
+
+// ------------------------------------------------------------ one-launch form
+// The whole batched bound as ONE launch of resident CTAs that take work items
+// from a list in a fixed global order (host-built, see build_flow): a block's
+// items are its start vector, then per Lanczos step its mat-vec tiles (up to 4
+// per item, pipelined), its reduction, its mat-vec tiles again and its step,
+// then the Ritz vector and the residual's two products and reduction, and its
+// bound.  Each CTA claims the next item with one atomic add (the claim of item
+// k + 1 is issued while item k waits for its inputs), waits until the block's
+// counter shows every item the new one depends on done (item.w = the number of
+// the block's earlier items; a mat-vec item loads its first tile's X before it
+// waits), runs it with the same per-tile and per-block device code as the
+// grouped launches, and adds 1 to the counter.  No grid-wide barrier: a block's next phase starts as soon
+// as its own previous phase is done, so the Lanczos steps of the large blocks
+// overlap the mat-vec tiles of the others.
+//
+// Progress: items are claimed in list order and an item waits only for items
+// of lower index.  The unfinished item of lowest index is therefore claimed by
+// a running CTA whose earlier items are all finished, and its inputs are
+// ready: it completes, whatever the residency of the other CTAs.  Every wait
+// is bounded: after g_flow_limit_ns the CTA raises the abort word, every CTA
+// that sees it leaves, and the batch reports PSD_ERR_TIMEOUT.
+//
+// Results are bit-identical to the grouped launches: each item runs the same
+// arithmetic on the same inputs, and every reduction order is fixed per block.
+__device__ unsigned long long g_flow_limit_ns = kWaitLimitNs;
+
+
+__device__ __forceinline__ unsigned ld_acquire_flow(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0: wait until *cnt >= need, or give up (abort word ctl[1]).  The
+// acquire load orders thread 0 after the producers' counts; the CTA barrier
+// that follows orders the other threads after it, and every read of data
+// another item wrote goes through L2 (ld.global.cg), where the producers'
+// stores were performed before their counts.
+__device__ __forceinline__ bool flow_wait(const unsigned* cnt, unsigned need, unsigned* ctl) {
+  if (ld_acquire_flow(cnt) >= need) return true;
+  const unsigned long long limit = g_flow_limit_ns;
+  const unsigned long long t0 = globaltimer_ns();
+  while (ld_acquire_flow(cnt) < need) {
+    if (ld_acquire_flow(ctl + 1) != 0u) return false;
+    if (globaltimer_ns() - t0 >= limit) {  // >=: a zero limit gives up on the first poll
+      atomicExch(ctl + 1, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Tile t of a block's upper tiles in their list order (column-major over the
+// upper triangle: t = bj (bj + 1) / 2 + bi).
+__device__ __forceinline__ void btile_of(int t, int& bi, int& bj) {
+  int j = static_cast<int>((sqrtf(8.f * static_cast<float>(t) + 1.f) - 1.f) * 0.5f);
+  while ((j + 1) * (j + 2) / 2 <= t) ++j;
+  while (j * (j + 1) / 2 > t) --j;
+  bj = j;
+  bi = t - j * (j + 1) / 2;
+}
+
+// Mat-vec item: tiles first .. first + cnt - 1 of block b (consecutive entries
+// of the tile list), the packed X of the first already in x; each next tile's
+// X and input slices are loaded while the previous tile is reduced.  Per
+// tile the same arithmetic as bsymv_tile.
+template <bool STATS>
+__device__ __forceinline__ void ph_bsymv_run(const BatchLanczos& L, int b, int first, int cnt, float (&x)[8][8],
+                                             float2 (*red)[kSymvTile], double* fro_sh) {
+  const BatchBlock bb = L.blk[b];
+  const BView v = view_of(L, bb);
+  int bi, bj;
+  btile_of(first - static_cast<int>(bb.toff), bi, bj);
+  float vi[8], vj[8];
+  btile_load_v<true>(v.vh, v.n, bi, bj, vi, vj);
+  for (int k = 0; k < cnt; ++k) {
+    float rsum[8], csum[8], fro;
+    unsigned mdiag;
+    if (bi == bj)
+      btile_fma<STATS, true>(v.n, bi, bj, vi, vj, x, rsum, csum, fro, mdiag);
+    else
+      btile_fma<STATS, false>(v.n, bi, bj, vi, vj, x, rsum, csum, fro, mdiag);
+    const int ci = bi, cj = bj;
+    if (k + 1 < cnt) {  // in flight during the reduction
+      btile_of(first + k + 1 - static_cast<int>(bb.toff), bi, bj);
+      btile_load_x<true>(L.xt + static_cast<int64_t>(first + k + 1) * kSymvTile * kSymvTile, v.n, bi, bj, x);
+      btile_load_v<true>(v.vh, v.n, bi, bj, vi, vj);
+    }
+    btile_reduce<STATS>(v.n, ci, cj, rsum, csum, fro, mdiag, v.P1, v.P2, L.tile_fro, first + k,
+                        &L.st[b].maxdiag_bits, red, fro_sh);
+    if (k + 1 < cnt) __syncthreads();  // red is written again by the next tile
+  }
+}
+
+__global__ void __launch_bounds__(kBT, 2) bflow_kernel(BatchLanczos L, const int4* __restrict__ flow, int nflow,
+                                                      unsigned* ctl, unsigned* cnt) {
+  __shared__ float2 red[8][kSymvTile];
+  __shared__ double fro_sh[8];
+  __shared__ int claim_sh[2];
+  __shared__ int ok_sh;
+  if (threadIdx.x == 0) claim_sh[0] = static_cast<int>(atomicAdd(ctl, 1u));
+  __syncthreads();
+  int slot = 0;
+  int cur = claim_sh[0];
+  int4 fn = cur < nflow ? __ldg(flow + cur) : make_int4(0, 0, 0, 0);
+  while (cur < nflow) {
+    const int4 f = fn;
+    const int kind = f.x & 0xff, j = (f.x >> 8) & 0xff, b = f.y;
+    float x[8][8];
+    if (kind == FK_MV) {  // X does not change during the bound: load before the wait
+      const BatchBlock& bb = L.blk[b];
+      int bi, bj;
+      btile_of(f.z - static_cast<int>(bb.toff), bi, bj);
+      btile_load_x<true>(L.xt + static_cast<int64_t>(f.z) * kSymvTile * kSymvTile, bb.n, bi, bj, x);
+    }
+    if (threadIdx.x == 0) {
+      const unsigned next = atomicAdd(ctl, 1u);  // in flight during the wait
+      ok_sh = flow_wait(cnt + b, static_cast<unsigned>(f.w), ctl);
+      claim_sh[slot ^ 1] = static_cast<int>(next);
+    }
+    __syncthreads();
+    if (!ok_sh) return;
+    // the next item's record, in flight during this one
+    const int nxt = claim_sh[slot ^ 1];
+    fn = nxt < nflow ? __ldg(flow + nxt) : make_int4(0, 0, 0, 0);
+    switch (kind) {
+      case FK_INIT: ph_binit(L, b); break;
+      case FK_MV: {
+        const int ntile = (f.x >> 20) & 0xf;
+        if (f.x & FF_STATS)
+          ph_bsymv_run<true>(L, b, f.z, ntile, x, red, fro_sh);
+        else if (!((f.x & FF_SKIP) && __ldcg(&L.st[b].done)))
+          ph_bsymv_run<false>(L, b, f.z, ntile, x, red, fro_sh);
+        break;
+      }
+      case FK_RED:
+        if ((f.x & FF_FRO) && threadIdx.x < 32) ph_bfro<true>(L, b);
+        ph_breduce<true>(L, b, (f.x & FF_RITZ) ? 1 : 0);
+        break;
+      case FK_STEP: ph_bstep<true>(L, b, j); break;
+      case FK_RITZ: ph_britz<true>(L, b); break;
+      default: ph_bbound<true>(L, b); break;
+    }
+    __syncthreads();  // every thread's stores of the item precede the count
+    // the count goes out from another warp: thread 0 goes on to the next claim
+    if (threadIdx.x == 32) {
+      __threadfence();
+      atomicAdd(cnt + b, 1u);
+    }
+    slot ^= 1;
+    cur = claim_sh[slot];
   }
 }
 
@@ -708,13 +988,19 @@ __global__ void __launch_bounds__(256) bcast_kernel(BatchCast c, const BatchBloc
 // shares of the block's final-product tiles, added in the block's own tile
 // order (cidx: positions of its tiles in the launch's tile list, range crange[b])
 // so that the sum does not depend on the schedule or the rest of the batch.
+// A one-launch bound that gave up (abort word set) marks every block: a block
+// whose items were not all run may still hold an earlier call's state.
 __global__ void bfinalize_kernel(const BatchBlock* __restrict__ blk, DevState* st, int count,
                                  const double* __restrict__ cres, const int* __restrict__ cidx,
-                                 const int2* __restrict__ crange, int shares) {
+                                 const int2* __restrict__ crange, int shares, const unsigned* flow_abort) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count) return;
   const float amax = __uint_as_float(st[b].absmax_bits);
   int status = st[b].status;
+  if (status == 0 && flow_abort && *flow_abort) {
+    status = PSD_ERR_TIMEOUT;
+    st[b].status = status;
+  }
   if (status == 0) {
     if (!(amax == amax) || isinf(amax))
       status = PSD_ERR_NONFINITE;
@@ -766,6 +1052,29 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
   return cudaGetLastError();
 }
 
+cudaError_t enqueue_batch_norm_bound_flow(const BatchLanczos& L, const int4* symv_items, int nsymv, const int4* flow,
+                                          int nflow, unsigned* ctl, int count, cudaStream_t s) {
+  static int occ = 0;  // resident CTAs per SM (same on every device of a process: one GPU type)
+  if (occ == 0) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bflow_kernel, kBT, 0) != cudaSuccess || o < 1)
+      return cudaErrorInvalidConfiguration;
+    occ = o;
+  }
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (2 + count), s);
+  if (e != cudaSuccess) return e;
+  BatchLanczos Lk = L;
+  Lk.skip_done = 0;
+  bpack_kernel<<<nsymv, 256, 0, s>>>(Lk, symv_items);
+  const int grid = std::max(1, std::min(occ * num_sms(), nflow));
+  bflow_kernel<<<grid, kBT, 0, s>>>(Lk, flow, nflow, ctl, ctl + 2);
+  return cudaGetLastError();
+}
+
+cudaError_t set_batch_flow_limit(unsigned long long ns) {
+  return cudaMemcpyToSymbol(g_flow_limit_ns, &ns, sizeof(ns));
+}
+
 cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* blk, const DevState* st,
                                const int4* items, int nitems, cudaStream_t s) {
   switch (dtype) {
@@ -778,8 +1087,9 @@ cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* 
 }
 
 cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, const double* cres,
-                                   const int* cidx, const int2* crange, int shares, cudaStream_t s) {
-  bfinalize_kernel<<<(count + 127) / 128, 128, 0, s>>>(blk, st, count, cres, cidx, crange, shares);
+                                   const int* cidx, const int2* crange, int shares, const unsigned* flow_abort,
+                                   cudaStream_t s) {
+  bfinalize_kernel<<<(count + 127) / 128, 128, 0, s>>>(blk, st, count, cres, cidx, crange, shares, flow_abort);
   return cudaGetLastError();
 }
 

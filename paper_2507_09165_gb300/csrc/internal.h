@@ -334,9 +334,26 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
                                      cudaStream_t stream);
 cudaError_t enqueue_batch_cast(int dtype, const BatchCast& c, const BatchBlock* blk, const DevState* st,
                                const int4* items, int nitems, cudaStream_t stream);
-// shares: final-product shares per tile position in cres (4, or 8 from the chain form).
+// Work items of the one-launch bound: x = kind | j << 8 | flags.
+enum FlowKind : int { FK_INIT = 0, FK_MV = 1, FK_RED = 2, FK_STEP = 3, FK_RITZ = 4, FK_BOUND = 5 };
+// FF_STATS: first product (||X||_F, max |X_ii|); FF_SKIP: no work once the
+// block broke down; FF_FRO: ||X||_F before the first reduction; FF_RITZ:
+// reduction of the residual pass (no done check).
+constexpr int FF_STATS = 1 << 16, FF_SKIP = 1 << 17, FF_FRO = 1 << 18, FF_RITZ = 1 << 19;
+// The same bound as ONE launch over a list of work items with per-block
+// counters (bit-identical): flow = nflow items {kind | j << 8 | flags | tiles
+// << 20, block, first symv item (mat-vec items: `tiles` consecutive ones), the
+// block's items that must be done first}; ctl = 2 + count words
+// (claim counter, abort word, per-block counters), zeroed here.
+cudaError_t enqueue_batch_norm_bound_flow(const BatchLanczos& L, const int4* symv_items, int nsymv, const int4* flow,
+                                          int nflow, unsigned* ctl, int count, cudaStream_t stream);
+// Wait limit of the one-launch bound's dependency waits (psd_debug_set knob 2).
+cudaError_t set_batch_flow_limit(unsigned long long ns);
+// shares: final-product shares per tile position in cres (4, or 8 from the chain form);
+// flow_abort: the one-launch bound's abort word (or null).
 cudaError_t enqueue_batch_finalize(const BatchBlock* blk, DevState* st, int count, const double* cres,
-                                   const int* cidx, const int2* crange, int shares, cudaStream_t stream);
+                                   const int* cidx, const int2* crange, int shares, const unsigned* flow_abort,
+                                   cudaStream_t stream);
 bool encode_tmap_rows(CUtensorMap* map, int dtype, const void* base, int64_t cols, int64_t rows, int64_t ld,
                       int box_rows, int row_bytes = kRowBytes16);
 

@@ -631,7 +631,11 @@ psd_status_t psd_debug_set(int32_t knob, double value) {
   }
   psd_status_t st = check_device();
   if (st != PSD_OK) return st;
-  return set_norm_bound_debug(knob, value) == cudaSuccess ? PSD_OK : PSD_ERR_CUDA;
+  if (set_norm_bound_debug(knob, value) != cudaSuccess) return PSD_ERR_CUDA;
+  if (knob == PSD_DEBUG_BARRIER_LIMIT_NS &&
+      set_batch_flow_limit(static_cast<unsigned long long>(value)) != cudaSuccess)
+    return PSD_ERR_CUDA;
+  return PSD_OK;
 }
 
 const char* psd_status_string(psd_status_t status) {

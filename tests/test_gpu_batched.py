@@ -221,3 +221,30 @@ def test_product_shapes_and_forms_give_the_same_bits(mats, prec, workload):
             assert i1[k]["lambda_bound"] == i0[k]["lambda_bound"]
             assert i1[k]["overshoot_max"] == i0[k]["overshoot_max"]
             assert abs(i1[k]["compl_resid"] - i0[k]["compl_resid"]) <= 1e-12 + 1e-9 * abs(i0[k]["compl_resid"])
+
+
+@pytest.mark.parametrize("workload", ["orders", "512 blocks"])
+def test_norm_bound_forms_give_the_same_bits(mats, workload):
+    # The batched norm bound runs as ONE launch whose CTAs claim work items
+    # (start vectors, mat-vec tiles, reductions, Lanczos steps, Ritz vectors,
+    # bounds) and wait only on their own block's earlier items, or as one
+    # grouped launch per phase.  Each item runs the same arithmetic in the same
+    # order, so outputs and whole reports must agree bit for bit; the orders
+    # include blocks below 20 (Lanczos breakdown: their later items do no work).
+    if workload == "orders":
+        ms = [m for m, _ in mats]
+    else:
+        ms = [synth.wigner(n, 7000 + i) for i, n in enumerate(synth.block_sizes(512, 7))]
+    res = []
+    try:
+        for form in (0, 1):
+            b.psd_batched_force_bound(form)
+            b.psd_release_workspaces()
+            res.append(Batch(ms).run("fp16"))
+    finally:
+        b.psd_batched_force_bound(-1)
+    (o0, i0), (o1, i1) = res
+    for k in range(len(ms)):
+        assert i0[k]["status"] == 0, k
+        assert np.array_equal(o0[k], o1[k]), (k, ms[k].shape[0])
+        assert i1[k] == i0[k], (k, ms[k].shape[0])

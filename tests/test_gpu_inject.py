@@ -5,8 +5,10 @@ norm bound scaled below ||X||_2 (the filter then sees a spectrum beyond its
 basin, which the overshoot report must catch) and a zero wait limit for the
 persistent norm bound's grid barriers (every barrier that is not already
 complete gives up at once; the CTAs leave at their next barrier and the status
-word carries PSD_ERR_TIMEOUT).  After each, the defaults are restored and a
-normal call on the same context must give the usual result, bit for bit.
+word carries PSD_ERR_TIMEOUT; the batched bound's dependency waits give up the
+same way and every block of the batch reports it).  After each, the defaults
+are restored and a normal call on the same context must give the usual
+result, bit for bit.
 """
 import numpy as np
 import pytest
@@ -81,3 +83,37 @@ def test_barrier_timeout_is_reported_and_the_context_stays_usable(wigner):
     assert info1["status"] == 0
     assert info1["lambda_bound"] == info0["lambda_bound"]
     assert torch.equal(again.view(torch.int32), ref.view(torch.int32))
+
+
+def test_batched_wait_timeout_is_reported_for_every_block():
+    # the batched bound's one-launch form waits on per-block counters
+    sizes = [700, 33, 256, 5, 1024, 129]
+    mats = [torch.from_numpy(synth.wigner(n, 3100 + i)).to(DEV) for i, n in enumerate(sizes)]
+    outs = [torch.full_like(M, float("nan")) for M in mats]
+    infos = [torch.zeros(b.INFO_BYTES, dtype=torch.uint8, device=DEV) for _ in mats]
+    descs = b.block_descs([(n, M, n, o, n, i) for n, M, o, i in zip(sizes, mats, outs, infos)])
+
+    def run():
+        for i in infos:
+            i.zero_()
+        b.psd_project_batched(len(sizes), descs, "fp16")
+        torch.cuda.synchronize()
+        return [o.cpu().clone() for o in outs], [b.info_from_bytes(i.cpu().numpy()) for i in infos]
+
+    prev = b.psd_batched_force_bound(1)
+    try:
+        ref, info0 = run()
+        assert all(i["status"] == 0 for i in info0)
+        try:
+            b.psd_debug_set(b.DEBUG_BARRIER_LIMIT_NS, 0)
+            _, info = run()
+        finally:
+            b.psd_debug_set(b.DEBUG_BARRIER_LIMIT_NS, 4e9)
+        again, info1 = run()
+    finally:
+        b.psd_batched_force_bound(prev)
+    assert all(i["status"] == PSD_ERR_TIMEOUT for i in info), [i["status"] for i in info]
+    assert all(i["status"] == 0 for i in info1)
+    for r, a, i0, i1 in zip(ref, again, info0, info1):
+        assert torch.equal(a.view(torch.int32), r.view(torch.int32))
+        assert i1 == i0
