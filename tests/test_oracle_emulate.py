@@ -180,3 +180,23 @@ def test_fp16_plain_misses_2e3_on_dominated_spectra(fam):
         assert _err(fam[k], plain) < 2e-3, k
     for k in ("clustered", "powerlaw"):
         assert _err(fam[k], plain) > 2e-3, k
+
+
+
+def test_fp16_with_early_polynomial_pairs_is_a_partial_remedy(fam):
+    # Plain FP16 except P of stages 2 and 3, stored as FP16 pairs (X P then
+    # costs two products, Y^2 with a pair output one): 24 tensor products.  It
+    # brings the clustered spectrum under 2e-3 and cuts every family's error,
+    # but not on this power-law instance, whose largest eigenvalues are
+    # negative (||F(X)||_F far below ||X||_2): there the roundings of the
+    # iterates themselves count, which only pairs for X_t (mixed-like costs)
+    # remove.  Not built as a precision for that reason.
+    pp = em.Plan(T, "f16", ["f16"] * T, ["f16", "f16x2", "f16x2", "f16", "f16", "f16", "f16"], ["f16"] * T)
+    plain = em.Plan.uniform(T, "f16")
+    assert pp.products() == 24
+    for k, case in fam.items():
+        assert _err(case, pp) < 0.85 * _err(case, plain), k
+    for k in ("gaussian", "wigner", "uniform", "clustered"):
+        assert _err(fam[k], pp) < 2e-3, k
+    assert _err(fam["clustered"], plain) > 2e-3
+    assert _err(fam["powerlaw"], pp) > 2e-3
