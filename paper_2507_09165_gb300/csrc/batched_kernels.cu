@@ -1054,13 +1054,13 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
 
 cudaError_t enqueue_batch_norm_bound_flow(const BatchLanczos& L, const int4* symv_items, int nsymv, const int4* flow,
                                           int nflow, unsigned* ctl, int count, cudaStream_t s) {
-  static int occ = 0;  // resident CTAs per SM (same on every device of a process: one GPU type)
-  if (occ == 0) {
+  // resident CTAs per SM (the same on every device of a process: one GPU
+  // type); computed once, thread-safe (function-local static)
+  static const int occ = [] {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bflow_kernel, kBT, 0) != cudaSuccess || o < 1)
-      return cudaErrorInvalidConfiguration;
-    occ = o;
-  }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bflow_kernel, kBT, 0) == cudaSuccess ? o : 0;
+  }();
+  if (occ < 1) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (2 + count), s);
   if (e != cudaSuccess) return e;
   BatchLanczos Lk = L;
