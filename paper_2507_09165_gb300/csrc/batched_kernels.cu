@@ -305,20 +305,6 @@ __device__ __forceinline__ void btile_reduce(int n, int bi, int bj, const float 
   }
 }
 
-template <bool STATS, bool DIAG>
-__device__ __forceinline__ void bsymv_tile(const float* __restrict__ T, int n, int bi, int bj,
-                                           const float* __restrict__ vh, float2* __restrict__ P1,
-                                           float2* __restrict__ P2, double* __restrict__ tile_fro,
-                                           int tile_slot, unsigned* maxdiag, float2 (*red)[kSymvTile],
-                                           double* fro_sh) {
-  float vi[8], vj[8], x[8][8];
-  btile_load_v<false>(vh, n, bi, bj, vi, vj);
-  btile_load_x<false>(T, n, bi, bj, x);
-  float rsum[8], csum[8], fro;
-  unsigned mdiag;
-  btile_fma<STATS, DIAG>(n, bi, bj, vi, vj, x, rsum, csum, fro, mdiag);
-  btile_reduce<STATS>(n, bi, bj, rsum, csum, fro, mdiag, P1, P2, tile_fro, tile_slot, maxdiag, red, fro_sh);
-}
 
 // Copies the 128 x 128 upper tiles of every block out of the caller's
 // matrices into L.xt, one contiguous 64 KB tile per mat-vec work item (column
@@ -348,33 +334,58 @@ __global__ void __launch_bounds__(256) bpack_kernel(BatchLanczos L, const int4* 
 // previous one read last, still in L2 (the packed tiles of a large batch
 // exceed L2).  The item -> partial slot mapping does not change: results are
 // identical.
-template <bool STATS>
-__device__ __forceinline__ void ph_bsymv(const BatchLanczos& L, const int4* __restrict__ items, int idx, bool skip,
-                                         float2 (*red)[kSymvTile], double* fro_sh) {
-  const int4 it = items[idx];
-  const int b = it.x;
-  // the block record and the done flag are independent loads: issue both
-  // before the branch
-  const BatchBlock bb = L.blk[b];
-  const int done = L.st[b].done;
-  const BView v = view_of(L, bb);
-  const float* T = L.xt + static_cast<int64_t>(idx) * kSymvTile * kSymvTile;
-  if (done && !STATS && skip) return;
-  if (it.y == it.z)
-    bsymv_tile<STATS, true>(T, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
-                            &L.st[b].maxdiag_bits, red, fro_sh);
-  else
-    bsymv_tile<STATS, false>(T, v.n, it.y, it.z, v.vh, v.P1, v.P2, L.tile_fro, it.w,
-                             &L.st[b].maxdiag_bits, red, fro_sh);
-}
 
+// The grouped mat-vec as a persistent launch: CTA c takes the items r = c,
+// c + G, ... (in the opposite order of the item list if `reverse`), and each
+// next tile's X and input slices are loaded while the previous tile is
+// reduced (a CTA per tile waits out every tile's load latency, and the small
+// blocks' mostly empty tiles cost as much as full ones).  Same per-tile
+// arithmetic and partial-sum slots as one CTA per tile: identical results.
 template <bool STATS>
-__global__ void __launch_bounds__(256, 2) bsymv_kernel(BatchLanczos L, const int4* __restrict__ items, int reverse) {
+__global__ void __launch_bounds__(256, 2) bsymv_run_kernel(BatchLanczos L, const int4* __restrict__ items, int nitems,
+                                                          int reverse) {
   __shared__ float2 red[8][kSymvTile];
   __shared__ double fro_sh[8];
-  const int idx = reverse ? static_cast<int>(gridDim.x) - 1 - static_cast<int>(blockIdx.x) : static_cast<int>(blockIdx.x);
-  ph_bsymv<STATS>(L, items, idx, L.skip_done != 0, red, fro_sh);
+  const int G = static_cast<int>(gridDim.x);
+  auto item_at = [&](int r) { return reverse ? nitems - 1 - r : r; };
+  int r = static_cast<int>(blockIdx.x);
+  if (r >= nitems) return;
+  int idx = item_at(r);
+  int4 it = items[idx];
+  BatchBlock bb = L.blk[it.x];
+  float x[8][8], vi[8], vj[8];
+  btile_load_x<false>(L.xt + static_cast<int64_t>(idx) * kSymvTile * kSymvTile, bb.n, it.y, it.z, x);
+  btile_load_v<false>(view_of(L, bb).vh, bb.n, it.y, it.z, vi, vj);
+  while (true) {
+    const BView v = view_of(L, bb);
+    const bool live = STATS || !(L.skip_done && L.st[it.x].done);
+    float rsum[8], csum[8], fro;
+    unsigned mdiag;
+    if (live) {
+      if (it.y == it.z)
+        btile_fma<STATS, true>(v.n, it.y, it.z, vi, vj, x, rsum, csum, fro, mdiag);
+      else
+        btile_fma<STATS, false>(v.n, it.y, it.z, vi, vj, x, rsum, csum, fro, mdiag);
+    }
+    const int rn = r + G;
+    const int4 cur = it;
+    const int cur_b = it.x;
+    if (rn < nitems) {  // in flight during the reduction
+      idx = item_at(rn);
+      it = items[idx];
+      bb = L.blk[it.x];
+      btile_load_x<false>(L.xt + static_cast<int64_t>(idx) * kSymvTile * kSymvTile, bb.n, it.y, it.z, x);
+      btile_load_v<false>(view_of(L, bb).vh, bb.n, it.y, it.z, vi, vj);
+    }
+    if (live)
+      btile_reduce<STATS>(v.n, cur.y, cur.z, rsum, csum, fro, mdiag, v.P1, v.P2, L.tile_fro, cur.w,
+                          &L.st[cur_b].maxdiag_bits, red, fro_sh);
+    if (rn >= nitems) break;
+    __syncthreads();  // red is written again by the next tile
+    r = rn;
+  }
 }
+
 
 // y_e of block b from its partial sums (fixed order, double-float, normalised), e < n:
 // P1 of the tiles bj = b(e) .. nb - 1, then P2 of bi = 0 .. b(e).  All (at most
@@ -798,7 +809,7 @@ __device__ __forceinline__ void btile_of(int t, int& bi, int& bj) {
 // Mat-vec item: tiles first .. first + cnt - 1 of block b (consecutive entries
 // of the tile list), the packed X of the first already in x; each next tile's
 // X and input slices are loaded while the previous tile is reduced.  Per
-// tile the same arithmetic as bsymv_tile.
+// tile the same arithmetic as the grouped mat-vec (bsymv_run_kernel).
 template <bool STATS>
 __device__ __forceinline__ void ph_bsymv_run(const BatchLanczos& L, int b, int first, int cnt, float (&x)[8][8],
                                              float2 (*red)[kSymvTile], double* fro_sh) {
@@ -1025,6 +1036,14 @@ __global__ void bfinalize_kernel(const BatchBlock* __restrict__ blk, DevState* s
 
 cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int4* symv_items, int nsymv,
                                      cudaStream_t s) {
+  // resident CTAs per SM of the persistent mat-vec (computed once, thread-safe)
+  static const int occ = [] {
+    int o = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bsymv_run_kernel<false>, 256, 0) == cudaSuccess ? o
+                                                                                                            : 0;
+  }();
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int mv_grid = std::max(1, std::min(occ * num_sms(), nsymv));
   BatchLanczos Lk = L;
   Lk.skip_done = 0;
   bpack_kernel<<<nsymv, 256, 0, s>>>(Lk, symv_items);
@@ -1033,21 +1052,21 @@ cudaError_t enqueue_batch_norm_bound(const BatchLanczos& L, int count, const int
   for (int j = 0; j < kMaxSteps; ++j) {
     Lk.skip_done = j == 0 ? 0 : 1;
     if (j == 0) {
-      bsymv_kernel<true><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
+      bsymv_run_kernel<true><<<mv_grid, 256, 0, s>>>(Lk, symv_items, nsymv, pass++ & 1);
       bfro_kernel<<<count, 32, 0, s>>>(Lk);
     } else {
-      bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
+      bsymv_run_kernel<false><<<mv_grid, 256, 0, s>>>(Lk, symv_items, nsymv, pass++ & 1);
     }
     breduce_kernel<<<count, kBT, 0, s>>>(Lk, 0);
     Lk.skip_done = 1;
-    bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
+    bsymv_run_kernel<false><<<mv_grid, 256, 0, s>>>(Lk, symv_items, nsymv, pass++ & 1);
     bstep_kernel<<<count, kBT, 0, s>>>(Lk, j);
   }
   britz_kernel<<<count, kBT, 0, s>>>(Lk);
   Lk.skip_done = 0;
-  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
+  bsymv_run_kernel<false><<<mv_grid, 256, 0, s>>>(Lk, symv_items, nsymv, pass++ & 1);
   breduce_kernel<<<count, kBT, 0, s>>>(Lk, 1);
-  bsymv_kernel<false><<<nsymv, 256, 0, s>>>(Lk, symv_items, pass++ & 1);
+  bsymv_run_kernel<false><<<mv_grid, 256, 0, s>>>(Lk, symv_items, nsymv, pass++ & 1);
   bbound_kernel<<<count, kBT, 0, s>>>(Lk);
   return cudaGetLastError();
 }
