@@ -70,11 +70,11 @@ def tensor_pipe(prec, n):
 
 
 # Tensor-core products of one projection per precision (each symmetric product does
-# n^3 (1 + 256/n) flops): fp16/bf16 22 (3T + 1, T = 7); mixed 32 (stages 1-3: Y with a pair
-# output 1, Y^2 of pairs 3, P X 2; stage 4: Y 1, P with a pair output 1, P X 2; stages 5-7
-# three each; final 1); fp32 93 TF32 products
+# n^3 (1 + 256/n) flops): fp16/bf16 22 (3T + 1, T = 7); mixed 30 (stages 2-3: Y with a pair
+# output 1, Y^2 of pairs 3, P X 2; stages 1 and 4: Y 1, P with a pair output 1, P X 2; stages
+# 5-7 three each; final 1); fp32 93 TF32 products
 # (31 split products of 3), whose peak is half the bf16 rate.
-CHAIN_PRODUCTS = {"fp16": (22, 1.0), "bf16": (22, 1.0), "mixed": (32, 1.0), "fp32": (93, 0.5)}
+CHAIN_PRODUCTS = {"fp16": (22, 1.0), "bf16": (22, 1.0), "mixed": (30, 1.0), "fp32": (93, 0.5)}
 
 
 def step_roofline(prec, n, ms_step, peak_bf16):
@@ -113,7 +113,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=10000)
     ap.add_argument("--precision", default="mixed",
-                    help="mixed (FP16 iterates, Y and P as FP16 hi/lo pairs in stages 1-3, P in stage 4; "
+                    help="mixed (FP16 iterates, P as FP16 hi/lo pairs in stages 1-4, Y in stages 2-3; "
                          "meets rel err <= 1e-3), "
                          "fp16, bf16, fp32, fp8_late")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the full-size accuracy check")
@@ -642,7 +642,7 @@ def run_ours(args):
     e2e_ms = reduce_max(ev0.elapsed_time(ev1) / e2e_steps, dev) if e2e_steps else None
 
     # dominant kernel: the symmetric tensor-core product of the chain, same kernel, shape and
-    # form as in the projection (mixed: the FP16-pair split product of stages 1-3; fp16/bf16:
+    # form as in the projection (mixed: the FP16-pair split product of stages 2-3; fp16/bf16:
     # the 16-bit product; both on SM pairs; fp32: the TF32x3 split product on one SM), timed
     # alone with CUDA events on the launching stream
     ld = (n + 63) // 64 * 64

@@ -69,11 +69,12 @@ typedef enum {
   PSD_PREC_FP16 = 1,  /* f~*_half (Table 2), T = 7, 22 products, FP16 operands,
                          FP32 accumulation in tensor memory */
   PSD_PREC_BF16 = 2,  /* as FP16 with BF16 operands */
-  PSD_PREC_MIXED = 3, /* f~*_half with FP16 iterates; in stages 1-3 Y = X^2 and
-                         the stage polynomial P are FP16 hi/lo pairs (Y^2 as
-                         three FP16 products, X P as two), in stage 4 P alone
-                         (formed from a single Y with a pair output); FP32
-                         accumulation; 32 tensor products in all */
+  PSD_PREC_MIXED = 3, /* f~*_half with FP16 iterates; in stages 1-4 the stage
+                         polynomial P is an FP16 hi/lo pair (X P as two FP16
+                         products), in stages 2-3 Y = X^2 too (Y^2 as three);
+                         in stages 1 and 4 P is formed from a single Y with a
+                         pair output; FP32 accumulation; 30 tensor products in
+                         all */
   PSD_PREC_FP8_EARLY = 4, /* reserved, returns PSD_ERR_UNSUPPORTED: e4m3 iterates in
                              the first stages diverge (the stage-1 coefficients
                              amplify the rounding of X^2 beyond the filter's basin) */

@@ -208,13 +208,13 @@ def chain_error(X, lam_tilde, coefs, scales, plan, ref=None):
 def named_plan(name, T=7):
     """Storage plans of the half-precision chain (T = 7) by precision name:
     "fp16" / "bf16": every matrix in that format (the paper's half-precision
-    chain); "mixed": FP16 iterates, Y and P as FP16 pairs in stages 1-3 and P
-    alone in stage 4; "fp8_late": FP16, with stages 6-7 and their input iterate
+    chain); "mixed": FP16 iterates, P as an FP16 pair in stages 1-4 and Y too
+    in stages 2-3; "fp8_late": FP16, with stages 6-7 and their input iterate
     in e4m3 (X_T in FP16)."""
     if name in ("fp16", "bf16"):
         return Plan.uniform(T, {"fp16": "f16", "bf16": "bf16"}[name], name)
     if name == "mixed":
-        y = ["f16x2" if t < 3 else "f16" for t in range(T)]
+        y = ["f16x2" if 1 <= t <= 2 else "f16" for t in range(T)]
         p = ["f16x2" if t < 4 else "f16" for t in range(T)]
         return Plan(T, "f16", y, p, ["f16"] * T, name)
     if name == "fp8_late":

@@ -46,13 +46,16 @@ inline int kind_dtype(const Mat& m) {
 inline int kind_lo_step(int kind) { return kind == MK_TF32X3 ? 2 : 1; }
 inline bool kind_is_pair(int kind) { return kind == MK_TF32X3 || kind == MK_F16X2; }
 
-// Mixed precision: Y and P of the first kMixedPairStages stages as FP16 pairs
-// (X_t stays FP16; a CPU emulation of the chain shows the roundings of Y and P
-// in the early stages carry the error, those of X_t do not), then
-// kMixedPStages stages with only P as a pair (Y = X^2 single, P formed from
-// it with a pair output: 4 tensor products instead of 6), the rest FP16.
-constexpr int kMixedPairStages = 3;
-constexpr int kMixedPStages = 1;
+// Mixed precision: P of the first kMixedPStages stages as an FP16 pair, and Y
+// of stages kMixedYFirst .. kMixedYLast (0-based) too; X_t stays FP16.  The
+// rounding model of the chain (CPU) shows the roundings of P and Y in the
+// early stages carry the error, those of X_t do not, and stage 1's Y the
+// least of them: without its pair the model's error grows from ~7e-4 to
+// ~8-9e-4 on spread spectra (and not at all on dominated ones) for one
+// pair x pair product less.  A stage with a single Y forms P from it with a
+// pair output (4 tensor products instead of 6).
+constexpr int kMixedPStages = 4;
+constexpr int kMixedYFirst = 1, kMixedYLast = 2;
 // FP8_LATE: the last kFp8Stages stages on e4m3 operands.  The first stages
 // cannot be: their coefficients (a_1 = 8.29, b_1 = -22.6) amplify the e4m3
 // rounding of X^2 (u = 2^-4) beyond the composite's basin.
@@ -87,10 +90,8 @@ inline StageKinds stage_kinds(psd_precision_t prec, int t, int T) {
   };
   StageKinds k{};
   k.x = xk(t);
-  if (prec == PSD_PREC_MIXED && t < kMixedPairStages) {
-    k.y = k.p = MK_F16X2;
-  } else if (prec == PSD_PREC_MIXED && t < kMixedPairStages + kMixedPStages) {
-    k.y = MK_16;
+  if (prec == PSD_PREC_MIXED && t < kMixedPStages) {
+    k.y = (t >= kMixedYFirst && t <= kMixedYLast) ? MK_F16X2 : MK_16;
     k.p = MK_F16X2;
   } else {
     k.y = k.p = k.x;
