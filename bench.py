@@ -46,11 +46,11 @@ ROOFLINE_TRAFFIC = {
 TENSOR_PIPE_SOURCES = ("chain.h", "internal.h", "normbound.cu", "psdproj.cu", "ptx.cuh", "symgemm.cu",
                        "symgemm_x3.cu", "tridiag.cuh")
 TENSOR_PIPE = {
-    "mixed": {"projection_pct": 77.15, "products_pct": 87.68,
-              "sha256": "296de588f8fdebef685b94f52d7f8445cc299c1c57432ebd42f0c91ad72d765b",
+    "mixed": {"projection_pct": 76.57, "products_pct": 87.17,
+              "sha256": "4ad25428269e9851a612e71a59668703c50ee19cf13e7fa3dc9d206f16f7e0d6",
               "profile": "profiles/tensor_pipe_n10000.md"},
-    "fp16": {"projection_pct": 70.98, "products_pct": 83.82,
-             "sha256": "296de588f8fdebef685b94f52d7f8445cc299c1c57432ebd42f0c91ad72d765b",
+    "fp16": {"projection_pct": 71.13, "products_pct": 83.84,
+             "sha256": "4ad25428269e9851a612e71a59668703c50ee19cf13e7fa3dc9d206f16f7e0d6",
              "profile": "profiles/tensor_pipe_n10000.md"},
 }
 
