@@ -245,7 +245,9 @@ __device__ __forceinline__ void btile_fma(int n, int bi, int bj, const float (&v
 // Combines the threads' sums in a fixed order (double-float) into the tile's
 // row partials P1[bj][rows] and column partials P2[bi][columns]; STATS: the
 // tile's share of ||X||_F^2 and max |X_ii|.  `red` is read after its barrier:
-// a loop over tiles needs another barrier before the next tile writes it.
+// a loop over tiles alternates two buffers, since a tile two ahead writes one
+// only after every thread has passed the barrier of the tile between (and so
+// finished reading it).
 template <bool STATS>
 __device__ __forceinline__ void btile_reduce(int n, int bi, int bj, const float (&rsum)[8], const float (&csum)[8],
                                              float fro, unsigned mdiag, float2* __restrict__ P1,
@@ -344,9 +346,10 @@ __global__ void __launch_bounds__(256) bpack_kernel(BatchLanczos L, const int4* 
 template <bool STATS>
 __global__ void __launch_bounds__(256, 2) bsymv_run_kernel(BatchLanczos L, const int4* __restrict__ items, int nitems,
                                                           int reverse) {
-  __shared__ float2 red[8][kSymvTile];
+  __shared__ float2 red[2][8][kSymvTile];  // consecutive live tiles alternate (btile_reduce)
   __shared__ double fro_sh[8];
   const int G = static_cast<int>(gridDim.x);
+  int buf = 0;
   auto item_at = [&](int r) { return reverse ? nitems - 1 - r : r; };
   int r = static_cast<int>(blockIdx.x);
   if (r >= nitems) return;
@@ -377,11 +380,12 @@ __global__ void __launch_bounds__(256, 2) bsymv_run_kernel(BatchLanczos L, const
       btile_load_x<false>(L.xt + static_cast<int64_t>(idx) * kSymvTile * kSymvTile, bb.n, it.y, it.z, x);
       btile_load_v<false>(view_of(L, bb).vh, bb.n, it.y, it.z, vi, vj);
     }
-    if (live)
+    if (live) {
       btile_reduce<STATS>(v.n, cur.y, cur.z, rsum, csum, fro, mdiag, v.P1, v.P2, L.tile_fro, cur.w,
-                          &L.st[cur_b].maxdiag_bits, red, fro_sh);
+                          &L.st[cur_b].maxdiag_bits, red[buf], fro_sh);
+      buf ^= 1;
+    }
     if (rn >= nitems) break;
-    __syncthreads();  // red is written again by the next tile
     r = rn;
   }
 }
@@ -812,7 +816,7 @@ __device__ __forceinline__ void btile_of(int t, int& bi, int& bj) {
 // tile the same arithmetic as the grouped mat-vec (bsymv_run_kernel).
 template <bool STATS>
 __device__ __forceinline__ void ph_bsymv_run(const BatchLanczos& L, int b, int first, int cnt, float (&x)[8][8],
-                                             float2 (*red)[kSymvTile], double* fro_sh) {
+                                             float2 (*red)[8][kSymvTile], double* fro_sh) {
   const BatchBlock bb = L.blk[b];
   const BView v = view_of(L, bb);
   int bi, bj;
@@ -833,14 +837,13 @@ __device__ __forceinline__ void ph_bsymv_run(const BatchLanczos& L, int b, int f
       btile_load_v<true>(v.vh, v.n, bi, bj, vi, vj);
     }
     btile_reduce<STATS>(v.n, ci, cj, rsum, csum, fro, mdiag, v.P1, v.P2, L.tile_fro, first + k,
-                        &L.st[b].maxdiag_bits, red, fro_sh);
-    if (k + 1 < cnt) __syncthreads();  // red is written again by the next tile
+                        &L.st[b].maxdiag_bits, red[k & 1], fro_sh);
   }
 }
 
 __global__ void __launch_bounds__(kBT, 2) bflow_kernel(BatchLanczos L, const int4* __restrict__ flow, int nflow,
                                                       unsigned* ctl, unsigned* cnt) {
-  __shared__ float2 red[8][kSymvTile];
+  __shared__ float2 red[2][8][kSymvTile];  // tiles of an item alternate (btile_reduce)
   __shared__ double fro_sh[8];
   __shared__ int claim_sh[2];
   __shared__ int ok_sh;

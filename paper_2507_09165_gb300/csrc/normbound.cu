@@ -108,7 +108,7 @@ static_assert(kVecThreads == kNT, "vector phases: one element per thread of a 25
 struct NBShared {
   union {
     struct {
-      float2 red[8][kSymvTile];
+      float2 red[2][8][kSymvTile];  // two buffers: consecutive tiles of a run alternate
       double fro[8];
     } mv;
     float2 part[8][32];
@@ -268,14 +268,18 @@ __device__ __forceinline__ void tile_fma(int n, const TileGeom& g, const float (
 }
 
 // Combines the threads' sums in a fixed order (double-float) into the tile's
-// row partials P1[bj][rows] and column partials P2[bi][columns].  Ends with a
-// CTA barrier (the shared buffers are reused by the next tile).
+// row partials P1[bj][rows] and column partials P2[bi][columns], through row
+// buffer `buf`.  Ends with a CTA barrier unless `sync_after` is false: a run
+// of tiles alternates the two buffers instead, since a tile two ahead writes a
+// buffer only after every thread has passed the barrier of the tile between
+// (and so finished reading it); the run is followed by a CTA barrier.
 template <bool STATS>
 __device__ __forceinline__ void tile_reduce_store(int n, const TileGeom& g, const float (&rsum)[8],
                                                   const float (&csum)[8], float fro, unsigned mdiag, float2* P1,
                                                   float2* P2, int64_t ps, double* tile_fro, DevState* st,
-                                                  NBShared& sh, int tile) {
-  float2 (*red)[kSymvTile] = sh.u.mv.red;
+                                                  NBShared& sh, int tile, int buf = 0,
+                                                  bool sync_after = true) {
+  float2 (*red)[kSymvTile] = sh.u.mv.red[buf];
   const int i0 = g.bi * kSymvTile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tr = lane & 15;
@@ -333,7 +337,7 @@ __device__ __forceinline__ void tile_reduce_store(int n, const TileGeom& g, cons
       tile_fro[tile] = sum;
     }
   }
-  __syncthreads();
+  if (sync_after) __syncthreads();
 }
 
 // Tile t of a product over X (t in [0, ntiles)), one tile per call.
@@ -352,7 +356,8 @@ __device__ __forceinline__ void ph_symv(const NBCtx& c, const float* X, int64_t 
 
 // Tiles r = first, first + stride, ... < ntiles of a product (in the
 // opposite order of the tile list if `rev`), each loaded while the previous
-// one is reduced: the same arithmetic per tile as ph_symv.
+// one is reduced: the same arithmetic per tile as ph_symv.  The caller ends
+// the run with a CTA barrier (the grid barrier after the phase).
 template <bool STATS>
 __device__ __forceinline__ void ph_symv_run(const NBCtx& c, const float* X, int64_t ld, int first, int stride,
                                             bool rev, NBShared& sh) {
@@ -360,6 +365,7 @@ __device__ __forceinline__ void ph_symv_run(const NBCtx& c, const float* X, int6
   auto tile_at = [&](int r) { return rev ? c.ntiles - 1 - r : r; };
   float vi[8], vj[8], x[8][8];
   int r = first;
+  int buf = 0;
   TileGeom g = tile_geom(tile_at(r));
   tile_load(X, ld, c.n, g, c.vh, vi, vj, x);
   while (true) {
@@ -373,10 +379,11 @@ __device__ __forceinline__ void ph_symv_run(const NBCtx& c, const float* X, int6
     const TileGeom gn = tile_geom(tile_at(rn < c.ntiles ? rn : r));
     if (rn < c.ntiles) tile_load(X, ld, c.n, gn, c.vh, vi, vj, x);  // in flight during the reduction
     tile_reduce_store<STATS>(c.n, g, rsum, csum, fro, mdiag, c.P1, c.P2, c.npad, c.tile_fro, c.st, sh,
-                             tile_at(r));
+                             tile_at(r), buf, false);
     if (rn >= c.ntiles) break;
     r = rn;
     g = gn;
+    buf ^= 1;
   }
 }
 
