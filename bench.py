@@ -46,11 +46,11 @@ ROOFLINE_TRAFFIC = {
 TENSOR_PIPE_SOURCES = ("chain.h", "internal.h", "normbound.cu", "psdproj.cu", "ptx.cuh", "symgemm.cu",
                        "symgemm_x3.cu", "tridiag.cuh")
 TENSOR_PIPE = {
-    "mixed": {"projection_pct": 76.57, "products_pct": 87.17,
-              "sha256": "4ad25428269e9851a612e71a59668703c50ee19cf13e7fa3dc9d206f16f7e0d6",
+    "mixed": {"projection_pct": 76.46, "products_pct": 87.16,
+              "sha256": "454acbe484f18579ca1009885be5105da92691aab1572739f8c6b05776700208",
               "profile": "profiles/tensor_pipe_n10000.md"},
-    "fp16": {"projection_pct": 71.13, "products_pct": 83.84,
-             "sha256": "4ad25428269e9851a612e71a59668703c50ee19cf13e7fa3dc9d206f16f7e0d6",
+    "fp16": {"projection_pct": 71.10, "products_pct": 83.85,
+             "sha256": "454acbe484f18579ca1009885be5105da92691aab1572739f8c6b05776700208",
              "profile": "profiles/tensor_pipe_n10000.md"},
 }
 
