@@ -163,9 +163,10 @@ typedef struct {
 } psd_block_desc_t;
 
 /* Projects `count` independent blocks with one sequence of grouped launches
- * (norm bound, cast and each of the 3T + 1 products is one launch over all
- * blocks), captured in a CUDA graph per (device, stream, precision, block
- * orders).  d_descs is an array of `count` descriptors in DEVICE memory; the
+ * (each phase of the norm bound -- a mat-vec over every block's upper tiles,
+ * the blocks' Lanczos steps --, the cast and each of the 3T + 1 products is
+ * one launch over all blocks), captured in a CUDA graph per (device, stream,
+ * precision, block orders).  d_descs is an array of `count` descriptors in DEVICE memory; the
  * library reads it back once per call (a synchronous copy of count * 48
  * bytes) to find the plan for the block orders.  Every block's result depends
  * only on that block: it is bit-identical to a batched call with that block
